@@ -1,0 +1,288 @@
+"""Oracle, part 2: the MRT-LB time step (FP64, numpy).
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import this module; only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use it.
+
+The step follows Shi, Yuan & Chai (arXiv 2512.16230) in the paper's order:
+
+* state: the transformed distribution f-bar of the full-correction scheme, Eq. (2-3);
+* macroscopic fields with the half-source correction: Eq. (2-4-2) (NSE) and Eq. (2-4-1) (NCDE);
+* equilibrium moments in the Hermite basis from the continuous moments M0..M3 of
+  Eq. (M-NSEs-6a) / (M-NSEs-6-1) with k = 0 and M30 = rho u u u (Sec. 3.4: multispeed lattices),
+  p = rho * cs2_eq (isothermal); for the NCDE from Eq. (M-NCDE-6): M0 = phi, M1 = u phi,
+  M2 = cs2_eq D(phi) I with M20 = 0;
+* the EDF and the source distributions from their Hermite moments by Eq. (feq-1) / Eq. (geq);
+* the collision f~ = f - Lambda f^ne + dt [G + (I - Lambda/2) F] of Eq. (2-3) with
+  Lambda = H^{-1} S H built from the full Q x Q Hermite matrix (Sec. 4, Eq. (H-MRT-LB));
+* propagation f(x + c_j dt, t + dt) = f~(x, t), Eq. (2-2b), periodic.
+
+Readings of points the paper leaves open (each is listed in the design notes):
+* NSE source split (Eq. (M-NSEs-2), (M-NSEs-5)): S = 0, F_F = F, F_G = 0, so the SDF F has
+  M0F = 0, M1F = F, M2F = 0 and G carries only M2G = (I - S2/2)(uF + Fu) (Eq. (M2Ga-1) with
+  S = 0); third-order Hermite moments of F and G are zero.
+* NCDE (App. A): S = 0, M1F = 0, G carries only M1G = (I - S1/2) d_t(u phi) with constant u
+  and d_t phi by the backward difference (phi^n - phi^{n-1}) / dt, phi^{-1} = phi^0;
+  the third-order Hermite moments of the NCDE equilibrium are zero.
+* rows of order >= 4 relax with one shared rate s_high.
+
+Arrays use the grid in C order with x fastest: a field has shape (n_z, n_y, n_x) in 3D and
+(n_y, n_x) in 2D; populations have a leading Q axis; velocity fields a leading d axis (u[0]=u_x).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import lattice as L
+
+
+def grid_shape(n):
+    """numpy shape of a field on a grid with n = (n_x, n_y[, n_z]) cells."""
+    return tuple(int(v) for v in reversed(n))
+
+
+def axis_of(alpha: int, d: int, lead: int = 1) -> int:
+    """numpy axis index of spatial axis alpha (0 = x) in an array with ``lead`` leading axes."""
+    return lead + (d - 1 - alpha)
+
+
+# ---------------------------------------------------------------------------------------------
+# Continuous moments and Hermite moments of the equilibrium
+# ---------------------------------------------------------------------------------------------
+
+def continuous_moment_nse(ex, rho, j, p):
+    """Raw continuous moment of the monomial with exponents ``ex`` for the NSE equilibrium:
+    M0 = rho, M1 = rho u, M2 = rho u u + p I, M3 = p (u_a d_bg + u_b d_ag + u_g d_ab) + rho u u u
+    (Eq. (M-NSEs-6a), Eq. (M-NSEs-6-1) with k = 0 and M30 = rho u u u)."""
+    axes = [a for a, k in enumerate(ex) for _ in range(k)]
+    u = [j[a] / rho for a in range(len(j))]
+    if len(axes) == 0:
+        return rho
+    if len(axes) == 1:
+        return j[axes[0]]
+    if len(axes) == 2:
+        a, b = axes
+        return rho * u[a] * u[b] + (p if a == b else 0.0)
+    if len(axes) == 3:
+        a, b, g = axes
+        out = rho * u[a] * u[b] * u[g]
+        if b == g:
+            out = out + p * u[a]
+        if a == g:
+            out = out + p * u[b]
+        if a == b:
+            out = out + p * u[g]
+        return out
+    raise ValueError("NSE equilibrium moments are specified up to third order")
+
+
+def hermite_moments_eq_nse(lat: L.Lattice, rho, j, cs2_eq):
+    """m^eq_r = P_r(M): each Hermite polynomial with its monomials replaced by the moments."""
+    p = rho * cs2_eq
+    out = []
+    for poly in lat.polys:
+        m = np.zeros_like(rho)
+        for ex, coef in poly.items():
+            m = m + coef * continuous_moment_nse(ex, rho, j, p)
+        out.append(m)
+    return np.stack(out)
+
+
+def hermite_moments_eq_ncde(lat: L.Lattice, phi, u_const, cs2_eq, nonlin):
+    """App. A, Eq. (M-NCDE-6): M0 = phi, M1 = B = u phi, M2 = cs2_eq D(phi) I (+ M20 = 0) with
+    D(phi) = phi + nonlin * phi^3 / 3; third-order Hermite moments zero."""
+    Dphi = phi + nonlin * phi ** 3 / 3.0
+    out = []
+    for poly, order in zip(lat.polys, lat.orders):
+        if order == 3:
+            out.append(np.zeros_like(phi))
+            continue
+        m = np.zeros_like(phi)
+        for ex, coef in poly.items():
+            axes = [a for a, k in enumerate(ex) for _ in range(k)]
+            if len(axes) == 0:
+                term = phi
+            elif len(axes) == 1:
+                term = u_const[axes[0]] * phi
+            else:
+                term = cs2_eq * Dphi if axes[0] == axes[1] else np.zeros_like(phi)
+            m = m + coef * term
+        out.append(m)
+    return np.stack(out)
+
+
+def from_hermite_moments(lat: L.Lattice, m):
+    """Eq. (feq-1) / Eq. (geq): g_i = w_i sum_k (H_k^T)_i (H_k W H_k^T)^{-1} m_{H,k}, k = 0..3.
+
+    ``m`` has shape (R, ncells); returns (Q, ncells)."""
+    out = np.zeros((lat.Q,) + m.shape[1:])
+    for k in range(4):
+        rows = lat.block(k)
+        Hk = lat.H[rows]                                  # (n_k, Q)
+        Gk = Hk @ np.diag(lat.w) @ Hk.T                   # H_k W H_k^T
+        coef = np.linalg.inv(Gk) @ m[rows].reshape(len(rows), -1)
+        out += (lat.w[:, None] * (Hk.T @ coef)).reshape(out.shape)
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# Model
+# ---------------------------------------------------------------------------------------------
+
+@dataclass
+class Model:
+    """One MRT-LB solve on a periodic grid of n = (n_x, n_y[, n_z]) cells."""
+    lat: L.Lattice
+    eq: str                                  # "nse" or "ncde"
+    n: tuple
+    s: np.ndarray                            # relaxation rate of each Hermite row (R values)
+    s_high: float = 1.0                      # shared rate of all rows of order >= 4
+    cs2_eq: float | None = None              # p / rho (NSE); prefactor of D(phi) (NCDE)
+    force: tuple | None = None               # (a, b, A, k[, phase]): F = A sin(2 pi k x_b / L_b + phase) e_a
+    u_const: np.ndarray | None = None        # NCDE convection velocity
+    nonlin: float = 0.0                      # NCDE: D(phi) = phi + nonlin phi^3 / 3
+    f: np.ndarray = field(default=None, repr=False)          # f-bar, shape (Q, *grid)
+    phi_prev: np.ndarray = field(default=None, repr=False)   # NCDE: phi at the previous step
+    step_count: int = 0
+
+    def __post_init__(self):
+        self.n = tuple(int(v) for v in self.n)
+        self.s = np.asarray(self.s, dtype=np.float64)
+        if self.cs2_eq is None:
+            self.cs2_eq = float(self.lat.cs2[0])
+        Q = self.lat.Q
+        S = np.diag(np.concatenate([self.s, np.full(Q - self.lat.R, self.s_high)]))
+        self.Hinv = L.hermite_inverse(self.lat)
+        self.Lam = self.Hinv @ S @ self.lat.Hfull       # Lambda = H^{-1} S H
+        self.shape = grid_shape(self.n)
+        if self.u_const is not None:
+            self.u_const = np.asarray(self.u_const, dtype=np.float64)
+
+    # -- body force ---------------------------------------------------------------------------
+    def force_field(self):
+        """F(x) = A sin(2 pi k x_b / L_b + phase) e_a, x_b = i_b c_b the cell coordinate, L_b = n_b c_b."""
+        d = self.lat.d
+        F = np.zeros((d,) + self.shape)
+        if self.force is None:
+            return F
+        a, b, A, k = self.force[:4]
+        phase = self.force[4] if len(self.force) > 4 else 0.0
+        idx = np.arange(self.n[b])
+        prof = A * np.sin(2.0 * np.pi * k * idx / self.n[b] + phase)
+        bshape = [1] * d
+        bshape[axis_of(b, d, lead=0)] = self.n[b]
+        F[a] = np.broadcast_to(prof.reshape(bshape), self.shape)
+        return F
+
+    # -- fields ----------------------------------------------------------------------------------
+    def fields(self, f=None):
+        """Eq. (2-4-2) (NSE, S = 0, F_F = F): rho = sum f, u = (sum c f + dt F / 2) / rho;
+        Eq. (2-4-1) (NCDE, S = 0): phi = sum f."""
+        f = self.f if f is None else f
+        if self.eq == "ncde":
+            return np.sum(f, axis=0), None
+        rho = np.sum(f, axis=0)
+        F = self.force_field()
+        j = np.stack([np.tensordot(self.lat.cvel[:, a], f, axes=(0, 0)) for a in range(self.lat.d)])
+        u = (j + 0.5 * F) / rho
+        return rho, u
+
+    def equilibrium(self, rho_or_phi, u=None):
+        """Eq. (feq-1) for the fields given."""
+        flat = rho_or_phi.reshape(-1)
+        if self.eq == "nse":
+            j = (u * rho_or_phi[None]).reshape(self.lat.d, -1)
+            m = hermite_moments_eq_nse(self.lat, flat, j, self.cs2_eq)
+        else:
+            m = hermite_moments_eq_ncde(self.lat, flat, self.u_const, self.cs2_eq, self.nonlin)
+        return from_hermite_moments(self.lat, m).reshape((self.lat.Q,) + self.shape)
+
+    def init_fields(self, rho_or_phi, u=None):
+        """f-bar(t=0) = f^eq(rho, u) (or f^eq(phi)); for the NCDE phi^{-1} = phi^0."""
+        rho_or_phi = np.asarray(rho_or_phi, dtype=np.float64)
+        self.f = self.equilibrium(rho_or_phi, None if u is None else np.asarray(u, dtype=np.float64))
+        self.phi_prev = rho_or_phi.copy() if self.eq == "ncde" else None
+        self.step_count = 0
+
+    def set_populations(self, f):
+        self.f = np.array(f, dtype=np.float64, copy=True)
+        if self.eq == "ncde" and self.phi_prev is None:
+            self.phi_prev = np.sum(self.f, axis=0)
+
+    # -- sources --------------------------------------------------------------------------------
+    def source_moments(self, fields):
+        """Hermite moments of the SDF F and of the auxiliary G (shape (R, ncells) each)."""
+        lat = self.lat
+        R = lat.R
+        ncell = int(np.prod(self.shape))
+        mF = np.zeros((R, ncell))
+        mG = np.zeros((R, ncell))
+        if self.eq == "nse":
+            if self.force is None:
+                return mF, mG
+            F = self.force_field().reshape(lat.d, -1)
+            u = fields[1].reshape(lat.d, -1)
+            for r, poly in enumerate(lat.polys):
+                o = lat.orders[r]
+                if o == 1:
+                    # M1F = F_F = F (Eq. (M-NSEs-2)); the row H_a = c_a carries F_a
+                    (ex,) = poly.keys()
+                    mF[r] = F[ex.index(1)]
+                elif o == 2:
+                    # M2G = (I - S2/2)(uF + Fu) (Eq. (M2Ga-1), S = 0), M0G = 0 so the H2
+                    # Hermite moment equals the raw second moment
+                    axes = [a for a, k in enumerate(max(poly, key=sum)) for _ in range(k)]
+                    a, b = axes
+                    mG[r] = (1.0 - 0.5 * self.s[r]) * (u[a] * F[b] + F[a] * u[b])
+            return mF, mG
+        # NCDE: M1G = (I - S1/2) u d_t phi (Eq. (M-NCDE-6) with M20 = 0, A1 = A2 = 0)
+        phi = fields[0].reshape(-1)
+        dphi = phi - self.phi_prev.reshape(-1)
+        for r, poly in enumerate(lat.polys):
+            if lat.orders[r] == 1:
+                (ex,) = poly.keys()
+                a = ex.index(1)
+                mG[r] = (1.0 - 0.5 * self.s[r]) * self.u_const[a] * dphi
+        return mF, mG
+
+    # -- one step --------------------------------------------------------------------------------
+    def collide(self):
+        """Eq. (2-3) collision: f~ = f - Lambda (f - f^eq) + dt [G + (I - Lambda/2) F]."""
+        lat = self.lat
+        rho_or_phi, u = self.fields()
+        feq = self.equilibrium(rho_or_phi, u)
+        mF, mG = self.source_moments((rho_or_phi, u))
+        Fd = from_hermite_moments(lat, mF).reshape(lat.Q, -1)
+        Gd = from_hermite_moments(lat, mG).reshape(lat.Q, -1)
+        f = self.f.reshape(lat.Q, -1)
+        fne = f - feq.reshape(lat.Q, -1)
+        ft = f - self.Lam @ fne + Gd + Fd - 0.5 * (self.Lam @ Fd)
+        if self.eq == "ncde":
+            self.phi_prev = rho_or_phi.copy()
+        return ft.reshape(self.f.shape)
+
+    def stream(self, ft):
+        """Eq. (2-2b): f_j(x + c_j dt, t + dt) = f~_j(x, t) on the periodic grid."""
+        out = np.empty_like(ft)
+        d = self.lat.d
+        for i in range(self.lat.Q):
+            shifts = tuple(int(self.lat.e[i, a]) for a in range(d))
+            axes = tuple(axis_of(a, d, lead=0) for a in range(d))
+            out[i] = np.roll(ft[i], shifts, axis=axes)
+        return out
+
+    def step(self, nsteps=1):
+        for _ in range(int(nsteps)):
+            self.f = self.stream(self.collide())
+            self.step_count += 1
+
+    def stream_only(self, nsteps=1):
+        for _ in range(int(nsteps)):
+            self.f = self.stream(self.f)
+
+    # -- diagnostics -----------------------------------------------------------------------------
+    def conserved_sums(self):
+        """Global sum_x sum_j f_j and sum_x sum_j c_j f_j (FP64)."""
+        tot = np.sum(self.f, axis=tuple(range(1, self.f.ndim)))
+        return np.concatenate([[tot.sum()], self.lat.cvel.T @ tot])

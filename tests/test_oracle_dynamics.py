@@ -1,0 +1,402 @@
+"""Pins of the oracle's equilibrium, collision, streaming and dynamics (CPU only).
+
+The expected values come from the paper's closed forms and from the mathematics, never from
+the oracle itself: continuous moments M0..M3 (Eq. (M-NSEs-6a), (M-NSEs-6-1)), the textbook
+third-order Hermite equilibrium (square, sixth-order isotropic lattice), exact conservation
+(Sec. 3), the block form Eq. (H-MRT-LB-1), the BGK special case, the viscosity law Eq. (4-29)
+through Taylor-Green and Kolmogorov flows, the NCDE diffusivity K = dt cs2 (1/s1 - 1/2)
+(Eq. (ME-NCDE-3)) and the non-equilibrium stress that M2G is designed to produce
+(Eq. (M-NSEs-4)). Planted-mistake variants show the pins catch a dropped auxiliary term.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lattice as L
+from oracle import mrt as M
+from paper_2512_16230_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+LATS = {
+    "rD2Q25": ((1.0, 4.0 / 3.0), (0.8, 0.8), (3.125e-4,) * 4),
+    "rD2Q21": ((1.0, 4.0 / 3.0), (0.8, 0.8), (7.29e-4,) * 3),
+    "rD2Q17": ((1.0, 4.0 / 3.0), (0.8, 0.8), (2.1875e-3,)),
+    "rD2Q13": ((1.0, 1.25), (0.8, 0.8), ()),
+    "rD3Q53": ((1.0, 1.0, 4.0 / 3.0), (0.624,) * 3, (2.9625e-4,)),
+    "rD3Q45": ((1.0, 1.0, 1.0), (0.6,) * 3, ()),
+    "rD3Q33": ((1.0, 1.0, 1.0), (0.5,) * 3, ()),
+}
+ANISO = {
+    "rD2Q25": ((1.0, 1.2), (0.7, 0.9), (2e-4, 1e-4, 3e-4, 5e-5)),
+    "rD3Q53": ((1.0, 1.2, 4.0 / 3.0), (0.6, 0.62, 0.64), (1e-4,)),
+}
+
+
+def lattice(kind, aniso=False):
+    c, cs2, fw = (ANISO if aniso else LATS)[kind]
+    return L.build(kind, c, cs2, fw)
+
+
+def _mono(cvel, axes):
+    out = np.ones(cvel.shape[0])
+    for a in axes:
+        out = out * cvel[:, a]
+    return out
+
+
+@pytest.mark.parametrize("kind,aniso", [(k, False) for k in LATS] + [(k, True) for k in ANISO])
+def test_equilibrium_moments(kind, aniso):
+    """Eq. (feq-1) reproduces every raw moment up to third order of the EDF of Sec. 3:
+    M0 = rho, M1 = rho u, M2 = rho uu + pI, M3 = p (u delta)_sym + rho uuu, p = rho cs2_eq."""
+    lat = lattice(kind, aniso)
+    d = lat.d
+    n = (5,) * d
+    rho, u = I.random_fields(n, d, seed=3, rho_amp=0.05, u_amp=0.1)
+    cs2_eq = 0.63
+    m = M.Model(lat, "nse", n, np.ones(lat.R), cs2_eq=cs2_eq)
+    feq = m.equilibrium(rho, u).reshape(lat.Q, -1)
+    r = rho.reshape(-1)
+    uu = u.reshape(d, -1)
+    p = r * cs2_eq
+    eye = np.eye(d)
+    M2 = np.einsum("n,an,bn->abn", r, uu, uu) + np.einsum("ab,n->abn", eye, p)
+    M3 = (np.einsum("n,an,bn,cn->abcn", r, uu, uu, uu)
+          + np.einsum("n,an,bc->abcn", p, uu, eye) + np.einsum("n,bn,ac->abcn", p, uu, eye)
+          + np.einsum("n,cn,ab->abcn", p, uu, eye))
+    assert np.allclose(feq.sum(0), r, rtol=1e-14, atol=0)
+    for a in range(d):
+        assert np.allclose(_mono(lat.cvel, (a,)) @ feq, r * uu[a], rtol=0, atol=1e-14)
+    for a, b in itertools.product(range(d), repeat=2):
+        assert np.allclose(_mono(lat.cvel, (a, b)) @ feq, M2[a, b], rtol=0, atol=1e-13)
+    for a, b, g in itertools.product(range(d), repeat=3):
+        assert np.allclose(_mono(lat.cvel, (a, b, g)) @ feq, M3[a, b, g], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", list(LATS))
+def test_equilibrium_at_rest(kind):
+    """f^eq(rho, u = 0) = w rho when every c_sa^2 equals p / rho."""
+    lat = lattice(kind)
+    n = (4,) * lat.d
+    rho = 1.0 + I.random_scalar(n, seed=1, lo=-0.1, hi=0.1)
+    m = M.Model(lat, "nse", n, np.ones(lat.R))
+    feq = m.equilibrium(rho, np.zeros((lat.d,) + rho.shape))
+    assert np.allclose(feq, lat.w.reshape((-1,) + (1,) * lat.d) * rho[None], rtol=1e-14, atol=1e-16)
+
+
+def test_equilibrium_textbook_square_lattice():
+    """On a square, sixth-order isotropic lattice (App. C D2Q17 case 3) no correction is needed
+    and Eq. (feq-1) is the textbook third-order Hermite equilibrium
+    w rho [1 + cu/cs2 + ((cu)^2 - cs2 u^2)/(2 cs2^2) + (cu)((cu)^2 - 3 cs2 u^2)/(6 cs2^3)]."""
+    case = json.load(open(os.path.join(GOLDEN, "d2q17_cases.json")))["case3"]
+    e = np.array([case["ex"], case["ey"]]).T
+    W = {k: float(eval(v, {"sqrt": math.sqrt, "__builtins__": {}})) for k, v in case["w"].items()}
+    w = np.array([W["w0"]] + [W["w1"]] * 4 + [W["w5"]] * 4 + [W["w9"]] * 4 + [W["w13"]] * 4)
+    cs2 = 0.75
+    lat = L.build_from("D2Q17-case3", 2, np.ones(2), np.full(2, cs2), e, w)
+    assert max(abs(v) for v in lat.corr.values()) < 1e-15
+    n = (3, 3)
+    rho, u = I.random_fields(n, 2, seed=9, u_amp=0.1)
+    m = M.Model(lat, "nse", n, np.ones(lat.R), cs2_eq=cs2)
+    feq = m.equilibrium(rho, u)
+    cu = np.einsum("ja,a...->j...", lat.cvel, u)
+    u2 = (u ** 2).sum(0)
+    want = w.reshape(-1, 1, 1) * rho * (1 + cu / cs2 + (cu ** 2 - cs2 * u2) / (2 * cs2 ** 2)
+                                        + cu * (cu ** 2 - 3 * cs2 * u2) / (6 * cs2 ** 3))
+    assert np.allclose(feq, want, rtol=1e-13, atol=1e-16)
+
+
+def _model(kind, eq, n, seed=0, force=None, aniso=False, s=None, s_high=1.3):
+    lat = lattice(kind, aniso)
+    rng = np.random.default_rng(seed)
+    s = rng.uniform(0.6, 1.9, lat.R) if s is None else s
+    kw = {}
+    if eq == "ncde":
+        kw = dict(u_const=np.linspace(0.02, 0.05, lat.d), nonlin=1.0)
+    m = M.Model(lat, eq, n, s, s_high, force=force, **kw)
+    return lat, m
+
+
+@pytest.mark.parametrize("kind", list(LATS))
+def test_collision_conserves_mass_and_momentum(kind):
+    """Sec. 3 (e Lambda = s0 e, M0^ne, M1^ne): the collision keeps sum_j f per cell and changes
+    sum_j c_j f by exactly dt F (Eq. (2-3) with F_F = F); the NCDE collision keeps phi."""
+    lat = lattice(kind)
+    d = lat.d
+    n = (6,) * (d - 1) + (5,)
+    _, m = _model(kind, "nse", n, force=(0, d - 1, 2e-3, 1, 0.3))
+    f = I.random_populations(n, lat.Q, seed=5)
+    m.set_populations(f)
+    ft = m.collide()
+    F = m.force_field()
+    assert np.allclose(ft.sum(0), f.sum(0), rtol=1e-14, atol=0)
+    for a in range(d):
+        before = np.tensordot(lat.cvel[:, a], f, axes=(0, 0))
+        after = np.tensordot(lat.cvel[:, a], ft, axes=(0, 0))
+        assert np.allclose(after - before, F[a], rtol=0, atol=1e-14)
+    _, m2 = _model(kind, "ncde", n)
+    m2.set_populations(f)
+    m2.phi_prev = f.sum(0) * 0.99
+    assert np.allclose(m2.collide().sum(0), f.sum(0), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("kind", ["rD2Q25", "rD2Q13", "rD3Q53", "rD3Q33"])
+def test_collision_matrix_block_form(kind):
+    """Eq. (H-MRT-LB-1): with block-diagonal S, Lambda = s0 I + W sum_k H_k^T (H_k W H_k^T)^{-1}
+    (S_k - s0 I) H_k; here s0 is the shared rate of the rows of order >= 4."""
+    lat, m = _model(kind, "nse", (4,) * lattice(kind).d)
+    sh = m.s_high
+    want = sh * np.eye(lat.Q)
+    for k in range(4):
+        rows = lat.block(k)
+        Hk = lat.H[rows]
+        G = Hk @ np.diag(lat.w) @ Hk.T
+        want = want + np.diag(lat.w) @ Hk.T @ np.linalg.inv(G) @ np.diag(m.s[rows] - sh) @ Hk
+    assert np.abs(m.Lam - want).max() < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["rD2Q25", "rD3Q53"])
+def test_collision_special_rates(kind):
+    """S = I gives Lambda = I and f~ = f^eq; equal rates s give the BGK collision
+    f~ = f - s (f - f^eq) (no source)."""
+    lat = lattice(kind)
+    n = (4,) * lat.d
+    f = I.random_populations(n, lat.Q, seed=11)
+    m = M.Model(lat, "nse", n, np.ones(lat.R), 1.0)
+    m.set_populations(f)
+    rho, u = m.fields()
+    assert np.allclose(m.collide(), m.equilibrium(rho, u), rtol=0, atol=1e-14)
+    s = 1.37
+    m = M.Model(lat, "nse", n, np.full(lat.R, s), s)
+    m.set_populations(f)
+    rho, u = m.fields()
+    assert np.allclose(m.collide(), f - s * (f - m.equilibrium(rho, u)), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("kind", ["rD2Q25", "rD3Q53"])
+def test_streaming_moves_each_population_by_its_velocity(kind):
+    """Eq. (2-2b) on a periodic grid: a unit value of population j at x lands at x + e_j
+    (wrapping), and streaming then streaming back (velocities negated) is the identity."""
+    lat = lattice(kind)
+    d = lat.d
+    n = (7, 5) if d == 2 else (6, 5, 4)
+    m = M.Model(lat, "nse", n, np.ones(lat.R))
+    x0 = (1,) * d
+    f = np.zeros((lat.Q,) + m.shape)
+    f[(slice(None),) + tuple(reversed(x0))] = 1.0
+    m.set_populations(f)
+    m.stream_only(1)
+    for j in range(lat.Q):
+        xj = tuple((x0[a] + lat.e[j, a]) % n[a] for a in range(d))
+        assert m.f[(j,) + tuple(reversed(xj))] == 1.0
+        assert m.f[j].sum() == 1.0
+    g = I.random_populations(n, lat.Q, seed=2)
+    m.set_populations(g)
+    m.stream_only(3)
+    back = np.stack([np.roll(m.f[j], tuple(-3 * int(lat.e[j, a]) for a in range(d)),
+                             axis=tuple(M.axis_of(a, d, 0) for a in range(d))) for j in range(lat.Q)])
+    assert np.array_equal(back, g)
+
+
+def _kinetic_energy(m):
+    rho, u = m.fields()
+    return 0.5 * np.sum(rho * (u ** 2).sum(0))
+
+
+def test_taylor_green_2d_decay_rd2q25():
+    """Config: rD2Q25, 64 x 48 cells, dy/dx = 4/3, u0 = 0.05 c_s, Re = 100, FP64, 200 steps.
+    The kinetic energy follows exp(-2 nu k^2 t) with nu = cs2 (1/s_nu - 1/2) (Eq. (4-29),
+    compressible, k = 0): within 1% at step 200, and the decay rate over steps 100-200 within 3%."""
+    c, cs2, fw = LATS["rD2Q25"]
+    n = (64, 48)
+    lat = L.build("rD2Q25", c, cs2, fw)
+    u0 = 0.05 * math.sqrt(cs2[0])
+    nu = u0 * (n[0] * c[0] / (2 * math.pi)) / 100.0
+    s = np.ones(lat.R)
+    s[3:6] = 1.0 / (nu / cs2[0] + 0.5)
+    m = M.Model(lat, "nse", n, s, 1.0)
+    rho, u = I.taylor_green_2d(n, c, u0, 1.0, cs2[0])
+    m.init_fields(rho, u)
+    k2 = 2 * (2 * math.pi / (n[0] * c[0])) ** 2
+    e0 = _kinetic_energy(m)
+    m.step(100)
+    e100 = _kinetic_energy(m)
+    m.step(100)
+    e200 = _kinetic_energy(m)
+    assert abs(e200 / e0 / math.exp(-2 * nu * k2 * 200) - 1) < 1e-2
+    rate = math.log(e100 / e200) / 100.0
+    assert abs(rate / (2 * nu * k2) - 1) < 3e-2
+    assert abs(m.conserved_sums()[0] - rho.sum()) < 1e-9
+
+
+def _kolmogorov_error(ny, nu=0.2, steps_factor=12.0):
+    c, cs2, fw = LATS["rD2Q13"]
+    n = (4, ny)
+    lat = L.build("rD2Q13", c, cs2, fw)
+    s = np.ones(lat.R)
+    s[3:6] = 1.0 / (nu / cs2[0] + 0.5)
+    ly = n[1] * c[1]
+    k = 2 * math.pi / ly
+    A = 1e-6
+    m = M.Model(lat, "nse", n, s, 1.0, force=(0, 1, A, 1))
+    rho, u = I.rest_state(n, 2)
+    m.init_fields(rho, u)
+    m.step(int(steps_factor / (nu * k * k)))
+    _, uu = m.fields()
+    y = I.coords(n, c)[1]
+    ana = A / (nu * k * k) * np.sin(k * y)
+    return np.linalg.norm(uu[0] - ana) / np.linalg.norm(ana)
+
+
+def test_kolmogorov_steady_state_second_order():
+    """Forced shear flow F = A sin(2 pi y / L_y) e_x: the steady profile approaches
+    u_x = A L_y^2 / (4 pi^2 rho nu) sin(2 pi y / L_y) at second order in the grid spacing."""
+    e1 = _kolmogorov_error(24)
+    e2 = _kolmogorov_error(48)
+    assert e1 < 2e-2
+    assert 3.5 < e1 / e2 < 4.5
+
+
+def _accelerated_stress(s2, drop_m2g=False):
+    c, cs2, fw = LATS["rD2Q25"]
+    lat = L.build("rD2Q25", c, cs2, fw)
+    s = np.ones(lat.R)
+    s[3:6] = s2
+    A = 1e-3
+    n = (3, 3)
+    m = M.Model(lat, "nse", n, s, 1.0, force=(0, 1, A, 0, math.pi / 2))   # uniform F = A e_x
+    if drop_m2g:      # planted mistake: the auxiliary moment M2G left out
+        orig = m.source_moments
+        m.source_moments = lambda fields: (orig(fields)[0], 0.0 * orig(fields)[1])
+    rho, u = I.rest_state(n, 2)
+    u[0] += 0.05
+    m.init_fields(rho, u)
+    m.step(60)
+    r, uu = m.fields()
+    mxx = np.tensordot(lat.H[3], m.f, axes=(0, 0))
+    neq = mxx - (r * uu[0] ** 2 + r * (m.cs2_eq - lat.cs2[0]))
+    return float(neq.mean()), float(-(uu[0] * A).mean())
+
+
+@pytest.mark.parametrize("s2", [0.8, 1.2, 1.8])
+def test_m2g_gives_rate_independent_stress(s2):
+    """Eq. (M-NSEs-4) with M2G = (I - S2/2)(uF + Fu): under uniform acceleration the second
+    non-equilibrium moment is -dt (uF + Fu)/2 whatever S2 is (xx component: -u_x F_x)."""
+    got, want = _accelerated_stress(s2)
+    assert abs(got / want - 1) < 1e-6      # start-up transient decays as (1 - s2)^n
+
+
+def test_m2g_pin_catches_dropped_term():
+    got, want = _accelerated_stress(0.8, drop_m2g=True)
+    assert abs(got / want - 1) > 0.5
+
+
+def _ncde_diffusivity(drop_m1g=False, K=0.02, ux=0.1):
+    c, cs2, _ = LATS["rD2Q13"]
+    lat = L.build("rD2Q13", c, cs2)
+    s = np.ones(lat.R)
+    s[1:3] = 1.0 / (K / cs2[0] + 0.5)
+    n = (96, 40)
+    m = M.Model(lat, "ncde", n, s, 1.0, u_const=np.array([ux, 0.0]), nonlin=0.0)
+    if drop_m1g:      # planted mistake: the auxiliary moment M1G left out
+        m.source_moments = lambda fields: (np.zeros((lat.R, int(np.prod(m.shape)))),) * 2
+    m.init_fields(I.gaussian_hill(n, c, 5.0, 1.0, center=(30.0, 25.0)))
+    x = I.coords(n, c)[0]
+    var = []
+    for steps in (100, 200):
+        m.step(steps)
+        phi, _ = m.fields()
+        xm = (phi * x).sum() / phi.sum()
+        var.append(((x - xm) ** 2 * phi).sum() / phi.sum())
+    return (var[1] - var[0]) / (2 * 200)
+
+
+def test_ncde_diffusivity_with_m1g():
+    """App. A, Eq. (ME-NCDE-3): with M1G = (I - S1/2) d_t(u phi) the hill spreads along the
+    advection with exactly K = dt cs2 (1/s1 - 1/2) (linear NCDE, u = (0.1, 0))."""
+    assert abs(_ncde_diffusivity() / 0.02 - 1) < 1e-4
+
+
+def test_m1g_pin_catches_dropped_term():
+    """Without M1G the moment equation keeps -dt (1/s1 - 1/2) u u : grad grad phi."""
+    got = _ncde_diffusivity(drop_m1g=True)
+    s1 = 1.0 / (0.02 / 0.8 + 0.5)
+    assert abs(got - (0.02 - (1 / s1 - 0.5) * 0.1 ** 2)) < 2e-6
+
+
+def _hill_error(r):
+    c, cs2, _ = LATS["rD2Q13"]
+    lat = L.build("rD2Q13", c, cs2)
+    K = 0.05
+    s = np.ones(lat.R)
+    s[1:3] = 1.0 / (K / cs2[0] + 0.5)
+    n = (64 * r, 52 * r)
+    u = np.array([0.15, 0.1]) / r
+    sig, steps = 6.0 * r, 150 * r * r
+    m = M.Model(lat, "ncde", n, s, 1.0, u_const=u, nonlin=0.0)
+    m.init_fields(I.gaussian_hill(n, c, sig, 1.0))
+    m.step(steps)
+    phi, _ = m.fields()
+    xs = I.coords(n, c)
+    lx, ly = n[0] * c[0], n[1] * c[1]
+    s2 = sig ** 2 + 2 * K * steps
+    x0 = [0.5 * lx + u[0] * steps, 0.5 * ly + u[1] * steps]
+    ana = np.zeros_like(phi)
+    for ix, iy in itertools.product((-1, 0, 1), repeat=2):
+        ana += sig ** 2 / s2 * np.exp(-((xs[0] - x0[0] + ix * lx) ** 2 + (xs[1] - x0[1] + iy * ly) ** 2) / (2 * s2))
+    return np.linalg.norm(phi - ana) / np.linalg.norm(ana)
+
+
+def test_gaussian_hill_linear_ncde_second_order():
+    """Linear NCDE (D(phi) = phi): the advected, diffusing Gaussian with its periodic images,
+    relative L2 error below 1e-2 and second-order convergence under diffusive refinement."""
+    e1, e2 = _hill_error(1), _hill_error(2)
+    assert e1 < 1e-2
+    assert 3.5 < e1 / e2 < 4.5
+
+
+def test_ncde_nonlinear_conserves_phi():
+    """With S = 0 and periodic boundaries sum_x phi is constant (nonlinear diffusion on)."""
+    c, cs2, _ = LATS["rD2Q13"]
+    lat = L.build("rD2Q13", c, cs2)
+    n = (40, 32)
+    s = np.ones(lat.R)
+    s[1:3] = 1.6
+    m = M.Model(lat, "ncde", n, s, 1.0, u_const=np.array([0.02, 0.01]), nonlin=1.0)
+    m.init_fields(I.gaussian_hill(n, c, 6.0, 1.0, noise=1e-3, seed=0))
+    total = m.fields()[0].sum()
+    m.step(50)
+    assert abs(m.fields()[0].sum() / total - 1) < 1e-13
+
+
+def _tgv3d_rate_error(nx):
+    c, cs2, fw = LATS["rD3Q53"]
+    n = (nx, nx, 3 * nx // 4)
+    lat = L.build("rD3Q53", c, cs2, fw)
+    nu = 0.1
+    s = np.ones(lat.R)
+    s[4:10] = 1.0 / (nu / cs2[0] + 0.5)
+    m = M.Model(lat, "nse", n, s, 1.0)
+    rho, u = I.taylor_green_3d(n, c, 0.01, 1.0, cs2[0])
+    m.init_fields(rho, u)
+    k2 = 3 * (2 * math.pi / nx) ** 2
+    m.step(20)
+    e20 = _kinetic_energy(m)
+    m.step(30)
+    e50 = _kinetic_energy(m)
+    return math.log(e20 / e50) / 30.0 / (2 * nu * k2) - 1
+
+
+def test_taylor_green_3d_decay_rd3q53():
+    """rD3Q53 on a rectangular 3D grid (dz/dx = 4/3, the negative weights of the shared-c_s
+    setting): at low Mach and Reynolds number the kinetic energy decays at 2 nu |k|^2 with
+    |k|^2 = 3 k^2 and nu = cs2 (1/s_nu - 1/2), converging at second order (16 and 32 cells per
+    wavelength). The window starts after the start-up transient, which decays like (1 - s_nu)^n."""
+    e16 = _tgv3d_rate_error(16)
+    e32 = _tgv3d_rate_error(32)
+    assert abs(e16) < 5e-2
+    assert 3.5 < e16 / e32 < 4.5
