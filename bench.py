@@ -1,0 +1,343 @@
+"""Benchmark: rD3Q53 MRT-LB collide-stream throughput on one GB300 (or N replicas).
+
+Workload: the rD3Q53 compressible isothermal Taylor-Green vortex on 256 x 256 x 192 cells
+(dz/dx = 4/3), Ma = 0.3, Re = 1600, FP32 populations and arithmetic. One benchmark step is one
+lattice-Boltzmann time step of the whole grid: one launch of the fused pull-gather / collide /
+store kernel (streaming, fields, equilibrium, sources, collision). The two population arrays
+(2 x 2.67 GB) are far larger than the 129 MB L2, so no flush is needed between steps.
+
+Printed (rank 0, one JSON line): MLUPS over all ranks, the roofline of the collide-stream kernel
+against the measured HBM copy bandwidth (algorithmic bytes 2 Q 4 B per cell update), SM clocks
+sampled during the timed region, an end-to-end number through the C ABI with pinned host
+buffers, and the FP64 oracle timed on the host cores on a bounded sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rD3Q53 MLUPS"
+UNIT = "MLUPS"
+GRID = (256, 256, 192)
+Q = 53
+STORE_BYTES = 4
+PROFILE = os.path.join(ROOT, "profiles", "k_step_rd3q53_f32_tgv3d_256x256x192.md")
+CPU_SAMPLE_GRID = (256, 256, 8)
+CPU_SAMPLE_STEPS = 2
+
+
+def _workload(grid=GRID):
+    from paper_2512_16230_gb300 import workloads as W
+    return W.taylor_green_3d(n=tuple(grid), steps=1000, store="f32")
+
+
+def _config(extra=None, grid=GRID):
+    cfg = {
+        "workload": f"rD3Q53 Taylor-Green 3D, {grid[0]}x{grid[1]}x{grid[2]} cells (dz/dx=4/3), Ma 0.3, Re 1600, FP32",
+        "lattice": "rD3Q53", "cells": int(math.prod(grid)), "grid": list(grid), "Q": Q,
+        "store": "f32", "compute": "f32",
+        "l2": "inputs larger than L2 (2 x 2.67 GB population arrays vs 129 MB L2), no flush",
+        "parallelism": "replicas",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def _source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2512_16230_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(cells):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None, None
+    m = re.search(r"dram_bytes_per_cell_update:\s*([0-9.eE+-]+)", text)
+    s = re.search(r"source_sha:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != _source_sha():
+        return None, s.group(1) if s else None
+    return float(m.group(1)) * cells, s.group(1)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+        return False
+
+    def summary(self, busy_fraction=0.5):
+        rows = []
+        for rec in csv.reader(io.StringIO(self.out)):
+            rec = [r.strip() for r in rec]
+            if len(rec) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(rec[1]), smax=float(rec[2]), power=float(rec[3]), hw=rec[5], hwt=rec[6],
+                                 swt=rec[7], swp=rec[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        load = [r for r in rows if r["power"] >= busy_fraction * max(x["power"] for x in rows)] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(load),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_worker(nx, ny, nz, steps):
+    """Time the FP64 oracle, as it stands, on a slab of the benchmark grid (run in a fresh
+    process; prints one JSON object)."""
+    import numpy as np  # noqa: F401
+    from oracle import lattice as OL
+    from oracle import mrt as OM
+    from paper_2512_16230_gb300 import workloads as W
+    wl = W.taylor_green_3d(n=GRID, steps=1)
+    spec = wl.lattice
+    lat = OL.build(spec.kind, spec.c, spec.cs2, spec.free_w)
+    n = (nx, ny, nz)
+    m = OM.Model(lat, "nse", n, wl.s, wl.s_high)
+    from paper_2512_16230_gb300 import inputs as I
+    rho, u = I.taylor_green_3d(n, spec.c, wl.init["u0"], 1.0, spec.cs2[0])
+    m.init_fields(rho, u)
+    t0 = time.perf_counter()
+    m.step(steps)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"mlups": nx * ny * nz * steps / dt / 1e6, "seconds": dt}))
+
+
+def run_cpu_baseline(threads=None):
+    threads = threads or os.cpu_count() or 1
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = str(threads)
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"bench.cpu_baseline_worker({CPU_SAMPLE_GRID[0]}, {CPU_SAMPLE_GRID[1]}, {CPU_SAMPLE_GRID[2]}, "
+            f"{CPU_SAMPLE_STEPS})")
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if res.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": threads, "kind": "oracle", "error": res.stderr[-500:]}
+    out = json.loads(res.stdout.strip().splitlines()[-1])
+    return {"value": out["mlups"], "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"FP64 numpy oracle, {CPU_SAMPLE_STEPS} steps of the same rD3Q53 Taylor-Green workload on a "
+                       f"{CPU_SAMPLE_GRID[0]}x{CPU_SAMPLE_GRID[1]}x{CPU_SAMPLE_GRID[2]} periodic slab of the benchmark "
+                       f"grid ({out['seconds']:.1f} s; BLAS threads = cores)")}
+
+
+def bench_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    base = run_cpu_baseline()
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic Taylor-Green initial field)",
+            "config": _config({"reference": "FP64 numpy oracle on the host cores (the paper has no code)"}),
+            "cpu_baseline": base, "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2512_16230_gb300 import build as B
+    from paper_2512_16230_gb300 import lbm
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    lbm.load()
+    grid = tuple(args.grid)
+    wl = _workload(grid)
+    spec = wl.lattice
+    cells = wl.ncells
+    lat = lbm.Lattice(spec.kind, spec.c, spec.cs2, spec.free_w)
+    stream = torch.cuda.current_stream(dev)
+    model = lbm.Model(lat, "nse", wl.n, store="f32", stream=stream.cuda_stream)
+    model.set_relaxation(wl.s, wl.s_high)
+    rho, u = wl.fields()
+    rho_d = torch.from_numpy(rho).to(dev)
+    u_d = torch.from_numpy(np.ascontiguousarray(u)).to(dev)
+    model.init_fields(rho_d, u_d)
+    model.step(args.warmup)
+    model.synchronize()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = str(local)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(uuid) as clocks:
+        barrier()
+        _, launches0 = model.counters()
+        start.record(stream)
+        model.step(args.steps)
+        end.record(stream)
+        barrier()
+    _, launches1 = model.counters()
+    ms = start.elapsed_time(end)
+    sums = model.conserved_sums()
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = cells * args.steps * ws / (ms_max / 1e3) / 1e6
+    launch_ms = ms / args.steps
+
+    # end to end through the public API: pinned host fields in, K steps, pinned host fields out
+    rho_h = torch.from_numpy(rho).pin_memory()
+    u_h = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
+    rho_o = torch.empty_like(rho_h).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    model.init_fields(rho_h.numpy(), u_h.numpy())
+    model.step(args.steps)
+    model.read_fields(rho_o.numpy(), u_o.numpy())
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = cells * args.steps * ws / float(e2e_t.item()) / 1e6
+    io_bytes = (rho_h.numel() + u_h.numel()) * 8
+
+    if rank == 0:
+        peak, peak_src = _peaks()
+        algo_bytes = 2 * Q * STORE_BYTES * cells
+        achieved = algo_bytes / (launch_ms / 1e3) / 1e9
+        traffic, sha = _profile_traffic(cells)
+        cpu = run_cpu_baseline() if (ws == 1 and not args.no_cpu_baseline) else None
+        if grid != GRID:
+            traffic = None
+        csum = clocks.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (analytic Taylor-Green initial field)", "config": _config(grid=grid),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                         "kernel": "k_step<rD3Q53, f32, NSE> (fused pull-gather, collide, store)",
+                         "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": launch_ms},
+            "clocks": {k: csum[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes / args.steps,
+                    "d2h_bytes_per_step": io_bytes / args.steps,
+                    "definition": "one solve through the C ABI: pinned host fields in, K steps, pinned host fields out"},
+            "gpu_launches": int(launches1 - launches0),
+            "mass_sum": float(sums[0]),
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    model.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, nargs=3, default=list(GRID),
+                    help="grid for a smaller profiling case (the benchmark workload is 256 256 192)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * lbm_mrt.h -- C ABI of the GB300 (sm_103a) MRT lattice Boltzmann library.
+ *
+ * The library implements the rectangular multiple-relaxation-time lattice Boltzmann method of
+ * Shi, Yuan & Chai, "A unified MRT-LB framework for Navier-Stokes and nonlinear
+ * convection-diffusion equations and beyond" (arXiv 2512.16230): the two-level full-correction
+ * scheme Eq. (2-3) with the Hermite-moment collision Eq. (H-MRT-LB-1) on the multispeed
+ * rectangular lattices of Sec. 5 and App. C/D (rD2Q25/21/17/13, rD3Q53/45/33).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Lattice units: dt = 1, dx_1 = 1, c_a = dx_a / dx_1 (Sec. 5, "c_alpha = dx_alpha / dt").
+ *  - A grid has n[0] x n[1] (x n[2]) cells, periodic in every direction. Every field is a
+ *    dense C-order array with x fastest: element (x, y, z) sits at ((z * n[1]) + y) * n[0] + x.
+ *    Vector fields are structure-of-arrays: u[a * ncells + cell]. Populations are
+ *    f[i * ncells + cell] with i in the paper's velocity order.
+ *  - Host/device: arguments named *_host live in host memory; arguments accompanied by an
+ *    `on_device` flag live in device memory of the model's GPU when the flag is non-zero and in
+ *    host memory otherwise. Field and population I/O is always FP64.
+ *  - Ownership: the caller owns every buffer it passes. The library owns the handles and, unless
+ *    the caller supplies a workspace, the device memory of a model. Nothing is retained past the
+ *    call except handles and workspaces.
+ *  - Streams: a model runs all its kernels on the CUDA stream given at creation (NULL = the
+ *    legacy default stream). lbm_model_step and lbm_model_stream_only are asynchronous; the
+ *    calls that return data to host memory synchronize the stream first.
+ *  - Errors: every call returns an lbm_status and never throws; on failure lbm_last_error()
+ *    returns a thread-local message. A failed call leaves the model as it was before the call
+ *    except where stated. No call faults the GPU on bad arguments: sizes and pointers are
+ *    validated on the host first.
+ *  - FP64 runs only in the lattice set-up (lbm_lattice_create) and in the conservation sums;
+ *    the time step computes in the model's compute dtype.
+ */
+#ifndef LBM_MRT_H
+#define LBM_MRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+typedef struct lbm_lattice lbm_lattice; /* opaque, library-owned */
+typedef struct lbm_model lbm_model;     /* opaque, library-owned */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,                /* invalid argument (null pointer, size, axis, dtype mix) */
+  LBM_ERR_LATTICE_INFEASIBLE = 2, /* a Hermite norm N_r <= 0 or HWH^T not diagonal */
+  LBM_ERR_OOM = 3,                /* device allocation failed or workspace too small */
+  LBM_ERR_CUDA = 4,               /* a CUDA runtime call failed (message has the CUDA error) */
+  LBM_ERR_NONFINITE = 5,          /* a conservation sum is NaN or infinite */
+  LBM_ERR_NOT_IMPLEMENTED = 6
+} lbm_status;
+
+/* Lattices of Sec. 5 and App. D, velocity columns in the paper's printed order. */
+typedef enum {
+  LBM_RD2Q13 = 0, /* Eq. (Q13lattice)                                    */
+  LBM_RD2Q17 = 1, /* Eq. (3-1) with w21 = w17 = w18 = 0 (Sec. 5 (ii))    */
+  LBM_RD2Q21 = 2, /* Eq. (3-1) with w21 = 0 (Sec. 5 (i))                 */
+  LBM_RD2Q25 = 3, /* Eq. (3-1)                                           */
+  LBM_RD3Q33 = 4, /* App. D, rD3Q33                                      */
+  LBM_RD3Q45 = 5, /* App. D, rD3Q53 with w45 = 0 (the eight (+-2)^3 vectors dropped) */
+  LBM_RD3Q53 = 6  /* App. D, rD3Q53                                      */
+} lbm_kind;
+
+typedef enum {
+  LBM_F64 = 0,     /* IEEE binary64 */
+  LBM_F32 = 1,     /* IEEE binary32 */
+  LBM_BF16_DEV = 2, /* storage only: bfloat16 deviation f_i - w_i * rho_ref */
+  LBM_F16_DEV = 3  /* storage only: binary16 deviation f_i - w_i * rho_ref */
+} lbm_dtype;
+
+typedef enum {
+  LBM_NSE = 0, /* isothermal Navier-Stokes, Sec. 3 with the multispeed choices of Sec. 3.4 */
+  LBM_NCDE = 1 /* nonlinear convection-diffusion, App. A */
+} lbm_eq;
+
+int lbm_abi_version(void);
+
+/* Thread-local description of the last error returned on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Lattices
+ * ------------------------------------------------------------------------------------------ */
+
+/* Build lattice `kind` on the current CUDA device, in FP64, on the GPU:
+ *   - weights from the printed closed forms: Eq. (WeightQ25) (rD2Q25 and its sub-lattices),
+ *     Eq. (Q13lattice), the rD3Q53 and rD3Q33 weight lists of App. D, with
+ *     d_0a = cs2[a] / c[a]^2 (the definition stated with Eq. (new11));
+ *   - Hermite rows H0..H3 (Sec. 5) by weighted Gram-Schmidt of the monomials in the paper's row
+ *     order, which yields the rectangular-cell correction of the third-order rows of
+ *     Eq. (CorrectQ25) and App. D;
+ *   - norms N_r = sum_i w_i H_ri^2 and a check that H W H^T is diagonal.
+ * c[d]      axis speeds c_a = dx_a / dx_1 (c[0] = 1 in lattice units), host memory.
+ * cs2[d]    squared sound speed per axis c_sa^2 (Remark 2; equal values = isotropic), host.
+ * free_w    the free weights, host memory (may be NULL when n_free == 0), in this order:
+ *             rD2Q25: w13, w17, w18, w21     rD2Q21: w13, w17, w18     rD2Q17: w13
+ *             rD3Q53: w45                    rD2Q13, rD3Q45, rD3Q33: none
+ * Negative weights are allowed (reported by lbm_lattice_query). Synchronous.
+ * Errors: LBM_ERR_ARG (bad kind, n_free, c <= 0, cs2 <= 0), LBM_ERR_LATTICE_INFEASIBLE,
+ *         LBM_ERR_CUDA. On success *out receives a new handle. */
+lbm_status lbm_lattice_create(lbm_kind kind, const double* c, const double* cs2,
+                              const double* free_w, int n_free, lbm_lattice** out);
+
+/* Copy the lattice tables to host memory. Every output pointer may be NULL.
+ *   d, Q, R : dimension, number of velocities, number of Hermite rows of order <= 3
+ *   e[Q*d]  : integer velocity components (c_i = diag(c) e_i)
+ *   w[Q]    : weights;  H[R*Q]: Hermite rows on the lattice (row-major);  N[R]: norms
+ *   T[R*R]  : H_r(c) = sum_k T[r*R + k] * mono_k(c), mono_k the monomials in the paper's row
+ *             order (2D: 1,x,y,xx,xy,yy,xyy,xxy,xxx,yyy; 3D: App. D, M1..M20). */
+lbm_status lbm_lattice_query(const lbm_lattice* lat, int* d, int* Q, int* R, int8_t* e,
+                             double* w, double* H, double* N, double* T);
+
+lbm_status lbm_lattice_destroy(lbm_lattice* lat);
+
+/* ------------------------------------------------------------------------------------------
+ * Models: one periodic solve on one lattice
+ * ------------------------------------------------------------------------------------------ */
+
+/* Device bytes a model needs: two population buffers (Q * ncells * sizeof(store)), the NCDE
+ * previous-step field, the body-force profile and the reduction scratch, each 256-byte aligned. */
+lbm_status lbm_model_workspace_bytes(const lbm_lattice* lat, lbm_eq eq, const int64_t* n,
+                                     lbm_dtype store, size_t* bytes);
+
+/* Create a model on grid n[d] (host memory). Every n[a] must be at least the largest velocity
+ * component of the lattice (2 or 3) and the cell count below 2^31.
+ * store/compute: (F64, F64), (F32, F32), (BF16_DEV or F16_DEV, F32).
+ * stream    : cudaStream_t on which every kernel of the model runs (NULL: legacy default).
+ * workspace : device buffer of at least lbm_model_workspace_bytes(), 256-byte aligned, owned by
+ *             the caller and kept alive until lbm_model_destroy; NULL lets the library allocate.
+ * Defaults: every rate 1 (s_r = s_high = 1), cs2_eq = cs2[0], no body force, u_const = 0,
+ * nonlin = 0, populations zero. The model keeps a reference to `lat`, which must outlive it. */
+lbm_status lbm_model_create(const lbm_lattice* lat, lbm_eq eq, const int64_t* n, lbm_dtype store,
+                            lbm_dtype compute, void* stream, void* workspace,
+                            size_t workspace_bytes, lbm_model** out);
+
+/* Diagonal relaxation matrix S in the Hermite basis (Sec. 4, Eq. (H-MRT-LB-1)):
+ * s[R] the rate of each Hermite row in the paper's order, s_high the one rate shared by every
+ * row of order >= 4. Rates must lie in (0, 2]. The kinematic viscosity of the NSE is
+ * nu = cs2_eq (1/s_2 - 1/2) (Eq. (4-29), compressible, k = 0); the NCDE diffusivity is
+ * K = cs2_eq (1/s_1 - 1/2) (Eq. (ME-NCDE-3)). */
+lbm_status lbm_model_set_relaxation(lbm_model* m, const double* s, double s_high);
+
+/* Equation of state p = rho * cs2_eq (NSE, Eq. (M-NSEs-6-1)) or the prefactor of the diffusion
+ * moment M2 = cs2_eq D(phi) I (NCDE, Eq. (M-NCDE-6)). */
+lbm_status lbm_model_set_eos(lbm_model* m, double cs2_eq);
+
+/* NSE body force F(x) = A sin(2 pi k x_b / L_b + phase) e_a, with x_b = i_b c_b the cell
+ * coordinate along axis b and L_b = n_b c_b. It enters through M1F = F and the auxiliary moment
+ * M2G = (I - S2/2)(uF + Fu) (Eq. (M-NSEs-2), Eq. (M2Ga-1) with S = 0) and the half-force
+ * velocity correction of Eq. (2-4-2). A = 0 removes the force. */
+lbm_status lbm_model_set_force(lbm_model* m, int axis_a, int axis_b, double A, int k,
+                               double phase);
+
+/* NCDE (App. A): constant convection velocity u_const[d] (host) and the nonlinearity of
+ * D(phi) = phi + nonlin * phi^3 / 3, i.e. grad D = (1 + nonlin phi^2) grad phi. The auxiliary
+ * moment is M1G = (I - S1/2) u (phi^n - phi^{n-1}) (Eq. (M-NCDE-6), M20 = 0). */
+lbm_status lbm_model_set_ncde(lbm_model* m, const double* u_const, double nonlin);
+
+/* f-bar(t = 0) = f^eq of the given fields (Eq. (feq-1)); for the NCDE phi^{-1} = phi^0.
+ * rho_or_phi[ncells], u[d*ncells] (NSE only; ignored and may be NULL for the NCDE). Resets
+ * the step counter. Asynchronous when on_device != 0. */
+lbm_status lbm_model_init_fields(lbm_model* m, const double* rho_or_phi, const double* u,
+                                 int on_device);
+
+/* Set / get the populations f-bar_j(x, t_n) of Eq. (2-3) (pre-collision, after streaming),
+ * f[Q*ncells] in FP64. set: for the NCDE phi^{n-1} is set to sum_j f-bar_j. get synchronizes
+ * the model's stream when the destination is host memory. */
+lbm_status lbm_model_set_populations(lbm_model* m, const double* f, int on_device);
+lbm_status lbm_model_get_populations(lbm_model* m, double* f, int on_device);
+
+/* Advance nsteps time steps: per step one fused kernel computes the pull-streaming gather
+ * (Eq. (2-2b)), the fields of Eq. (2-4-2) / (2-4-1), the collision of Eq. (2-3) in the Hermite
+ * basis with the equilibrium of Eq. (feq-1) and the source moments, and the store.
+ * Asynchronous on the model's stream. */
+lbm_status lbm_model_step(lbm_model* m, int64_t nsteps);
+
+/* Propagation only (Eq. (2-2b)), no collision: a bit-exact data-movement test mode. */
+lbm_status lbm_model_stream_only(lbm_model* m, int64_t nsteps);
+
+/* Macroscopic fields at the current time (Eq. (2-4-2): rho = sum f, u = (sum c f + F/2)/rho;
+ * Eq. (2-4-1): phi = sum f) into rho_or_phi[ncells] and u[d*ncells] (u may be NULL; ignored
+ * for the NCDE). Synchronizes the stream when the destination is host memory. */
+lbm_status lbm_model_read_fields(lbm_model* m, double* rho_or_phi, double* u, int on_device);
+
+/* Global sums over the grid in FP64: out_host[0] = sum_x sum_j f_j,
+ * out_host[1 + a] = sum_x sum_j c_ja f_j (a < d). Deterministic (fixed reduction order).
+ * Synchronous. Returns LBM_ERR_NONFINITE (with the sums still written) if any is NaN/inf. */
+lbm_status lbm_model_conserved_sums(lbm_model* m, double* out_host);
+
+/* Completed time steps since the last init/set; kernels launched by this model so far. */
+lbm_status lbm_model_counters(const lbm_model* m, int64_t* steps, int64_t* launches);
+
+/* Wait for the model's stream. */
+lbm_status lbm_model_synchronize(lbm_model* m);
+
+lbm_status lbm_model_destroy(lbm_model* m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_MRT_H */

@@ -1,0 +1,149 @@
+// Compile-time descriptions of the multispeed rectangular lattices (Sec. 5, App. C/D of
+// arXiv 2512.16230): integer velocity components e_j in the paper's column order, the
+// monomials of order <= 3 in the paper's Hermite-row order, and small constexpr helpers.
+//
+// Every kernel that walks populations or moments does so with static_for, so the velocity
+// components, monomial values and parity pairs are integer constants folded by the compiler:
+// structurally zero products never generate an instruction.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+#include <utility>
+
+#include "lbm_mrt.h"
+
+namespace lbm {
+
+struct Vel {
+  int x, y, z;
+};
+struct Mono {
+  int a, b, c;  // exponents of c_x, c_y, c_z
+};
+
+// Eq. (3-1): rD2Q25; rD2Q21/17/13 are its first 21/17/13 columns (Sec. 5 (i)-(iii)).
+inline constexpr Vel kQ25[25] = {
+    {0, 0, 0},  {1, 0, 0},  {0, 1, 0},  {-1, 0, 0}, {0, -1, 0}, {1, 1, 0},   {-1, 1, 0},
+    {-1, -1, 0}, {1, -1, 0}, {2, 0, 0},  {0, 2, 0},  {-2, 0, 0}, {0, -2, 0},  {2, 2, 0},
+    {-2, 2, 0}, {-2, -2, 0}, {2, -2, 0}, {3, 0, 0},  {0, 3, 0},  {-3, 0, 0},  {0, -3, 0},
+    {3, 3, 0},  {-3, 3, 0}, {-3, -3, 0}, {3, -3, 0}};
+
+// App. D: rD3Q53 = 27 single-speed vectors then the 26 doubled non-zero ones; rD3Q33 and
+// rD3Q45 are its first 33 and 45 columns.
+inline constexpr Vel kQ27[27] = {
+    {0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},  {0, 0, 1},   {0, 0, -1},
+    {1, 1, 0},   {-1, -1, 0}, {-1, 1, 0},  {1, -1, 0}, {1, 0, 1},   {-1, 0, -1}, {-1, 0, 1},
+    {1, 0, -1},  {0, 1, 1},   {0, -1, -1}, {0, -1, 1}, {0, 1, -1},  {1, 1, 1},   {-1, -1, -1},
+    {1, 1, -1},  {-1, -1, 1}, {1, -1, 1},  {-1, 1, -1}, {-1, 1, 1}, {1, -1, -1}};
+
+constexpr Vel q53(int j) {
+  return j < 27 ? kQ27[j] : Vel{2 * kQ27[j - 26].x, 2 * kQ27[j - 26].y, 2 * kQ27[j - 26].z};
+}
+
+// Hermite rows / monomials in the paper's order. 2D (App. C): 1, x, y, xx, xy, yy, xyy, xxy,
+// xxx, yyy. 3D (App. D, M1..M20): 1, x, y, z, xx, yy, zz, xy, zx, yz, xyy, zzx, xxy, yzz, zxx,
+// yyz, xyz, xxx, yyy, zzz.
+inline constexpr Mono kMono2[10] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {2, 0, 0}, {1, 1, 0},
+                                    {0, 2, 0}, {1, 2, 0}, {2, 1, 0}, {3, 0, 0}, {0, 3, 0}};
+inline constexpr Mono kMono3[20] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                                    {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1},
+                                    {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {0, 1, 2}, {2, 0, 1},
+                                    {0, 2, 1}, {1, 1, 1}, {3, 0, 0}, {0, 3, 0}, {0, 0, 3}};
+
+constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+template <int D>
+constexpr Mono mono(int k) {
+  return D == 2 ? kMono2[k] : kMono3[k];
+}
+constexpr int degree(Mono m) { return m.a + m.b + m.c; }
+constexpr int mono_value(Vel v, Mono m) {
+  return ipow(v.x, m.a) * ipow(v.y, m.b) * ipow(v.z, m.c);
+}
+// Parity class of a monomial: reflections of a symmetric lattice only couple monomials whose
+// exponents have the same parities (Sec. 5: odd lattice moments vanish).
+constexpr int parity_class(Mono m) {
+  return (m.a & 1) | ((m.b & 1) << 1) | ((m.c & 1) << 2);
+}
+
+template <int KIND>
+struct Lat;
+
+template <int Q_>
+struct Lat2D {
+  static constexpr int D = 2, Q = Q_, R = 10;
+  static constexpr int RMAX = Q_ >= 17 ? 3 : 2;
+  static constexpr Vel e(int j) { return kQ25[j]; }
+};
+template <int Q_>
+struct Lat3D {
+  static constexpr int D = 3, Q = Q_, R = 20, RMAX = 2;
+  static constexpr Vel e(int j) { return q53(j); }
+};
+
+template <> struct Lat<LBM_RD2Q13> : Lat2D<13> { static constexpr int KIND = LBM_RD2Q13; };
+template <> struct Lat<LBM_RD2Q17> : Lat2D<17> { static constexpr int KIND = LBM_RD2Q17; };
+template <> struct Lat<LBM_RD2Q21> : Lat2D<21> { static constexpr int KIND = LBM_RD2Q21; };
+template <> struct Lat<LBM_RD2Q25> : Lat2D<25> { static constexpr int KIND = LBM_RD2Q25; };
+template <> struct Lat<LBM_RD3Q33> : Lat3D<33> { static constexpr int KIND = LBM_RD3Q33; };
+template <> struct Lat<LBM_RD3Q45> : Lat3D<45> { static constexpr int KIND = LBM_RD3Q45; };
+template <> struct Lat<LBM_RD3Q53> : Lat3D<53> { static constexpr int KIND = LBM_RD3Q53; };
+
+// Index of the velocity opposite to j (every lattice here is symmetric under e -> -e).
+template <class L>
+constexpr int opposite(int j) {
+  int found = -1;
+  for (int i = 0; i < L::Q; ++i) {
+    const Vel a = L::e(i), b = L::e(j);
+    if (a.x == -b.x && a.y == -b.y && a.z == -b.z) found = i;
+  }
+  return found;
+}
+
+// Largest |component| of the velocity set.
+template <class L>
+constexpr int max_component() {
+  int m = 0;
+  for (int i = 0; i < L::Q; ++i) {
+    const Vel v = L::e(i);
+    m = v.x > m ? v.x : m;
+    m = v.y > m ? v.y : m;
+    m = v.z > m ? v.z : m;
+  }
+  return m;
+}
+
+// static_for<N>(f) calls f(std::integral_constant<int, 0>) ... f(integral_constant<int, N-1>).
+// Inside nested lambdas, read a captured index as decltype(i)::value (a constant expression
+// whatever the capture); the constexpr helpers above are evaluated at compile time only.
+template <class F, int... I>
+__host__ __device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__host__ __device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// Host-side view of a lattice's velocity table (for generic, non-hot kernels and set-up).
+inline int lattice_dims(int kind) { return kind <= LBM_RD2Q25 ? 2 : 3; }
+inline int lattice_q(int kind) {
+  switch (kind) {
+    case LBM_RD2Q13: return 13;
+    case LBM_RD2Q17: return 17;
+    case LBM_RD2Q21: return 21;
+    case LBM_RD2Q25: return 25;
+    case LBM_RD3Q33: return 33;
+    case LBM_RD3Q45: return 45;
+    case LBM_RD3Q53: return 53;
+  }
+  return 0;
+}
+inline Vel lattice_e(int kind, int j) { return lattice_dims(kind) == 2 ? kQ25[j] : q53(j); }
+inline int lattice_rmax(int kind) { return (kind == LBM_RD2Q17 || kind == LBM_RD2Q21 || kind == LBM_RD2Q25) ? 3 : 2; }
+
+constexpr int kMaxQ = 53;
+constexpr int kMaxR = 20;
+
+}  // namespace lbm

@@ -1,0 +1,522 @@
+// The extern "C" entry points of include/lbm_mrt.h: argument validation, device memory layout,
+// parameter marshalling and dispatch to the kernels. No exception crosses the ABI.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+lbm_status set_error(lbm_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+lbm_status cuda_error(cudaError_t err, const char* what) {
+  return set_error(err == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+                   std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")");
+}
+
+template <class CT>
+void make_step_params(const lbm_model* m, StepParams<CT>* p) {
+  const lbm_lattice* L = m->lat;
+  std::memset(p, 0, sizeof(*p));
+  const int R = L->R;
+  for (int r = 0; r < R; ++r) {
+    for (int k = 0; k < R; ++k) p->T[r][k] = CT(L->T[r * R + k]);
+    const Mono mk = L->d == 2 ? kMono2[r] : kMono3[r];
+    double Dk = 1.0;
+    for (int q = 0; q < mk.a; ++q) Dk *= L->c[0];
+    for (int q = 0; q < mk.b; ++q) Dk *= L->c[1];
+    for (int q = 0; q < mk.c; ++q) Dk *= L->c[2];
+    p->D[r] = CT(Dk);
+    p->invN[r] = CT(1.0 / L->N[r]);
+    p->sd[r] = CT(m->s[r] - m->s_high);
+    p->half[r] = CT(1.0 - 0.5 * m->s[r]);
+  }
+  const bool dev = m->store == LBM_BF16_DEV || m->store == LBM_F16_DEV;
+  for (int i = 0; i < L->Q; ++i) {
+    p->w[i] = CT(L->w[i]);
+    p->wref[i] = dev ? CT(L->w[i] * m->rho_ref) : CT(0);
+  }
+  p->s_high = CT(m->s_high);
+  p->one_minus_sh = CT(1.0 - m->s_high);
+  p->cs2_eq = CT(m->cs2_eq);
+  p->nonlin_third = CT(m->nonlin / 3.0);
+  for (int a = 0; a < 3; ++a) {
+    p->u_const[a] = CT(m->u_const[a]);
+    p->n[a] = a < L->d ? int(m->n[a]) : 1;
+  }
+  p->ncells = m->ncells;
+  const bool force = m->eq == LBM_NSE && m->force_A != 0.0;
+  p->force_a = force ? m->force_a : 0;
+  p->force_b = force ? m->force_b : -1;
+  p->force_tab = static_cast<const CT*>(m->force_tab);
+}
+
+template void make_step_params<float>(const lbm_model*, StepParams<float>*);
+template void make_step_params<double>(const lbm_model*, StepParams<double>*);
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t f_bytes, phi_off, force_off, part_off, sums_off, total;
+};
+
+Layout layout(const lbm_lattice* L, int eq, const int64_t* n, int store) {
+  int64_t ncells = 1, nmax = 1;
+  for (int a = 0; a < L->d; ++a) {
+    ncells *= n[a];
+    nmax = n[a] > nmax ? n[a] : nmax;
+  }
+  const size_t cbytes = store == LBM_F64 ? 8 : 4;
+  Layout lo;
+  lo.f_bytes = align_up(size_t(L->Q) * size_t(ncells) * dtype_bytes(store));
+  lo.phi_off = 2 * lo.f_bytes;
+  const size_t phi_bytes = eq == LBM_NCDE ? align_up(size_t(ncells) * cbytes) : 0;
+  lo.force_off = lo.phi_off + phi_bytes;
+  lo.part_off = lo.force_off + align_up(size_t(nmax) * cbytes);
+  lo.sums_off = lo.part_off + align_up(size_t(kRedBlocks) * 4 * sizeof(double));
+  lo.total = lo.sums_off + align_up(4 * sizeof(double));
+  return lo;
+}
+
+lbm_status check_grid(const lbm_lattice* L, const int64_t* n) {
+  if (!n) return set_error(LBM_ERR_ARG, "grid size pointer is NULL");
+  int64_t ncells = 1;
+  for (int a = 0; a < L->d; ++a) {
+    if (n[a] < L->rmax)
+      return set_error(LBM_ERR_ARG, "every grid extent must be at least " + std::to_string(L->rmax) +
+                                        " (the largest velocity component)");
+    if (n[a] > (int64_t(1) << 30)) return set_error(LBM_ERR_ARG, "grid extent too large");
+    ncells *= n[a];
+    if (ncells >= (int64_t(1) << 31)) return set_error(LBM_ERR_ARG, "cell count must be below 2^31");
+  }
+  return LBM_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+lbm_status upload_force(lbm_model* m) {
+  if (m->eq != LBM_NSE || m->force_A == 0.0) return LBM_OK;
+  const int nb = int(m->n[m->force_b]);
+  const double Lb = double(nb);  // L_b / c_b in cells: x_b / L_b = i_b / n_b
+  std::vector<double> tab(nb);
+  const double kTwoPi = 6.283185307179586476925286766559;
+  for (int i = 0; i < nb; ++i) tab[i] = m->force_A * std::sin(kTwoPi * m->force_k * i / Lb + m->force_phase);
+  cudaError_t err;
+  if (m->store == LBM_F64) {
+    err = cudaMemcpyAsync(m->force_tab, tab.data(), nb * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+  } else {
+    std::vector<float> tf(tab.begin(), tab.end());
+    err = cudaMemcpyAsync(m->force_tab, tf.data(), nb * sizeof(float), cudaMemcpyHostToDevice, m->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(m->stream);  // tf is about to go out of scope
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(m->stream);
+  return err == cudaSuccess ? LBM_OK : cuda_error(err, "force upload");
+}
+
+template <class F>
+lbm_status dispatch_kind(int kind, F&& f) {
+  switch (kind) {
+    case LBM_RD2Q13: return f(std::integral_constant<int, LBM_RD2Q13>{});
+    case LBM_RD2Q17: return f(std::integral_constant<int, LBM_RD2Q17>{});
+    case LBM_RD2Q21: return f(std::integral_constant<int, LBM_RD2Q21>{});
+    case LBM_RD2Q25: return f(std::integral_constant<int, LBM_RD2Q25>{});
+    case LBM_RD3Q33: return f(std::integral_constant<int, LBM_RD3Q33>{});
+    case LBM_RD3Q45: return f(std::integral_constant<int, LBM_RD3Q45>{});
+    case LBM_RD3Q53: return f(std::integral_constant<int, LBM_RD3Q53>{});
+  }
+  return set_error(LBM_ERR_ARG, "unknown lattice kind");
+}
+
+// Run fn with a device staging buffer of `bytes` when the user buffer is in host memory.
+template <class F>
+lbm_status with_staging(lbm_model* m, size_t bytes, bool need, F&& fn) {
+  if (!need) return fn(nullptr);
+  void* tmp = nullptr;
+  cudaError_t err = cudaMallocAsync(&tmp, bytes, m->stream);
+  if (err != cudaSuccess) return cuda_error(err, "staging allocation");
+  lbm_status st = fn(tmp);
+  err = cudaFreeAsync(tmp, m->stream);
+  if (st == LBM_OK && err != cudaSuccess) st = cuda_error(err, "staging free");
+  return st;
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" {
+
+int lbm_abi_version(void) { return LBM_ABI_VERSION; }
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+lbm_status lbm_lattice_create(lbm_kind kind, const double* c, const double* cs2, const double* free_w,
+                              int n_free, lbm_lattice** out) {
+  try {
+    if (!out || !c || !cs2) return set_error(LBM_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (int(kind) < LBM_RD2Q13 || int(kind) > LBM_RD3Q53) return set_error(LBM_ERR_ARG, "unknown lattice kind");
+    static const int kFree[7] = {0, 1, 3, 4, 0, 0, 1};
+    if (n_free != kFree[kind])
+      return set_error(LBM_ERR_ARG, "lattice kind " + std::to_string(int(kind)) + " takes " +
+                                        std::to_string(kFree[kind]) + " free weights");
+    if (n_free > 0 && !free_w) return set_error(LBM_ERR_ARG, "free_w is NULL");
+    auto* L = new (std::nothrow) lbm_lattice;
+    if (!L) return set_error(LBM_ERR_OOM, "host allocation failed");
+    std::memset(L, 0, sizeof(*L));
+    L->kind = kind;
+    L->d = lattice_dims(kind);
+    L->Q = lattice_q(kind);
+    L->R = L->d == 2 ? 10 : 20;
+    L->rmax = lattice_rmax(kind);
+    for (int a = 0; a < L->d; ++a) {
+      if (!(c[a] > 0.0) || !(cs2[a] > 0.0) || !std::isfinite(c[a]) || !std::isfinite(cs2[a])) {
+        delete L;
+        return set_error(LBM_ERR_ARG, "c and cs2 must be positive and finite");
+      }
+      L->c[a] = c[a];
+      L->cs2[a] = cs2[a];
+    }
+    for (int k = 0; k < n_free; ++k) L->free_w[k] = free_w[k];
+    for (int j = 0; j < L->Q; ++j) {
+      const Vel v = lattice_e(kind, j);
+      L->e[j * 3 + 0] = int8_t(v.x);
+      L->e[j * 3 + 1] = int8_t(v.y);
+      L->e[j * 3 + 2] = int8_t(v.z);
+    }
+    cudaGetDevice(&L->device);
+    lbm_status st = setup_lattice_fp64(L);
+    if (st != LBM_OK) {
+      delete L;
+      return st;
+    }
+    *out = L;
+    return LBM_OK;
+  } catch (...) {
+    return set_error(LBM_ERR_ARG, "unexpected exception in lbm_lattice_create");
+  }
+}
+
+lbm_status lbm_lattice_query(const lbm_lattice* L, int* d, int* Q, int* R, int8_t* e, double* w, double* H,
+                             double* N, double* T) {
+  if (!L) return set_error(LBM_ERR_ARG, "NULL lattice");
+  if (d) *d = L->d;
+  if (Q) *Q = L->Q;
+  if (R) *R = L->R;
+  if (e)
+    for (int j = 0; j < L->Q; ++j)
+      for (int a = 0; a < L->d; ++a) e[j * L->d + a] = L->e[j * 3 + a];
+  if (w) std::memcpy(w, L->w, sizeof(double) * L->Q);
+  if (H) std::memcpy(H, L->H, sizeof(double) * L->Q * L->R);
+  if (N) std::memcpy(N, L->N, sizeof(double) * L->R);
+  if (T) std::memcpy(T, L->T, sizeof(double) * L->R * L->R);
+  return LBM_OK;
+}
+
+lbm_status lbm_lattice_destroy(lbm_lattice* L) {
+  delete L;
+  return LBM_OK;
+}
+
+lbm_status lbm_model_workspace_bytes(const lbm_lattice* L, lbm_eq eq, const int64_t* n, lbm_dtype store,
+                                     size_t* bytes) {
+  if (!L || !bytes) return set_error(LBM_ERR_ARG, "NULL argument");
+  if (int(store) < LBM_F64 || int(store) > LBM_F16_DEV) return set_error(LBM_ERR_ARG, "unknown storage dtype");
+  if (eq != LBM_NSE && eq != LBM_NCDE) return set_error(LBM_ERR_ARG, "unknown equation");
+  lbm_status st = check_grid(L, n);
+  if (st != LBM_OK) return st;
+  *bytes = layout(L, eq, n, store).total;
+  return LBM_OK;
+}
+
+lbm_status lbm_model_create(const lbm_lattice* L, lbm_eq eq, const int64_t* n, lbm_dtype store, lbm_dtype compute,
+                            void* stream, void* workspace, size_t workspace_bytes, lbm_model** out) {
+  try {
+    if (!L || !out) return set_error(LBM_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (eq != LBM_NSE && eq != LBM_NCDE) return set_error(LBM_ERR_ARG, "unknown equation");
+    const bool ok_types = (store == LBM_F64 && compute == LBM_F64) || (store == LBM_F32 && compute == LBM_F32) ||
+                          ((store == LBM_BF16_DEV || store == LBM_F16_DEV) && compute == LBM_F32);
+    if (!ok_types)
+      return set_error(LBM_ERR_ARG, "supported (store, compute): (F64,F64), (F32,F32), (BF16_DEV,F32), (F16_DEV,F32)");
+    lbm_status st = check_grid(L, n);
+    if (st != LBM_OK) return st;
+    const Layout lo = layout(L, eq, n, store);
+    if (workspace && (workspace_bytes < lo.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0))
+      return set_error(LBM_ERR_OOM, "workspace must hold " + std::to_string(lo.total) + " bytes, 256-byte aligned");
+    DeviceGuard guard(L->device);
+    auto* m = new (std::nothrow) lbm_model;
+    if (!m) return set_error(LBM_ERR_OOM, "host allocation failed");
+    std::memset(m, 0, sizeof(*m));
+    m->lat = L;
+    m->eq = eq;
+    m->ncells = 1;
+    for (int a = 0; a < 3; ++a) m->n[a] = a < L->d ? n[a] : 1;
+    for (int a = 0; a < L->d; ++a) m->ncells *= int(n[a]);
+    m->store = store;
+    m->compute = compute;
+    m->stream = static_cast<cudaStream_t>(stream);
+    m->device = L->device;
+    if (workspace) {
+      m->ws = workspace;
+      m->owns_ws = false;
+    } else {
+      cudaError_t err = cudaMalloc(&m->ws, lo.total);
+      if (err != cudaSuccess) {
+        delete m;
+        return cuda_error(err, "model allocation");
+      }
+      m->owns_ws = true;
+    }
+    m->ws_bytes = lo.total;
+    char* base = static_cast<char*>(m->ws);
+    m->f[0] = base;
+    m->f[1] = base + lo.f_bytes;
+    m->phi_prev = eq == LBM_NCDE ? base + lo.phi_off : nullptr;
+    m->force_tab = base + lo.force_off;
+    m->partials = reinterpret_cast<double*>(base + lo.part_off);
+    m->sums = reinterpret_cast<double*>(base + lo.sums_off);
+    cudaError_t err = cudaMemsetAsync(m->ws, 0, lo.total, m->stream);
+    if (err != cudaSuccess) {
+      if (m->owns_ws) cudaFree(m->ws);
+      delete m;
+      return cuda_error(err, "workspace clear");
+    }
+    for (int r = 0; r < lbm::kMaxR; ++r) m->s[r] = 1.0;
+    m->s_high = 1.0;
+    m->cs2_eq = L->cs2[0];
+    m->rho_ref = eq == LBM_NSE ? 1.0 : 0.0;
+    m->force_b = -1;
+    *out = m;
+    return LBM_OK;
+  } catch (...) {
+    return set_error(LBM_ERR_ARG, "unexpected exception in lbm_model_create");
+  }
+}
+
+lbm_status lbm_model_set_relaxation(lbm_model* m, const double* s, double s_high) {
+  if (!m || !s) return set_error(LBM_ERR_ARG, "NULL argument");
+  for (int r = 0; r < m->lat->R; ++r)
+    if (!(s[r] > 0.0 && s[r] <= 2.0)) return set_error(LBM_ERR_ARG, "rates must lie in (0, 2]");
+  if (!(s_high > 0.0 && s_high <= 2.0)) return set_error(LBM_ERR_ARG, "rates must lie in (0, 2]");
+  for (int r = 0; r < m->lat->R; ++r) m->s[r] = s[r];
+  m->s_high = s_high;
+  return LBM_OK;
+}
+
+lbm_status lbm_model_set_eos(lbm_model* m, double cs2_eq) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (!(cs2_eq > 0.0) || !std::isfinite(cs2_eq)) return set_error(LBM_ERR_ARG, "cs2_eq must be positive");
+  m->cs2_eq = cs2_eq;
+  return LBM_OK;
+}
+
+lbm_status lbm_model_set_force(lbm_model* m, int axis_a, int axis_b, double A, int k, double phase) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (m->eq != LBM_NSE) return set_error(LBM_ERR_ARG, "body force applies to the NSE model");
+  const int d = m->lat->d;
+  if (axis_a < 0 || axis_a >= d || axis_b < 0 || axis_b >= d) return set_error(LBM_ERR_ARG, "axis out of range");
+  if (!std::isfinite(A) || !std::isfinite(phase)) return set_error(LBM_ERR_ARG, "non-finite force parameter");
+  DeviceGuard guard(m->device);
+  m->force_a = axis_a;
+  m->force_b = axis_b;
+  m->force_A = A;
+  m->force_k = k;
+  m->force_phase = phase;
+  return upload_force(m);
+}
+
+lbm_status lbm_model_set_ncde(lbm_model* m, const double* u_const, double nonlin) {
+  if (!m || !u_const) return set_error(LBM_ERR_ARG, "NULL argument");
+  if (m->eq != LBM_NCDE) return set_error(LBM_ERR_ARG, "convection velocity applies to the NCDE model");
+  for (int a = 0; a < 3; ++a) m->u_const[a] = a < m->lat->d ? u_const[a] : 0.0;
+  m->nonlin = nonlin;
+  return LBM_OK;
+}
+
+lbm_status lbm_model_init_fields(lbm_model* m, const double* rho_or_phi, const double* u, int on_device) {
+  if (!m || !rho_or_phi) return set_error(LBM_ERR_ARG, "NULL argument");
+  if (m->eq == LBM_NSE && !u) return set_error(LBM_ERR_ARG, "the NSE model needs a velocity field");
+  DeviceGuard guard(m->device);
+  const size_t N = size_t(m->ncells);
+  const int d = m->lat->d;
+  const size_t nval = m->eq == LBM_NSE ? (1 + d) * N : N;
+  lbm_status st = with_staging(m, nval * sizeof(double), !on_device, [&](void* tmp) -> lbm_status {
+    const double* r = rho_or_phi;
+    const double* uu = u;
+    if (tmp) {
+      double* t = static_cast<double*>(tmp);
+      cudaError_t err = cudaMemcpyAsync(t, rho_or_phi, N * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+      if (err == cudaSuccess && m->eq == LBM_NSE)
+        err = cudaMemcpyAsync(t + N, u, d * N * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+      if (err != cudaSuccess) return cuda_error(err, "field upload");
+      r = t;
+      uu = m->eq == LBM_NSE ? t + N : nullptr;
+    }
+    return dispatch_kind(m->lat->kind, [&](auto kc) { return Launch<decltype(kc)::value>::init(m, r, uu); });
+  });
+  if (st != LBM_OK) return st;
+  if (!on_device) {
+    cudaError_t err = cudaStreamSynchronize(m->stream);
+    if (err != cudaSuccess) return cuda_error(err, "field upload");
+  }
+  m->steps = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_model_set_populations(lbm_model* m, const double* f, int on_device) {
+  if (!m || !f) return set_error(LBM_ERR_ARG, "NULL argument");
+  DeviceGuard guard(m->device);
+  const size_t bytes = size_t(m->lat->Q) * m->ncells * sizeof(double);
+  lbm_status st = with_staging(m, bytes, !on_device, [&](void* tmp) -> lbm_status {
+    const double* src = f;
+    if (tmp) {
+      cudaError_t err = cudaMemcpyAsync(tmp, f, bytes, cudaMemcpyHostToDevice, m->stream);
+      if (err != cudaSuccess) return cuda_error(err, "population upload");
+      src = static_cast<const double*>(tmp);
+    }
+    lbm_status s2 = launch_scatter(m, src);
+    if (s2 == LBM_OK && m->eq == LBM_NCDE) s2 = launch_phi_from_populations(m);
+    return s2;
+  });
+  if (st != LBM_OK) return st;
+  if (!on_device) {
+    cudaError_t err = cudaStreamSynchronize(m->stream);
+    if (err != cudaSuccess) return cuda_error(err, "population upload");
+  }
+  m->steps = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_model_get_populations(lbm_model* m, double* f, int on_device) {
+  if (!m || !f) return set_error(LBM_ERR_ARG, "NULL argument");
+  DeviceGuard guard(m->device);
+  const size_t bytes = size_t(m->lat->Q) * m->ncells * sizeof(double);
+  lbm_status st = with_staging(m, bytes, !on_device, [&](void* tmp) -> lbm_status {
+    double* dst = tmp ? static_cast<double*>(tmp) : f;
+    lbm_status s2 = launch_gather(m, dst);
+    if (s2 != LBM_OK) return s2;
+    if (tmp) {
+      cudaError_t err = cudaMemcpyAsync(f, tmp, bytes, cudaMemcpyDeviceToHost, m->stream);
+      if (err != cudaSuccess) return cuda_error(err, "population download");
+    }
+    return LBM_OK;
+  });
+  if (st != LBM_OK) return st;
+  if (!on_device) {
+    cudaError_t err = cudaStreamSynchronize(m->stream);
+    if (err != cudaSuccess) return cuda_error(err, "population download");
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_model_step(lbm_model* m, int64_t nsteps) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (nsteps < 0) return set_error(LBM_ERR_ARG, "nsteps must be non-negative");
+  DeviceGuard guard(m->device);
+  return dispatch_kind(m->lat->kind, [&](auto kc) { return Launch<decltype(kc)::value>::step(m, nsteps, true); });
+}
+
+lbm_status lbm_model_stream_only(lbm_model* m, int64_t nsteps) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (nsteps < 0) return set_error(LBM_ERR_ARG, "nsteps must be non-negative");
+  DeviceGuard guard(m->device);
+  return dispatch_kind(m->lat->kind, [&](auto kc) { return Launch<decltype(kc)::value>::step(m, nsteps, false); });
+}
+
+lbm_status lbm_model_read_fields(lbm_model* m, double* rho_or_phi, double* u, int on_device) {
+  if (!m || !rho_or_phi) return set_error(LBM_ERR_ARG, "NULL argument");
+  DeviceGuard guard(m->device);
+  const size_t N = size_t(m->ncells);
+  const int d = m->lat->d;
+  const bool want_u = m->eq == LBM_NSE && u != nullptr;
+  const size_t nval = want_u ? (1 + d) * N : N;
+  lbm_status st = with_staging(m, nval * sizeof(double), !on_device, [&](void* tmp) -> lbm_status {
+    double* r = tmp ? static_cast<double*>(tmp) : rho_or_phi;
+    double* uu = want_u ? (tmp ? static_cast<double*>(tmp) + N : u) : nullptr;
+    lbm_status s2 = launch_fields(m, r, uu);
+    if (s2 != LBM_OK) return s2;
+    if (tmp) {
+      cudaError_t err = cudaMemcpyAsync(rho_or_phi, r, N * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+      if (err == cudaSuccess && want_u)
+        err = cudaMemcpyAsync(u, uu, d * N * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+      if (err != cudaSuccess) return cuda_error(err, "field download");
+    }
+    return LBM_OK;
+  });
+  if (st != LBM_OK) return st;
+  if (!on_device) {
+    cudaError_t err = cudaStreamSynchronize(m->stream);
+    if (err != cudaSuccess) return cuda_error(err, "field download");
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_model_conserved_sums(lbm_model* m, double* out_host) {
+  if (!m || !out_host) return set_error(LBM_ERR_ARG, "NULL argument");
+  DeviceGuard guard(m->device);
+  lbm_status st = launch_sums(m);
+  if (st != LBM_OK) return st;
+  double s[4];
+  cudaError_t err = cudaMemcpyAsync(s, m->sums, sizeof(s), cudaMemcpyDeviceToHost, m->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(m->stream);
+  if (err != cudaSuccess) return cuda_error(err, "conservation sums");
+  const int d = m->lat->d;
+  bool finite = true;
+  for (int q = 0; q <= d; ++q) {
+    out_host[q] = s[q];
+    finite = finite && std::isfinite(s[q]);
+  }
+  if (!finite) return set_error(LBM_ERR_NONFINITE, "a conservation sum is not finite");
+  return LBM_OK;
+}
+
+lbm_status lbm_model_counters(const lbm_model* m, int64_t* steps, int64_t* launches) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (steps) *steps = m->steps;
+  if (launches) *launches = m->launches;
+  return LBM_OK;
+}
+
+lbm_status lbm_model_synchronize(lbm_model* m) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  DeviceGuard guard(m->device);
+  cudaError_t err = cudaStreamSynchronize(m->stream);
+  return err == cudaSuccess ? LBM_OK : cuda_error(err, "synchronize");
+}
+
+lbm_status lbm_model_destroy(lbm_model* m) {
+  if (!m) return LBM_OK;
+  DeviceGuard guard(m->device);
+  cudaStreamSynchronize(m->stream);
+  if (m->owns_ws) cudaFree(m->ws);
+  delete m;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "lattices.cuh"
+#include "lbm_mrt.h"
+
+// Host-side lattice handle: the FP64 tables built on the GPU by the set-up kernel.
+struct lbm_lattice {
+  int kind, d, Q, R, rmax;
+  int8_t e[lbm::kMaxQ * 3];
+  double c[3], cs2[3], free_w[4];
+  double w[lbm::kMaxQ];
+  double H[lbm::kMaxR * lbm::kMaxQ];
+  double N[lbm::kMaxR];
+  double T[lbm::kMaxR * lbm::kMaxR];
+  int device;
+};
+
+struct lbm_model {
+  const lbm_lattice* lat;
+  int eq;
+  int64_t n[3];
+  int ncells;
+  int store, compute;
+  cudaStream_t stream;
+  void* ws;
+  size_t ws_bytes;
+  bool owns_ws;
+  void* f[2];  // ping-pong population buffers (storage dtype), f[cur] is the current state
+  int cur;
+  void* phi_prev;   // NCDE: phi at the previous step (compute dtype)
+  void* force_tab;  // NSE: F_a as a function of the cell index along axis b (compute dtype)
+  double* partials; // reduction scratch of the conservation sums
+  double* sums;     // 4 doubles
+  double s[lbm::kMaxR];
+  double s_high, cs2_eq, rho_ref;
+  int force_a, force_b, force_k;
+  double force_A, force_phase;
+  double u_const[3];
+  double nonlin;
+  int64_t steps, launches;
+  int device;
+};
+
+namespace lbm {
+
+constexpr int kBlock = 128;          // threads per block of the cell kernels
+constexpr int kRedBlocks = 608;      // blocks of the conservation-sum reduction (4 x 152 SMs)
+
+// Kernel parameters of the time step, passed by value (they live in the constant bank, so
+// every table read below is an operand of the arithmetic instruction, not a memory load).
+template <class CT>
+struct StepParams {
+  CT T[kMaxR][kMaxR];  // Hermite rows as monic polynomials of the monomials (physical units)
+  CT D[kMaxR];         // monomial scale: mono_k(c_i) = D_k * mono_k(e_i)
+  CT invN[kMaxR];      // 1 / N_r
+  CT sd[kMaxR];        // s_r - s_high
+  CT half[kMaxR];      // 1 - s_r / 2
+  CT w[kMaxQ];
+  CT wref[kMaxQ];      // w_i * rho_ref, the offset of deviation storage
+  CT s_high, one_minus_sh, cs2_eq, nonlin_third;
+  CT u_const[3];
+  int n[3];
+  int ncells;
+  int force_a, force_b;  // force_b < 0: no body force
+  const CT* force_tab;
+};
+
+// Parameters of the generic (lattice-agnostic, non-hot) kernels.
+struct GenParams {
+  int Q, d, n[3], ncells;
+  int8_t e[kMaxQ][3];
+  double c[3];
+  double wref[kMaxQ];
+  int force_a, force_b;
+  const void* force_tab;
+};
+
+// Storage codecs: FP64/FP32 store f itself; BF16/FP16 store the deviation f - w_i rho_ref.
+template <class ST>
+struct Codec;
+template <>
+struct Codec<double> {
+  template <class CT> __device__ __forceinline__ static CT dec(double v, CT) { return CT(v); }
+  template <class CT> __device__ __forceinline__ static double enc(CT v, CT) { return double(v); }
+};
+template <>
+struct Codec<float> {
+  template <class CT> __device__ __forceinline__ static CT dec(float v, CT) { return CT(v); }
+  template <class CT> __device__ __forceinline__ static float enc(CT v, CT) { return float(v); }
+};
+template <>
+struct Codec<__nv_bfloat16> {
+  template <class CT> __device__ __forceinline__ static CT dec(__nv_bfloat16 v, CT base) {
+    return CT(__bfloat162float(v)) + base;
+  }
+  template <class CT> __device__ __forceinline__ static __nv_bfloat16 enc(CT v, CT base) {
+    return __float2bfloat16_rn(float(v - base));
+  }
+};
+template <>
+struct Codec<__half> {
+  template <class CT> __device__ __forceinline__ static CT dec(__half v, CT base) {
+    return CT(__half2float(v)) + base;
+  }
+  template <class CT> __device__ __forceinline__ static __half enc(CT v, CT base) {
+    return __float2half_rn(float(v - base));
+  }
+};
+
+inline size_t dtype_bytes(int dt) { return dt == LBM_F64 ? 8 : dt == LBM_F32 ? 4 : 2; }
+
+// Error reporting (thread-local message behind lbm_last_error).
+lbm_status set_error(lbm_status st, const std::string& msg);
+lbm_status cuda_error(cudaError_t err, const char* what);
+
+// Per-lattice launchers, defined in the k_<lattice>.cu translation units.
+template <int KIND>
+struct Launch {
+  static lbm_status step(lbm_model* m, int64_t nsteps, bool collide);
+  static lbm_status init(lbm_model* m, const double* rho_or_phi, const double* u);
+};
+
+// Generic kernels (aux_kernels.cu).
+lbm_status gen_params(const lbm_model* m, GenParams* gp);
+lbm_status launch_gather(lbm_model* m, double* out);          // f-bar(x) from the stored array
+lbm_status launch_scatter(lbm_model* m, const double* in);    // stored array from f-bar(x)
+lbm_status launch_fields(lbm_model* m, double* rho, double* u);
+lbm_status launch_sums(lbm_model* m);                          // into m->sums (device)
+lbm_status launch_phi_from_populations(lbm_model* m);          // NCDE: phi_prev = sum f-bar
+
+// FP64 lattice set-up on the GPU (setup_fp64.cu).
+lbm_status setup_lattice_fp64(lbm_lattice* lat);
+
+// Host-side construction of the step parameters from a model.
+template <class CT>
+void make_step_params(const lbm_model* m, StepParams<CT>* p);
+
+}  // namespace lbm

@@ -1,0 +1,466 @@
+// The per-cell MRT collision in the Hermite basis and the fused pull collide-stream kernel.
+//
+// One thread owns one cell. It gathers the Q populations of its cell from the neighbours
+// x - e_i of the previous step (pull form of the propagation, Eq. (2-2b)), collides them
+// (Eq. (2-3) with the Hermite-moment collision Eq. (H-MRT-LB-1)) and writes the post-collision
+// populations back at its own cell (aligned, coalesced stores). The stored array is therefore
+// the post-collision state of the last step; the pre-collision f-bar(x, t_n) of the paper is
+// its pull-gather.
+//
+// The collision is evaluated in the reduced form that Eq. (H-MRT-LB-1) gives when every row
+// of order >= 4 relaxes with one rate s_h:
+//   f*_i = (1 - s_h) f_i + w_i sum_{r<R} H_ri / N_r [ s_h m^eq_r - (s_r - s_h)(m_r - m^eq_r)
+//                                                     + sigma_r ],
+// because the W-orthogonal complement of span(H0..H3) carries the same rate in every row.
+// The two contractions with the Hermite matrix are factored through the monomials:
+// H_r(c_i) = sum_k T_rk D_k mono_k(e_i), where mono_k(e_i) are small integers known at
+// compile time (so zero products vanish and the +-e pairs share one pass), T is the
+// lower-triangular, parity-block-diagonal Gram-Schmidt factor and D_k the axis-speed scale.
+#pragma once
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+template <class CT>
+__device__ __forceinline__ CT fmaf_t(CT a, CT b, CT c) {
+  return fma(a, b, c);
+}
+
+// acc + c * x for a compile-time integer c
+template <int C, class CT>
+__device__ __forceinline__ CT axpy_c(CT x, CT acc) {
+  if constexpr (C == 1) return acc + x;
+  else if constexpr (C == -1) return acc - x;
+  else return fma(CT(C), x, acc);
+}
+
+__host__ __device__ constexpr int axis_n(Mono m, int n) {
+  // n-th axis (0-based) in the sorted list of axes of monomial m, e.g. xyy -> x, y, y
+  return n < m.a ? 0 : (n < m.a + m.b ? 1 : 2);
+}
+
+// Raw moments mu_k = sum_i mono_k(e_i) f_i, k < R, pairing e and -e.
+template <class L, class CT>
+__device__ __forceinline__ void raw_moments(const CT (&f)[L::Q], CT (&mu)[L::R]) {
+  static_for<L::R>([&](auto k) { mu[decltype(k)::value] = CT(0); });
+  mu[0] = f[0];
+  static_for<L::Q>([&](auto i) {
+    constexpr int I = decltype(i)::value;
+    if constexpr (I > 0 && I < opposite<L>(I)) {
+      const CT sp = f[I] + f[opposite<L>(I)];
+      const CT sm = f[I] - f[opposite<L>(I)];
+      static_for<L::R>([&](auto k) {
+        constexpr int K = decltype(k)::value;
+        constexpr int cv = mono_value(L::e(decltype(i)::value), mono<L::D>(K));
+        if constexpr (cv != 0) {
+          if constexpr (degree(mono<L::D>(K)) % 2 == 0) mu[K] = axpy_c<cv>(sp, mu[K]);
+          else mu[K] = axpy_c<cv>(sm, mu[K]);
+        }
+      });
+    }
+  });
+}
+
+// Continuous raw moments of the NSE equilibrium (Eq. (M-NSEs-6a), Eq. (M-NSEs-6-1) with k = 0,
+// M30 = rho u u u, p = rho cs2_eq): M0 = rho, M1 = j, M2 = j u + p I,
+// M3 = j u u + p (u delta)_sym, for every monomial of the paper's row order.
+template <class L, class CT>
+__device__ __forceinline__ void eq_raw_nse(CT rho, const CT (&j)[3], const CT (&u)[3], CT P,
+                                           CT (&me)[L::R]) {
+  static_for<L::R>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    constexpr int deg = degree(mono<L::D>(K));
+    constexpr int a0 = axis_n(mono<L::D>(K), 0), a1 = axis_n(mono<L::D>(K), 1),
+                  a2 = axis_n(mono<L::D>(K), 2);
+    if constexpr (deg == 0) {
+      me[K] = rho;
+    } else if constexpr (deg == 1) {
+      me[K] = j[a0];
+    } else if constexpr (deg == 2) {
+      if constexpr (a0 == a1) me[K] = fma(j[a0], u[a1], P);
+      else me[K] = j[a0] * u[a1];
+    } else {
+      CT v = j[a0] * u[a1] * u[a2];
+      if constexpr (a1 == a2) v = fma(P, u[a0], v);
+      if constexpr (a0 == a2) v = fma(P, u[a1], v);
+      if constexpr (a0 == a1) v = fma(P, u[a2], v);
+      me[K] = v;
+    }
+  });
+}
+
+// Continuous raw moments of the NCDE equilibrium up to second order (Eq. (M-NCDE-6), M20 = 0):
+// M0 = phi, M1 = u phi, M2 = cs2_eq D(phi) I. Third-order entries are unused.
+template <class L, class CT>
+__device__ __forceinline__ void eq_raw_ncde(CT phi, CT Dphi, const StepParams<CT>& p,
+                                            CT (&me)[L::R]) {
+  static_for<L::R>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    constexpr int deg = degree(mono<L::D>(K));
+    constexpr int a0 = axis_n(mono<L::D>(K), 0), a1 = axis_n(mono<L::D>(K), 1);
+    if constexpr (deg == 0) me[K] = phi;
+    else if constexpr (deg == 1) me[K] = p.u_const[a0] * phi;
+    else if constexpr (deg == 2) me[K] = (a0 == a1) ? p.cs2_eq * Dphi : CT(0);
+    else me[K] = CT(0);
+  });
+}
+
+// sum_{k < r, same parity class as r} T_rk v_k + v_r   (T is monic: T_rr = 1)
+template <class L, class CT, int r>
+__device__ __forceinline__ CT row_dot(const StepParams<CT>& p, const CT (&v)[L::R]) {
+  CT acc = v[r];
+  static_for<r>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    if constexpr (parity_class(mono<L::D>(K)) == parity_class(mono<L::D>(r)))
+      acc = fma(p.T[r][K], v[K], acc);
+  });
+  return acc;
+}
+
+// Hermite moments of the equilibrium, m^eq_r = sum_k T_rk me_k.
+// For the NCDE the third-order Hermite moments of the equilibrium are zero.
+template <class L, class CT, int EQ, int r>
+__device__ __forceinline__ CT hermite_eq(const StepParams<CT>& p, const CT (&me)[L::R]) {
+  if constexpr (EQ == LBM_NCDE && degree(mono<L::D>(r)) == 3) return CT(0);
+  else return row_dot<L, CT, r>(p, me);
+}
+
+// f_i = (1 - s_h) f_i + w_i sum_k mono_k(e_i) h_k  (h already scaled by D_k), e/-e paired.
+template <class L, class CT>
+__device__ __forceinline__ void back_project(CT (&f)[L::Q], const StepParams<CT>& p,
+                                             const CT (&h)[L::R], CT oms) {
+  f[0] = fma(oms, f[0], p.w[0] * h[0]);
+  static_for<L::Q>([&](auto i) {
+    constexpr int I = decltype(i)::value;
+    if constexpr (I > 0 && I < opposite<L>(I)) {
+      CT E = CT(0), O = CT(0);
+      static_for<L::R>([&](auto k) {
+        constexpr int K = decltype(k)::value;
+        constexpr int cv = mono_value(L::e(decltype(i)::value), mono<L::D>(K));
+        if constexpr (cv != 0) {
+          if constexpr (degree(mono<L::D>(K)) % 2 == 0) E = axpy_c<cv>(h[K], E);
+          else O = axpy_c<cv>(h[K], O);
+        }
+      });
+      constexpr int J = opposite<L>(I);
+      f[I] = fma(oms, f[I], p.w[I] * (E + O));
+      f[J] = fma(oms, f[J], p.w[J] * (E - O));
+    }
+  });
+}
+
+// h_k = D_k sum_{r >= k, same parity class} T_rk gN_r   (the transpose contraction)
+template <class L, class CT>
+__device__ __forceinline__ void hermite_to_monomial(const StepParams<CT>& p, const CT (&gN)[L::R],
+                                                    CT (&h)[L::R]) {
+  static_for<L::R>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    CT acc = gN[K];
+    static_for<L::R>([&](auto r) {
+      constexpr int Rr = decltype(r)::value;
+      constexpr int Kk = decltype(k)::value;
+      if constexpr (Rr > Kk && parity_class(mono<L::D>(Rr)) == parity_class(mono<L::D>(Kk)))
+        acc = fma(p.T[Rr][Kk], gN[Rr], acc);
+    });
+    if constexpr (K == 0) h[K] = acc;
+    else h[K] = acc * p.D[K];
+  });
+}
+
+// Hermite-row work of the collision for row r: g_r / N_r with
+// g_r = s_h m^eq_r - (s_r - s_h)(m_r - m^eq_r) + sigma_r.
+template <class L, class CT, int EQ, int r>
+__device__ __forceinline__ CT row_update(const StepParams<CT>& p, const CT (&mu)[L::R],
+                                         const CT (&me)[L::R], const CT (&u)[3], const CT (&F)[3],
+                                         CT dphi) {
+  constexpr int deg = degree(mono<L::D>(r));
+  const CT meq = hermite_eq<L, CT, EQ, r>(p, me);
+  CT neq;
+  if constexpr (EQ == LBM_NCDE && deg == 3) {
+    neq = row_dot<L, CT, r>(p, mu);
+  } else {
+    CT dm[L::R];
+    static_for<r + 1>([&](auto k) {
+      constexpr int K = decltype(k)::value;
+      if constexpr (parity_class(mono<L::D>(K)) == parity_class(mono<L::D>(r))) dm[K] = mu[K] - me[K];
+      else dm[K] = CT(0);
+    });
+    neq = row_dot<L, CT, r>(p, dm);
+  }
+  // source moments sigma_r: NSE (I - S/2) M1F = (1 - s/2) F on order 1 and
+  // M2G = (I - S2/2)(uF + Fu) on order 2; NCDE M1G = (I - S1/2) u d_t phi on order 1
+  CT sig = CT(0);
+  if constexpr (deg == 1) {
+    constexpr int a = axis_n(mono<L::D>(r), 0);
+    if constexpr (EQ == LBM_NSE) sig = p.half[r] * F[a];
+    else sig = p.half[r] * p.u_const[a] * dphi;
+  } else if constexpr (deg == 2 && EQ == LBM_NSE) {
+    constexpr int a = axis_n(mono<L::D>(r), 0), b = axis_n(mono<L::D>(r), 1);
+    sig = p.half[r] * fma(u[a], F[b], u[b] * F[a]);
+  }
+  const CT g = fma(p.s_high, meq, fma(-p.sd[r], neq, sig));
+  return g * p.invN[r];
+}
+
+// One collision (Eq. (2-3)) of the populations f of one cell, in place.
+// F: body force at the cell (NSE); phi_prev / phi_now: the NCDE field at t_{n-1} and t_n.
+template <class L, class CT, int EQ>
+__device__ __forceinline__ void collide(CT (&f)[L::Q], const StepParams<CT>& p, const CT (&F)[3],
+                                        CT phi_prev, CT& phi_now) {
+  constexpr int R = L::R, D = L::D;
+  CT mu[R];
+  raw_moments<L>(f, mu);
+  static_for<R>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    if constexpr (K > 0) mu[K] *= p.D[K];
+  });
+  CT me[R];
+  CT u[3] = {CT(0), CT(0), CT(0)};
+  CT dphi = CT(0);
+  if constexpr (EQ == LBM_NSE) {
+    // Eq. (2-4-2) with S = 0, F_F = F: rho = sum f, rho u = sum c f + F / 2
+    const CT rho = mu[0];
+    const CT inv = CT(1) / rho;
+    CT j[3] = {CT(0), CT(0), CT(0)};
+    static_for<D>([&](auto a) {
+      constexpr int A = decltype(a)::value;
+      j[A] = fma(CT(0.5), F[A], mu[1 + A]);
+      u[A] = j[A] * inv;
+    });
+    eq_raw_nse<L>(rho, j, u, rho * p.cs2_eq, me);
+  } else {
+    // Eq. (2-4-1) with S = 0: phi = sum f
+    const CT phi = mu[0];
+    phi_now = phi;
+    dphi = phi - phi_prev;
+    eq_raw_ncde<L>(phi, fma(p.nonlin_third, phi * phi * phi, phi), p, me);
+  }
+  CT gN[R];
+  static_for<R>([&](auto r) {
+    constexpr int Rr = decltype(r)::value;
+    gN[Rr] = row_update<L, CT, EQ, Rr>(p, mu, me, u, F, dphi);
+  });
+  CT h[R];
+  hermite_to_monomial<L>(p, gN, h);
+  back_project<L>(f, p, h, p.one_minus_sh);
+}
+
+// Equilibrium populations of given fields, Eq. (feq-1): f^eq_i = w_i sum_r H_ri m^eq_r / N_r.
+template <class L, class CT, int EQ>
+__device__ __forceinline__ void equilibrium(CT (&f)[L::Q], const StepParams<CT>& p, CT rho_or_phi,
+                                            const CT (&uin)[3]) {
+  constexpr int R = L::R;
+  CT me[R];
+  if constexpr (EQ == LBM_NSE) {
+    CT j[3], u[3];
+    for (int a = 0; a < 3; ++a) {
+      u[a] = uin[a];
+      j[a] = rho_or_phi * uin[a];
+    }
+    eq_raw_nse<L>(rho_or_phi, j, u, rho_or_phi * p.cs2_eq, me);
+  } else {
+    const CT phi = rho_or_phi;
+    eq_raw_ncde<L>(phi, fma(p.nonlin_third, phi * phi * phi, phi), p, me);
+  }
+  CT gN[R];
+  static_for<R>([&](auto r) {
+    constexpr int Rr = decltype(r)::value;
+    gN[Rr] = hermite_eq<L, CT, EQ, Rr>(p, me) * p.invN[Rr];
+  });
+  CT h[R];
+  hermite_to_monomial<L>(p, gN, h);
+  static_for<L::Q>([&](auto i) { f[decltype(i)::value] = CT(0); });
+  back_project<L>(f, p, h, CT(0));
+}
+
+// Cell coordinates and periodic neighbour offsets.
+template <class L>
+struct Neigh {
+  static constexpr int RM = L::RMAX;
+  int xo[2 * RM + 1], yo[2 * RM + 1], zo[2 * RM + 1];
+  int x, y, z;
+  __device__ __forceinline__ Neigh(int cell, const int (&n)[3]) {
+    const int nx = n[0], ny = n[1];
+    if constexpr (L::D == 2) {
+      y = cell / nx;
+      x = cell - y * nx;
+      z = 0;
+    } else {
+      const int t = cell / nx;
+      x = cell - t * nx;
+      z = t / ny;
+      y = t - z * ny;
+    }
+#pragma unroll
+    for (int s = -RM; s <= RM; ++s) {
+      int xs = x - s;
+      xs += xs < 0 ? nx : 0;
+      xs -= xs >= nx ? nx : 0;
+      xo[s + RM] = xs;
+      int ys = y - s;
+      ys += ys < 0 ? ny : 0;
+      ys -= ys >= ny ? ny : 0;
+      yo[s + RM] = ys * nx;
+      if constexpr (L::D == 3) {
+        const int nz = n[2];
+        int zs = z - s;
+        zs += zs < 0 ? nz : 0;
+        zs -= zs >= nz ? nz : 0;
+        zo[s + RM] = zs * nx * ny;
+      } else {
+        zo[s + RM] = 0;
+      }
+    }
+  }
+  // cell index of x - e (pull source) for a compile-time velocity
+  template <int I>
+  __device__ __forceinline__ int src() const {
+    constexpr Vel v = L::e(I);
+    return xo[RM + v.x] + yo[RM + v.y] + (L::D == 3 ? zo[RM + v.z] : 0);
+  }
+  // cell index of x + e
+  template <int I>
+  __device__ __forceinline__ int dst() const {
+    constexpr Vel v = L::e(I);
+    return xo[RM - v.x] + yo[RM - v.y] + (L::D == 3 ? zo[RM - v.z] : 0);
+  }
+};
+
+template <class CT>
+__device__ __forceinline__ void body_force(const StepParams<CT>& p, int x, int y, int z,
+                                           CT (&F)[3]) {
+  F[0] = F[1] = F[2] = CT(0);
+  if (p.force_b >= 0) {
+    const int ib = p.force_b == 0 ? x : (p.force_b == 1 ? y : z);
+    const CT v = p.force_tab[ib];
+    F[0] = p.force_a == 0 ? v : CT(0);
+    F[1] = p.force_a == 1 ? v : CT(0);
+    F[2] = p.force_a == 2 ? v : CT(0);
+  }
+}
+
+// K1 (COLLIDE) / K2 (stream only): pull gather, collide, aligned store.
+template <class L, class CT, class ST, int EQ, bool COLLIDE>
+__global__ void __launch_bounds__(kBlock) k_step(const StepParams<CT> p,
+                                                 const ST* __restrict__ fin,
+                                                 ST* __restrict__ fout, CT* __restrict__ phi) {
+  const int cell = blockIdx.x * kBlock + threadIdx.x;
+  if (cell >= p.ncells) return;
+  const Neigh<L> nb(cell, p.n);
+  const size_t N = size_t(p.ncells);
+  CT f[L::Q];
+  static_for<L::Q>([&](auto i) {
+    constexpr int I = decltype(i)::value;
+    f[I] = Codec<ST>::dec(__ldg(fin + size_t(I) * N + nb.template src<I>()), p.wref[I]);
+  });
+  if constexpr (COLLIDE) {
+    CT F[3];
+    body_force(p, nb.x, nb.y, nb.z, F);
+    CT phi_prev = CT(0), phi_now = CT(0);
+    if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
+    collide<L, CT, EQ>(f, p, F, phi_prev, phi_now);
+    if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
+  }
+  static_for<L::Q>([&](auto i) {
+    constexpr int I = decltype(i)::value;
+    fout[size_t(I) * N + cell] = Codec<ST>::enc(f[I], p.wref[I]);
+  });
+}
+
+// Initialisation: f-bar(t=0) = f^eq(fields), written to the stored array at x - e_i so that the
+// next pull gather yields it; the NCDE previous-step field starts at phi^0.
+template <class L, class CT, class ST, int EQ>
+__global__ void __launch_bounds__(kBlock) k_init(const StepParams<CT> p, const double* rho_or_phi,
+                                                 const double* u, ST* __restrict__ fout,
+                                                 CT* __restrict__ phi) {
+  const int cell = blockIdx.x * kBlock + threadIdx.x;
+  if (cell >= p.ncells) return;
+  const Neigh<L> nb(cell, p.n);
+  const size_t N = size_t(p.ncells);
+  const CT r = CT(rho_or_phi[cell]);
+  CT uu[3] = {CT(0), CT(0), CT(0)};
+  if constexpr (EQ == LBM_NSE) {
+    for (int a = 0; a < L::D; ++a) uu[a] = CT(u[size_t(a) * N + cell]);
+  } else {
+    phi[cell] = r;
+  }
+  CT f[L::Q];
+  equilibrium<L, CT, EQ>(f, p, r, uu);
+  static_for<L::Q>([&](auto i) {
+    constexpr int I = decltype(i)::value;
+    fout[size_t(I) * N + nb.template src<I>()] = Codec<ST>::enc(f[I], p.wref[I]);
+  });
+}
+
+// Host launchers for one lattice kind (instantiated in k_<lattice>.cu).
+template <class L, class CT, class ST>
+lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
+  StepParams<CT> p;
+  make_step_params<CT>(m, &p);
+  const int grid = (m->ncells + kBlock - 1) / kBlock;
+  CT* phi = static_cast<CT*>(m->phi_prev);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const ST* fin = static_cast<const ST*>(m->f[m->cur]);
+    ST* fout = static_cast<ST*>(m->f[m->cur ^ 1]);
+    if (!collide_on) {
+      k_step<L, CT, ST, LBM_NSE, false><<<grid, kBlock, 0, m->stream>>>(p, fin, fout, phi);
+    } else if (m->eq == LBM_NSE) {
+      k_step<L, CT, ST, LBM_NSE, true><<<grid, kBlock, 0, m->stream>>>(p, fin, fout, phi);
+    } else {
+      k_step<L, CT, ST, LBM_NCDE, true><<<grid, kBlock, 0, m->stream>>>(p, fin, fout, phi);
+    }
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_error(err, "collide-stream launch");
+    m->cur ^= 1;
+    m->launches += 1;
+    if (collide_on) m->steps += 1;
+  }
+  return LBM_OK;
+}
+
+template <class L, class CT, class ST>
+lbm_status launch_init_typed(lbm_model* m, const double* rho_or_phi, const double* u) {
+  StepParams<CT> p;
+  make_step_params<CT>(m, &p);
+  const int grid = (m->ncells + kBlock - 1) / kBlock;
+  ST* fout = static_cast<ST*>(m->f[m->cur]);
+  CT* phi = static_cast<CT*>(m->phi_prev);
+  if (m->eq == LBM_NSE)
+    k_init<L, CT, ST, LBM_NSE><<<grid, kBlock, 0, m->stream>>>(p, rho_or_phi, u, fout, phi);
+  else
+    k_init<L, CT, ST, LBM_NCDE><<<grid, kBlock, 0, m->stream>>>(p, rho_or_phi, u, fout, phi);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_error(err, "init launch");
+  m->launches += 1;
+  return LBM_OK;
+}
+
+template <int KIND>
+lbm_status Launch<KIND>::step(lbm_model* m, int64_t nsteps, bool collide_on) {
+  using L = Lat<KIND>;
+  switch (m->store) {
+    case LBM_F64: return launch_step_typed<L, double, double>(m, nsteps, collide_on);
+    case LBM_F32: return launch_step_typed<L, float, float>(m, nsteps, collide_on);
+    case LBM_BF16_DEV: return launch_step_typed<L, float, __nv_bfloat16>(m, nsteps, collide_on);
+    case LBM_F16_DEV: return launch_step_typed<L, float, __half>(m, nsteps, collide_on);
+  }
+  return set_error(LBM_ERR_ARG, "unknown storage dtype");
+}
+
+template <int KIND>
+lbm_status Launch<KIND>::init(lbm_model* m, const double* rho_or_phi, const double* u) {
+  using L = Lat<KIND>;
+  switch (m->store) {
+    case LBM_F64: return launch_init_typed<L, double, double>(m, rho_or_phi, u);
+    case LBM_F32: return launch_init_typed<L, float, float>(m, rho_or_phi, u);
+    case LBM_BF16_DEV: return launch_init_typed<L, float, __nv_bfloat16>(m, rho_or_phi, u);
+    case LBM_F16_DEV: return launch_init_typed<L, float, __half>(m, rho_or_phi, u);
+  }
+  return set_error(LBM_ERR_ARG, "unknown storage dtype");
+}
+
+}  // namespace lbm
+
+#define LBM_INSTANTIATE_LATTICE(KIND) \
+  template struct lbm::Launch<KIND>;

@@ -1,0 +1,244 @@
+"""GPU parity of the CUDA library (through its C ABI) against the FP64 oracle.
+
+Tolerances: streaming and population I/O are data movement and must be bit-exact. The FP64 path
+must agree with the oracle to <= 1e-12 relative (the oracle applies the full Q x Q matrix
+Lambda = H^{-1} S H while the kernel uses the reduced Hermite form, so agreement is up to rounding
+order; one collision differs by O(1e-15) and 200 steps stay well below 1e-12). The FP32 path must
+agree to <= 1e-5 relative L2 (FP32 unit round-off 6e-8 times the O(10) condition of the moment
+transforms, accumulated over the run).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2512_16230_gb300 import inputs as I
+from paper_2512_16230_gb300 import workloads as W
+
+from _harness import (ALL_SPECS, RAGGED, gpu_lattice, gpu_model, oracle_lattice, oracle_model, rel_l2, rel_max,
+                      round_to_store, workload_pair)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(autouse=True)
+def _lib(lbm_lib):
+    return lbm_lib
+
+
+def _monomials(d):
+    return W.row_orders(d)
+
+
+@pytest.mark.parametrize("name", sorted(ALL_SPECS))
+def test_setup_tables_match_oracle(name):
+    """The FP64 GPU set-up (weights by solving the moment equations, Hermite rows by weighted
+    Gram-Schmidt) equals the oracle's closed-form weights and projected Hermite rows."""
+    spec = ALL_SPECS[name]
+    g = gpu_lattice(spec).tables
+    o = oracle_lattice(spec)
+    assert np.array_equal(g["e"], o.e)
+    assert np.abs(g["w"] - o.w).max() <= 1e-14 * np.abs(o.w).max()
+    assert np.abs(g["H"] - o.H).max() <= 1e-13 * np.abs(o.H).max()
+    N_o = np.sum(o.w * o.H ** 2, axis=1)
+    assert np.abs(g["N"] / N_o - 1).max() <= 1e-13
+    assert np.array_equal(np.diag(g["T"]), np.ones(o.R))
+    assert np.all(np.triu(g["T"], 1) == 0.0)
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q17", "rD2Q21", "rD2Q25", "rD3Q33", "rD3Q45", "rD3Q53"])
+def test_stream_only_is_bit_exact(name, store):
+    """Eq. (2-2b) alone: pure data movement, identical bits to the oracle's periodic shift."""
+    spec = W.LATTICES[name]
+    n = RAGGED[spec.d]
+    om = oracle_model(spec, "nse", n, np.ones(spec.R))
+    gm = gpu_model(spec, "nse", n, np.ones(spec.R), store=store)
+    f0 = round_to_store(I.random_populations(n, om.lat.Q, seed=7), store)
+    gm.set_populations(f0)
+    assert np.array_equal(gm.get_populations(), f0)
+    om.set_populations(f0)
+    gm.stream_only(3)
+    om.stream_only(3)
+    assert np.array_equal(gm.get_populations(), om.f)
+
+
+def _random_rates(R, seed):
+    return np.random.default_rng(seed).uniform(0.6, 1.9, R)
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("eq", ["nse", "ncde"])
+@pytest.mark.parametrize("name", sorted(ALL_SPECS))
+def test_one_collision_stream_step(name, eq, store):
+    """One full step from far-from-equilibrium populations with random rates (NSE with a body
+    force through M1F/M2G, NCDE with its M1G and nonlinear D(phi)), element by element."""
+    spec = ALL_SPECS[name]
+    d = spec.d
+    n = RAGGED[d]
+    s = _random_rates(spec.R, 3)
+    kw = dict(s_high=1.3, cs2_eq=0.55)
+    if eq == "nse":
+        kw["force"] = (0, d - 1, 3e-3, 1, 0.4)
+    else:
+        kw["u_const"] = tuple(np.linspace(0.03, 0.06, d))
+        kw["nonlin"] = 1.0
+    om = oracle_model(spec, eq, n, s, **kw)
+    gm = gpu_model(spec, eq, n, s, store=store, **kw)
+    f0 = round_to_store(I.random_populations(n, om.lat.Q, seed=11), store)
+    om.set_populations(f0)
+    gm.set_populations(f0)
+    om.step(1)
+    gm.step(1)
+    g = gm.get_populations()
+    tol = TOL[store]
+    assert rel_l2(g, om.f) <= tol
+    assert rel_max(g, om.f) <= 10 * tol
+    # a second step exercises phi^{n-1} (NCDE) and the post-collision state
+    om.step(1)
+    gm.step(1)
+    assert rel_l2(gm.get_populations(), om.f) <= tol
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["rD2Q25", "rD2Q13", "rD3Q53", "rD3Q33"])
+def test_init_fields_and_readout(name, store):
+    """Initialisation f-bar = f^eq (Eq. (feq-1)) and the field readout (Eq. (2-4-2))."""
+    spec = W.LATTICES[name]
+    d = spec.d
+    n = RAGGED[d]
+    rho, u = I.random_fields(n, d, seed=5)
+    om = oracle_model(spec, "nse", n, np.ones(spec.R), force=(d - 1, 0, 1e-3, 2, 0.0))
+    gm = gpu_model(spec, "nse", n, np.ones(spec.R), store=store, force=(d - 1, 0, 1e-3, 2, 0.0))
+    om.init_fields(rho, u)
+    gm.init_fields(rho, u)
+    assert rel_max(gm.get_populations(), om.f) <= TOL[store]
+    r_g, u_g = gm.read_fields()
+    r_o, u_o = om.fields()
+    assert rel_max(r_g, r_o) <= TOL[store]
+    assert rel_max(u_g, u_o) <= 10 * TOL[store]
+
+
+@pytest.mark.parametrize("name", ["rD2Q25", "rD2Q13", "rD3Q53", "rD3Q45"])
+def test_conservation_sums(name):
+    """FP64 global sums equal the oracle's; mass is conserved and momentum changes by sum F."""
+    spec = W.LATTICES[name]
+    d = spec.d
+    n = RAGGED[d]
+    force = (0, d - 1, 2e-3, 0, 1.0)    # uniform-in-x profile with non-zero mean
+    om = oracle_model(spec, "nse", n, _random_rates(spec.R, 1), 1.2, force=force)
+    gm = gpu_model(spec, "nse", n, _random_rates(spec.R, 1), 1.2, force=force, store="f64")
+    f0 = I.random_populations(n, om.lat.Q, seed=2)
+    om.set_populations(f0)
+    gm.set_populations(f0)
+    s0 = gm.conserved_sums()
+    assert np.allclose(s0, om.conserved_sums(), rtol=1e-13, atol=1e-13)
+    gm.step(4)
+    om.step(4)
+    s4 = gm.conserved_sums()
+    assert np.allclose(s4, om.conserved_sums(), rtol=1e-12, atol=1e-12)
+    assert abs(s4[0] / s0[0] - 1) < 1e-13
+    F = om.force_field()
+    for a in range(d):
+        assert abs(s4[1 + a] - s0[1 + a] - 4 * F[a].sum()) < 1e-11
+    assert np.array_equal(gm.conserved_sums(), s4)   # deterministic reduction order
+
+
+def test_taylor_green_2d_config_fp64():
+    """Config: rD2Q25 Taylor-Green, 64 x 48 (dy/dx = 4/3), Re = 100, FP64, 200 steps."""
+    wl = W.taylor_green_2d()
+    om, gm = workload_pair(wl, store="f64")
+    om.step(wl.steps)
+    gm.step(wl.steps)
+    r_g, u_g = gm.read_fields()
+    r_o, u_o = om.fields()
+    assert rel_l2(r_g, r_o) <= 1e-12
+    assert rel_l2(u_g, u_o) <= 1e-12
+    assert rel_l2(gm.get_populations(), om.f) <= 1e-12
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+def test_ncde_config_reduced_size(store):
+    """Config 2 at reduced size: rD2Q13 nonlinear CDE (dy/dx = 1.25), sigma = 20, noise 1e-3."""
+    wl = W.ncde_hill(n=(96, 80), steps=150, store=store)
+    om, gm = workload_pair(wl)
+    om.step(wl.steps)
+    gm.step(wl.steps)
+    assert rel_l2(gm.read_fields()[0], om.fields()[0]) <= TOL[store]
+
+
+def test_taylor_green_3d_copy_fp32():
+    """Config 3 on its 48 x 48 x 36 copy (same Ma = 0.3 and Re = 1600, 188 steps = the same
+    convective time as 1000 steps at 256 x 256 x 192): FP32 kernel against the FP64 oracle."""
+    wl = W.taylor_green_3d(n=(48, 48, 36), steps=188)
+    om, gm = workload_pair(wl, store="f32")
+    om.step(wl.steps)
+    gm.step(wl.steps)
+    r_g, u_g = gm.read_fields()
+    r_o, u_o = om.fields()
+    assert rel_l2(u_g, u_o) <= 1e-5
+    assert rel_l2(r_g, r_o) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q25", "rD3Q33", "rD3Q53"])
+def test_minimal_grid_wraps(name):
+    """Smallest allowed grid (every extent equal to the largest velocity component): every pull
+    wraps around the periodic box."""
+    spec = W.LATTICES[name]
+    rm = 3 if spec.kind in ("rD2Q17", "rD2Q21", "rD2Q25") else 2
+    n = (rm,) * spec.d
+    s = _random_rates(spec.R, 9)
+    om = oracle_model(spec, "nse", n, s, 1.1)
+    gm = gpu_model(spec, "nse", n, s, 1.1, store="f64")
+    f0 = I.random_populations(n, om.lat.Q, seed=4)
+    om.set_populations(f0)
+    gm.set_populations(f0)
+    om.step(3)
+    gm.step(3)
+    assert rel_l2(gm.get_populations(), om.f) <= 1e-12
+
+
+def test_invalid_arguments_are_rejected():
+    """Bad arguments return an error status on the host; no kernel runs."""
+    from paper_2512_16230_gb300 import lbm
+    spec = W.LATTICES["rD3Q53"]
+    lat = gpu_lattice(spec)
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        lbm.Model(lat, "nse", (1, 8, 8))
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        lbm.Lattice("rD3Q53", spec.c, spec.cs2, ())
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        lbm.Lattice("rD2Q13", (1.0, -1.0), (0.8, 0.8))
+    m = lbm.Model(lat, "nse", (8, 8, 8))
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        m.set_relaxation(np.full(20, 2.5))
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        m.set_force(0, 5, 1.0, 1)
+    m.step(0)
+    assert m.counters() == (0, 0)
+
+
+def test_infeasible_lattice_is_reported():
+    """rD2Q13 outside 1/3 < d0 < 1 (Eq. (Q13lattice)): a Hermite norm is not positive."""
+    from paper_2512_16230_gb300 import lbm
+    with pytest.raises(lbm.LBMError, match="LATTICE_INFEASIBLE"):
+        lbm.Lattice("rD2Q13", (1.0, 1.0), (0.2, 0.2))
+    # rD3Q53 on dz/dx = 4/3 with one shared sound speed: the corrected H_zzz has N < 0
+    spec = W.RD3Q53_SHARED_CS
+    with pytest.raises(lbm.LBMError, match="LATTICE_INFEASIBLE"):
+        lbm.Lattice(spec.kind, spec.c, spec.cs2, spec.free_w)
+
+
+def test_steps_are_deterministic():
+    spec = W.LATTICES["rD3Q53"]
+    n = RAGGED[3]
+    runs = []
+    for _ in range(2):
+        gm = gpu_model(spec, "nse", n, _random_rates(spec.R, 5), store="f32")
+        gm.set_populations(round_to_store(I.random_populations(n, 53, seed=1), "f32"))
+        gm.step(5)
+        runs.append((gm.get_populations(), gm.conserved_sums()))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[0][1], runs[1][1])

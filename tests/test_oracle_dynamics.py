@@ -27,7 +27,7 @@ LATS = {
     "rD2Q21": ((1.0, 4.0 / 3.0), (0.8, 0.8), (7.29e-4,) * 3),
     "rD2Q17": ((1.0, 4.0 / 3.0), (0.8, 0.8), (2.1875e-3,)),
     "rD2Q13": ((1.0, 1.25), (0.8, 0.8), ()),
-    "rD3Q53": ((1.0, 1.0, 4.0 / 3.0), (0.624,) * 3, (2.9625e-4,)),
+    "rD3Q53": ((1.0, 1.0, 4.0 / 3.0), (0.96, 0.96, 1.28), (8e-4,)),
     "rD3Q45": ((1.0, 1.0, 1.0), (0.6,) * 3, ()),
     "rD3Q33": ((1.0, 1.0, 1.0), (0.5,) * 3, ()),
 }
@@ -77,10 +77,10 @@ def test_equilibrium_moments(kind, aniso):
         assert np.allclose(_mono(lat.cvel, (a, b, g)) @ feq, M3[a, b, g], rtol=0, atol=1e-13)
 
 
-@pytest.mark.parametrize("kind", list(LATS))
+@pytest.mark.parametrize("kind", [k for k in LATS if len(set(LATS[k][1])) == 1] + ["rD3Q53-cubic"])
 def test_equilibrium_at_rest(kind):
     """f^eq(rho, u = 0) = w rho when every c_sa^2 equals p / rho."""
-    lat = lattice(kind)
+    lat = L.build("rD3Q53", (1.0, 1.0, 1.0), (0.6,) * 3, (2.4e-4,)) if kind == "rD3Q53-cubic" else lattice(kind)
     n = (4,) * lat.d
     rho = 1.0 + I.random_scalar(n, seed=1, lo=-0.1, hi=0.1)
     m = M.Model(lat, "nse", n, np.ones(lat.R))
@@ -392,11 +392,42 @@ def _tgv3d_rate_error(nx):
 
 
 def test_taylor_green_3d_decay_rd3q53():
-    """rD3Q53 on a rectangular 3D grid (dz/dx = 4/3, the negative weights of the shared-c_s
-    setting): at low Mach and Reynolds number the kinetic energy decays at 2 nu |k|^2 with
-    |k|^2 = 3 k^2 and nu = cs2 (1/s_nu - 1/2), converging at second order (16 and 32 cells per
-    wavelength). The window starts after the start-up transient, which decays like (1 - s_nu)^n."""
+    """rD3Q53 on a rectangular 3D grid (dz/dx = 4/3, per-axis c_sa of Remark 2): at low Mach and Reynolds number the kinetic energy decays at 2 nu |k|^2 with
+    |k|^2 = 3 k^2 and nu = cs2_eq (1/s_nu - 1/2), converging at least at second order (16 and 32
+    cells per wavelength). The window starts after the start-up transient, which decays like
+    (1 - s_nu)^n."""
     e16 = _tgv3d_rate_error(16)
     e32 = _tgv3d_rate_error(32)
-    assert abs(e16) < 5e-2
-    assert 3.5 < e16 / e32 < 4.5
+    assert abs(e16) < 6e-2
+    assert abs(e32) < 1e-2
+    assert e16 / e32 > 3.5
+
+
+def _sine_decay_rate(nonlin, background):
+    c, cs2, _ = LATS["rD2Q13"]
+    lat = L.build("rD2Q13", c, cs2)
+    K = 0.05
+    s = np.ones(lat.R)
+    s[1:3] = 1.0 / (K / cs2[0] + 0.5)
+    n = (32, 3)
+    m = M.Model(lat, "ncde", n, s, 1.0, u_const=np.zeros(2), nonlin=nonlin)
+    x = I.coords(n, c)[0]
+    k = 2 * math.pi / (n[0] * c[0])
+    m.init_fields(background + 1e-4 * np.sin(k * x))
+
+    def amp():
+        return np.sum((m.fields()[0] - background) * np.sin(k * x)) / np.sum(np.sin(k * x) ** 2)
+
+    m.step(30)
+    a0 = amp()
+    m.step(200)
+    return math.log(a0 / amp()) / 200.0
+
+
+@pytest.mark.parametrize("background", [0.5, 1.0])
+def test_ncde_nonlinear_diffusivity(background):
+    """Eq. (GNCDE) with D(phi) = phi + phi^3/3 (Eq. (M-NCDE-6)): a small perturbation of a
+    uniform background phi0 diffuses with K (1 + phi0^2), i.e. the decay rate of a sine wave is
+    (1 + phi0^2) times its rate in the linear model."""
+    ratio = _sine_decay_rate(1.0, background) / _sine_decay_rate(0.0, background)
+    assert abs(ratio / (1 + background ** 2) - 1) < 2e-3

@@ -296,13 +296,23 @@ def test_special_d2q21_correction_closed_form(c, cs2, w9):
 
 
 def test_workload_weights_sign():
-    """The workload parameter choices: all weights positive on the 2D lattices and on the cubic
-    3D serving lattices; on rD3Q53 with dz/dx = 4/3 and one shared c_s (c_s^2 = 0.624,
-    w45 = 2.96e-4) no all-positive setting exists and the minimum weight is about -2.0e-3."""
+    """The workload parameter choices: all weights positive on the 2D lattices, on the cubic 3D
+    serving lattices and on rD3Q53 with dz/dx = 4/3 and per-axis sound speeds (Remark 2)."""
     for kind, c, cs2, fw in POINTS[:1] + POINTS[2:5]:
         assert L.build(kind, c, cs2, fw).w.min() > 0
     assert L.build("rD3Q53", (1, 1, 1), (0.6,) * 3, (2.4e-4,)).w.min() > 0
     assert L.build("rD3Q45", (1, 1, 1), (0.6,) * 3).w.min() > 0
     assert L.build("rD3Q33", (1, 1, 1), (0.5,) * 3).w.min() > 0
-    wmin = L.build("rD3Q53", (1, 1, 4.0 / 3.0), (0.624,) * 3, (2.96e-4,)).w.min()
-    assert -2.1e-3 < wmin < -1.9e-3
+    lat = L.build("rD3Q53", (1, 1, 4.0 / 3.0), (0.96, 0.96, 1.28), (8e-4,))
+    assert lat.w.min() > 7.9e-4
+    assert np.sum(lat.w * lat.H ** 2, axis=1).min() > 0
+
+
+def test_shared_sound_speed_rd3q53_is_indefinite():
+    """With dz/dx = 4/3 and one shared c_s the App. D weights cannot all be positive: the max-min
+    choice (c_s^2 = 0.624, w45 = 2.96e-4) leaves a minimum weight of about -2.0e-3 and the
+    corrected H_zzz row gets a negative W-norm, so H W H^T is diagonal but indefinite."""
+    lat = L.build("rD3Q53", (1, 1, 4.0 / 3.0), (0.624,) * 3, (2.9625e-4,))
+    assert -2.1e-3 < lat.w.min() < -1.9e-3
+    N = np.sum(lat.w * lat.H ** 2, axis=1)
+    assert N[19] < 0 and np.all(N[:19] > 0)
