@@ -38,8 +38,9 @@ GRID = (256, 256, 192)
 Q = 53
 STORE_BYTES = 4
 PROFILE = os.path.join(ROOT, "profiles", "k_step_rd3q53_f32_tgv3d_256x256x192.md")
-CPU_SAMPLE_GRID = (256, 256, 8)
-CPU_SAMPLE_STEPS = 2
+CPU_SAMPLE_GRID = (256, 256, 16)    # cpu_baseline: ~10-30 s of oracle work on the GPU machine
+CPU_SAMPLE_STEPS = 8
+REF_BUDGET_S = 150.0                  # --impl reference: wall-clock budget for W + K sample steps
 
 
 def _workload(grid=GRID):
@@ -196,16 +197,72 @@ def run_cpu_baseline(threads=None):
                        f"grid ({out['seconds']:.1f} s; BLAS threads = cores)")}
 
 
+def reference_worker(steps, warmup, budget_s):
+    """The reference arm: the FP64 oracle, as it stands, advancing a slab of the benchmark grid by
+    one time step per benchmark step. The slab is sized from a one-step calibration so that the
+    W + K steps fit the budget. Prints one JSON object."""
+    from oracle import lattice as OL
+    from oracle import mrt as OM
+    from paper_2512_16230_gb300 import inputs as I
+    from paper_2512_16230_gb300 import workloads as W
+    wl = W.taylor_green_3d(n=GRID, steps=1)
+    spec = wl.lattice
+    lat = OL.build(spec.kind, spec.c, spec.cs2, spec.free_w)
+
+    def slab(nz):
+        n = (GRID[0], GRID[1], nz)
+        m = OM.Model(lat, "nse", n, wl.s, wl.s_high)
+        rho, u = I.taylor_green_3d(n, spec.c, wl.init["u0"], 1.0, spec.cs2[0])
+        m.init_fields(rho, u)
+        return n, m
+
+    n, m = slab(2)
+    t0 = time.perf_counter()
+    m.step(1)
+    per_cell = (time.perf_counter() - t0) / math.prod(n)
+    cells = max(2 * 2 * 2, int(budget_s / max(steps + warmup, 1) / per_cell))
+    nz, ny = 2, GRID[1]
+    while GRID[0] * ny * nz * 2 <= cells and nz < GRID[2]:
+        nz *= 2
+    while GRID[0] * ny * nz > cells and ny > 2:
+        ny //= 2
+    n = (GRID[0], ny, nz)
+    m = OM.Model(lat, "nse", n, wl.s, wl.s_high)
+    rho, u = I.taylor_green_3d(n, spec.c, wl.init["u0"], 1.0, spec.cs2[0])
+    m.init_fields(rho, u)
+    m.step(warmup)
+    t0 = time.perf_counter()
+    m.step(steps)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"mlups": math.prod(n) * steps / dt / 1e6, "seconds": dt, "n": list(n)}))
+
+
 def bench_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    base = run_cpu_baseline()
-    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic Taylor-Green initial field)",
+    threads = os.cpu_count() or 1
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = str(threads)
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"bench.reference_worker({args.steps}, {args.warmup}, {REF_BUDGET_S})")
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if res.returncode != 0:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + res.stderr[-300:]}))
+        return
+    out = json.loads(res.stdout.strip().splitlines()[-1])
+    n = out["n"]
+    sample = (f"FP64 numpy oracle, {args.warmup} + {args.steps} time steps of the rD3Q53 Taylor-Green workload "
+              f"on a {n[0]}x{n[1]}x{n[2]} periodic block of the benchmark grid per benchmark step "
+              f"({out['seconds']:.1f} s timed, BLAS threads = {threads})")
+    base = {"value": out["mlups"], "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+    line = {"impl": "reference", "metric": METRIC, "value": out["mlups"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * out["seconds"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (analytic Taylor-Green initial field)",
             "config": _config({"reference": "FP64 numpy oracle on the host cores (the paper has no code)"}),
-            "cpu_baseline": base, "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+            "cpu_baseline": base, "e2e": {"value": out["mlups"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
