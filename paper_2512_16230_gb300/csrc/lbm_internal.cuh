@@ -51,7 +51,11 @@ struct lbm_model {
 
 namespace lbm {
 
-constexpr int kBlock = 128;          // threads per block of the cell kernels
+// Launch shape of the cell kernels (tuned on GB300; see the kernel notes in mrt_kernels.cuh).
+#ifndef LBM_K1_BLOCK
+#define LBM_K1_BLOCK 128
+#endif
+constexpr int kBlock = LBM_K1_BLOCK;  // threads per block of the cell kernels
 constexpr int kRedBlocks = 608;      // blocks of the conservation-sum reduction (4 x 152 SMs)
 
 // Kernel parameters of the time step, passed by value (they live in the constant bank, so
