@@ -192,6 +192,19 @@ lbm_status lbm_model_read_fields(lbm_model* m, double* rho_or_phi, double* u, in
  * Synchronous. Returns LBM_ERR_NONFINITE (with the sums still written) if any is NaN/inf. */
 lbm_status lbm_model_conserved_sums(lbm_model* m, double* out_host);
 
+/* The same sums for callers that may not allocate device memory (graph capture, fixed-budget or
+ * pool-managed device memory, out-of-memory diagnostics). The paper has no counterpart: this is
+ * an interface variant of lbm_model_conserved_sums. Allocates nothing and synchronizes nothing:
+ * the reduction scratch is a static device array of 608 x 4 doubles (19,456 bytes) resident on
+ * every GPU that loads the library, the result goes to out_dev[4] (device memory, caller-owned,
+ * out_dev[0] = mass, out_dev[1 + a] = momentum, unused entries 0), asynchronously on the model's
+ * stream. The first call on each device looks up the array's address (and may load device code):
+ * make it before any stream capture. All calls share the array and every call rewrites the slots
+ * it reads, so no clearing is needed, but calls whose kernels overlap on the GPU race on it.
+ * The reduction never needs more than the 608 slots; a build whose reduction grid exceeds the
+ * array is rejected with LBM_ERR_ARG. Non-finite sums are not detected (no host read). */
+lbm_status lbm_model_conserved_sums_noalloc(lbm_model* m, double* out_dev);
+
 /* Completed time steps since the last init/set; kernels launched by this model so far. */
 lbm_status lbm_model_counters(const lbm_model* m, int64_t* steps, int64_t* launches);
 

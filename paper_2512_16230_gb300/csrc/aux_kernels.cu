@@ -255,4 +255,19 @@ lbm_status launch_sums(lbm_model* m) {
   });
 }
 
+lbm_status launch_sums_into(lbm_model* m, double* partials, int partial_slots, double* out) {
+  if (partial_slots < kRedBlocks) return set_error(LBM_ERR_ARG, "reduction scratch too small");
+  GenParams p;
+  gen_params(m, &p);
+  return dispatch_store(m, [&](auto st, auto ct) {
+    using ST = decltype(st);
+    using CT = decltype(ct);
+    k_sums_partial<ST, CT><<<kRedBlocks, 256, 0, m->stream>>>(p, static_cast<const ST*>(m->f[m->cur]), partials);
+    lbm_status s = after_launch(m, "sums launch");
+    if (s != LBM_OK) return s;
+    k_sums_final<<<1, 128, 0, m->stream>>>(partials, kRedBlocks, out);
+    return after_launch(m, "sums final launch");
+  });
+}
+
 }  // namespace lbm

@@ -139,6 +139,9 @@ lbm_status launch_scatter(lbm_model* m, const double* in);    // stored array fr
 lbm_status launch_fields(lbm_model* m, double* rho, double* u);
 lbm_status launch_sums(lbm_model* m);                          // into m->sums (device)
 lbm_status launch_phi_from_populations(lbm_model* m);          // NCDE: phi_prev = sum f-bar
+// The conservation-sum kernels with caller-provided reduction scratch (partial_slots x 4
+// doubles, at least kRedBlocks slots) and result (4 doubles, device memory).
+lbm_status launch_sums_into(lbm_model* m, double* partials, int partial_slots, double* out);
 
 // FP64 lattice set-up on the GPU (setup_fp64.cu).
 lbm_status setup_lattice_fp64(lbm_lattice* lat);

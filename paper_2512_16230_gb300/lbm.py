@@ -51,6 +51,7 @@ SIGNATURES = {
     "lbm_model_stream_only": (c_int, [_P, c_int64]),
     "lbm_model_read_fields": (c_int, [_P, _P, _P, c_int]),
     "lbm_model_conserved_sums": (c_int, [_P, _PD]),
+    "lbm_model_conserved_sums_noalloc": (c_int, [_P, _P]),
     "lbm_model_counters": (c_int, [_P, _PI64, _PI64]),
     "lbm_model_synchronize": (c_int, [_P]),
     "lbm_model_destroy": (c_int, [_P]),
@@ -268,6 +269,15 @@ class Model:
         out = (c_double * 4)()
         _check(load().lbm_model_conserved_sums(self.handle, out), "lbm_model_conserved_sums")
         return np.array(out[: 1 + self.d])
+
+    def conserved_sums_noalloc(self, out):
+        """Sums into ``out`` (a torch CUDA float64 tensor of 4 elements) without any device
+        allocation; asynchronous on the model's stream."""
+        p, dev, _ = _ptr(out)
+        if not dev or out.numel() < 4:
+            raise ValueError("out must be a torch CUDA float64 tensor with 4 elements")
+        _check(load().lbm_model_conserved_sums_noalloc(self.handle, c_void_p(p)), "lbm_model_conserved_sums_noalloc")
+        return out
 
     def counters(self):
         s, l = c_int64(), c_int64()
