@@ -157,6 +157,22 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_max(value, ws, device=None):
+    """Max of a float over the ranks of the default process group (identity for one rank)."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank, steps, ws, seconds_max):
+    """Whole-job MLUPS: every rank advances its own replica, timed by the slowest rank."""
+    return cells_per_rank * steps * ws / seconds_max / 1e6
+
+
 def cpu_baseline_worker(nx, ny, nz, steps):
     """Time the FP64 oracle, as it stands, on a slab of the benchmark grid (run in a fresh
     process; prints one JSON object)."""
@@ -320,11 +336,8 @@ def bench_ours(args):
     _, launches1 = model.counters()
     ms = start.elapsed_time(end)
     sums = model.conserved_sums()
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = cells * args.steps * ws / (ms_max / 1e3) / 1e6
+    ms_max = reduce_max(ms, ws, dev)
+    value = job_throughput(cells, args.steps, ws, ms_max / 1e3)
     launch_ms = ms / args.steps
 
     # end to end through the public API: pinned host fields in, K steps, pinned host fields out
@@ -339,10 +352,7 @@ def bench_ours(args):
     model.read_fields(rho_o.numpy(), u_o.numpy())
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = cells * args.steps * ws / float(e2e_t.item()) / 1e6
+    e2e_value = job_throughput(cells, args.steps, ws, reduce_max(e2e_s, ws, dev))
     io_bytes = (rho_h.numel() + u_h.numel()) * 8
 
     if rank == 0:

@@ -8,9 +8,11 @@ namespace lbm {
 
 namespace {
 
+// Periodic wrap of a coordinate displaced by at most one grid extent (every extent is at least
+// the largest velocity component, checked at model creation).
 __device__ __forceinline__ int wrap(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
+  v += v < 0 ? n : 0;
+  return v >= n ? v - n : v;
 }
 
 __device__ __forceinline__ void coords(const GenParams& p, int cell, int& x, int& y, int& z) {
@@ -36,7 +38,8 @@ __device__ __forceinline__ int shifted(const GenParams& p, int x, int y, int z, 
 
 // f-bar_i(x) = A_i(x - e_i): the pre-collision populations from the stored array.
 template <class ST, class CT>
-__global__ void k_gather(const GenParams p, const ST* __restrict__ A, double* __restrict__ out) {
+__global__ void k_gather(const GenParams p, const GenTables<CT> t, const ST* __restrict__ A,
+                         double* __restrict__ out) {
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= p.ncells) return;
   int x, y, z;
@@ -44,13 +47,14 @@ __global__ void k_gather(const GenParams p, const ST* __restrict__ A, double* __
   const size_t N = size_t(p.ncells);
   for (int i = 0; i < p.Q; ++i) {
     const int src = shifted(p, x, y, z, i, -1);
-    out[size_t(i) * N + cell] = double(Codec<ST>::template dec<CT>(A[size_t(i) * N + src], CT(p.wref[i])));
+    out[size_t(i) * N + cell] = double(Codec<ST>::template dec<CT>(A[size_t(i) * N + src], t.wref[i]));
   }
 }
 
 // A_i(x - e_i) = f-bar_i(x)
 template <class ST, class CT>
-__global__ void k_scatter(const GenParams p, const double* __restrict__ in, ST* __restrict__ A) {
+__global__ void k_scatter(const GenParams p, const GenTables<CT> t, const double* __restrict__ in,
+                          ST* __restrict__ A) {
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= p.ncells) return;
   int x, y, z;
@@ -58,14 +62,14 @@ __global__ void k_scatter(const GenParams p, const double* __restrict__ in, ST* 
   const size_t N = size_t(p.ncells);
   for (int i = 0; i < p.Q; ++i) {
     const int dst = shifted(p, x, y, z, i, -1);
-    A[size_t(i) * N + dst] = Codec<ST>::template enc<CT>(CT(in[size_t(i) * N + cell]), CT(p.wref[i]));
+    A[size_t(i) * N + dst] = Codec<ST>::template enc<CT>(CT(in[size_t(i) * N + cell]), t.wref[i]);
   }
 }
 
 // Eq. (2-4-2): rho = sum f, u = (sum c f + F/2) / rho; Eq. (2-4-1): phi = sum f.
 // Computed in the model's compute dtype from the gathered f-bar.
 template <class ST, class CT>
-__global__ void k_fields(const GenParams p, const ST* __restrict__ A, int nse,
+__global__ void k_fields(const GenParams p, const GenTables<CT> t, const ST* __restrict__ A, int nse,
                          double* __restrict__ rho_out, double* __restrict__ u_out) {
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= p.ncells) return;
@@ -75,9 +79,11 @@ __global__ void k_fields(const GenParams p, const ST* __restrict__ A, int nse,
   CT rho = CT(0), j[3] = {CT(0), CT(0), CT(0)};
   for (int i = 0; i < p.Q; ++i) {
     const int src = shifted(p, x, y, z, i, -1);
-    const CT f = Codec<ST>::template dec<CT>(A[size_t(i) * N + src], CT(p.wref[i]));
+    const CT f = Codec<ST>::template dec<CT>(A[size_t(i) * N + src], t.wref[i]);
     rho += f;
-    for (int a = 0; a < p.d; ++a) j[a] = fma(CT(p.c[a] * p.e[i][a]), f, j[a]);
+    j[0] = fma(t.ce[i][0], f, j[0]);
+    j[1] = fma(t.ce[i][1], f, j[1]);
+    j[2] = fma(t.ce[i][2], f, j[2]);
   }
   rho_out[cell] = double(rho);
   if (!nse || u_out == nullptr) return;
@@ -91,7 +97,7 @@ __global__ void k_fields(const GenParams p, const ST* __restrict__ A, int nse,
 
 // NCDE: phi_prev(x) = sum_i f-bar_i(x)
 template <class ST, class CT>
-__global__ void k_phi(const GenParams p, const ST* __restrict__ A, CT* __restrict__ phi) {
+__global__ void k_phi(const GenParams p, const GenTables<CT> t, const ST* __restrict__ A, CT* __restrict__ phi) {
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= p.ncells) return;
   int x, y, z;
@@ -99,7 +105,7 @@ __global__ void k_phi(const GenParams p, const ST* __restrict__ A, CT* __restric
   const size_t N = size_t(p.ncells);
   CT s = CT(0);
   for (int i = 0; i < p.Q; ++i)
-    s += Codec<ST>::template dec<CT>(A[size_t(i) * N + shifted(p, x, y, z, i, -1)], CT(p.wref[i]));
+    s += Codec<ST>::template dec<CT>(A[size_t(i) * N + shifted(p, x, y, z, i, -1)], t.wref[i]);
   phi[cell] = s;
 }
 
@@ -114,17 +120,19 @@ __device__ __forceinline__ double warp_sum(double v) {
 // order and writes its four partial sums. Streaming is a permutation, so the stored array has
 // the same totals as f-bar and needs no gather.
 template <class ST, class CT>
-__global__ void __launch_bounds__(256) k_sums_partial(const GenParams p, const ST* __restrict__ A,
-                                                      double* __restrict__ partials) {
+__global__ void __launch_bounds__(256) k_sums_partial(const GenParams p, const GenTables<CT> t,
+                                                      const ST* __restrict__ A, double* __restrict__ partials) {
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const size_t N = size_t(p.ncells);
   for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < p.ncells;
        cell += gridDim.x * blockDim.x) {
     CT m = CT(0), j[3] = {CT(0), CT(0), CT(0)};
     for (int i = 0; i < p.Q; ++i) {
-      const CT f = Codec<ST>::template dec<CT>(A[size_t(i) * N + cell], CT(p.wref[i]));
+      const CT f = Codec<ST>::template dec<CT>(A[size_t(i) * N + cell], t.wref[i]);
       m += f;
-      for (int a = 0; a < p.d; ++a) j[a] = fma(CT(p.c[a] * p.e[i][a]), f, j[a]);
+      j[0] = fma(t.ce[i][0], f, j[0]);
+      j[1] = fma(t.ce[i][1], f, j[1]);
+      j[2] = fma(t.ce[i][2], f, j[2]);
     }
     acc[0] += double(m);
     for (int a = 0; a < 3; ++a) acc[1 + a] += double(j[a]);
@@ -163,6 +171,16 @@ lbm_status dispatch_store(const lbm_model* m, F&& f) {
   return set_error(LBM_ERR_ARG, "unknown storage dtype");
 }
 
+template <class CT>
+GenTables<CT> gen_tables(const GenParams& p) {
+  GenTables<CT> t{};
+  for (int i = 0; i < p.Q; ++i) {
+    for (int a = 0; a < 3; ++a) t.ce[i][a] = a < p.d ? CT(p.c[a] * p.e[i][a]) : CT(0);
+    t.wref[i] = CT(p.wref[i]);
+  }
+  return t;
+}
+
 lbm_status after_launch(lbm_model* m, const char* what) {
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_error(err, what);
@@ -197,7 +215,7 @@ lbm_status launch_gather(lbm_model* m, double* out) {
   return dispatch_store(m, [&](auto st, auto ct) {
     using ST = decltype(st);
     using CT = decltype(ct);
-    k_gather<ST, CT><<<grid, 128, 0, m->stream>>>(p, static_cast<const ST*>(m->f[m->cur]), out);
+    k_gather<ST, CT><<<grid, 128, 0, m->stream>>>(p, gen_tables<CT>(p), static_cast<const ST*>(m->f[m->cur]), out);
     return after_launch(m, "gather launch");
   });
 }
@@ -209,7 +227,7 @@ lbm_status launch_scatter(lbm_model* m, const double* in) {
   return dispatch_store(m, [&](auto st, auto ct) {
     using ST = decltype(st);
     using CT = decltype(ct);
-    k_scatter<ST, CT><<<grid, 128, 0, m->stream>>>(p, in, static_cast<ST*>(m->f[m->cur]));
+    k_scatter<ST, CT><<<grid, 128, 0, m->stream>>>(p, gen_tables<CT>(p), in, static_cast<ST*>(m->f[m->cur]));
     return after_launch(m, "scatter launch");
   });
 }
@@ -221,7 +239,7 @@ lbm_status launch_fields(lbm_model* m, double* rho, double* u) {
   return dispatch_store(m, [&](auto st, auto ct) {
     using ST = decltype(st);
     using CT = decltype(ct);
-    k_fields<ST, CT><<<grid, 128, 0, m->stream>>>(p, static_cast<const ST*>(m->f[m->cur]),
+    k_fields<ST, CT><<<grid, 128, 0, m->stream>>>(p, gen_tables<CT>(p), static_cast<const ST*>(m->f[m->cur]),
                                                     m->eq == LBM_NSE ? 1 : 0, rho, u);
     return after_launch(m, "fields launch");
   });
@@ -234,7 +252,7 @@ lbm_status launch_phi_from_populations(lbm_model* m) {
   return dispatch_store(m, [&](auto st, auto ct) {
     using ST = decltype(st);
     using CT = decltype(ct);
-    k_phi<ST, CT><<<grid, 128, 0, m->stream>>>(p, static_cast<const ST*>(m->f[m->cur]),
+    k_phi<ST, CT><<<grid, 128, 0, m->stream>>>(p, gen_tables<CT>(p), static_cast<const ST*>(m->f[m->cur]),
                                                  static_cast<CT*>(m->phi_prev));
     return after_launch(m, "phi launch");
   });
@@ -247,7 +265,7 @@ lbm_status launch_sums(lbm_model* m) {
     using ST = decltype(st);
     using CT = decltype(ct);
     k_sums_partial<ST, CT><<<kRedBlocks, 256, 0, m->stream>>>(
-        p, static_cast<const ST*>(m->f[m->cur]), m->partials);
+        p, gen_tables<CT>(p), static_cast<const ST*>(m->f[m->cur]), m->partials);
     lbm_status s = after_launch(m, "sums launch");
     if (s != LBM_OK) return s;
     k_sums_final<<<1, 128, 0, m->stream>>>(m->partials, kRedBlocks, m->sums);
@@ -262,7 +280,7 @@ lbm_status launch_sums_into(lbm_model* m, double* partials, int partial_slots, d
   return dispatch_store(m, [&](auto st, auto ct) {
     using ST = decltype(st);
     using CT = decltype(ct);
-    k_sums_partial<ST, CT><<<kRedBlocks, 256, 0, m->stream>>>(p, static_cast<const ST*>(m->f[m->cur]), partials);
+    k_sums_partial<ST, CT><<<kRedBlocks, 256, 0, m->stream>>>(p, gen_tables<CT>(p), static_cast<const ST*>(m->f[m->cur]), partials);
     lbm_status s = after_launch(m, "sums launch");
     if (s != LBM_OK) return s;
     k_sums_final<<<1, 128, 0, m->stream>>>(partials, kRedBlocks, out);

@@ -87,6 +87,14 @@ struct GenParams {
   const void* force_tab;
 };
 
+// Per-velocity tables of the generic kernels in their compute dtype (c_ia and w_i rho_ref), so
+// that no FP64 arithmetic runs per population when the model computes in FP32.
+template <class CT>
+struct GenTables {
+  CT ce[kMaxQ][3];
+  CT wref[kMaxQ];
+};
+
 // Storage codecs: FP64/FP32 store f itself; BF16/FP16 store the deviation f - w_i rho_ref.
 template <class ST>
 struct Codec;
