@@ -114,6 +114,51 @@ constexpr int max_component() {
   return m;
 }
 
+// Primitive directions: every velocity is e = m d with d primitive (components coprime, first
+// non-zero component positive) and m in {+-1, +-2, +-3}. Since mono_k(m d) = m^deg(k) mono_k(d),
+// the populations of one direction can be combined per degree before the monomial products.
+constexpr int iabs(int v) { return v < 0 ? -v : v; }
+constexpr int gcd2(int a, int b) { return b == 0 ? a : gcd2(b, a % b); }
+constexpr Vel primitive(Vel v) {
+  const int g = gcd2(gcd2(iabs(v.x), iabs(v.y)), iabs(v.z));
+  const Vel p{v.x / g, v.y / g, v.z / g};
+  const int lead = p.x != 0 ? p.x : (p.y != 0 ? p.y : p.z);
+  return lead < 0 ? Vel{-p.x, -p.y, -p.z} : p;
+}
+constexpr bool same_vel(Vel a, Vel b) { return a.x == b.x && a.y == b.y && a.z == b.z; }
+
+template <class L>
+constexpr int num_directions() {
+  int n = 0;
+  for (int i = 1; i < L::Q; ++i) {
+    bool seen = false;
+    for (int j = 1; j < i; ++j) seen = seen || same_vel(primitive(L::e(j)), primitive(L::e(i)));
+    n += seen ? 0 : 1;
+  }
+  return n;
+}
+// k-th primitive direction, in order of first appearance in the velocity table
+template <class L>
+constexpr Vel direction(int k) {
+  int n = 0;
+  for (int i = 1; i < L::Q; ++i) {
+    bool seen = false;
+    for (int j = 1; j < i; ++j) seen = seen || same_vel(primitive(L::e(j)), primitive(L::e(i)));
+    if (!seen) {
+      if (n == k) return primitive(L::e(i));
+      ++n;
+    }
+  }
+  return Vel{0, 0, 0};
+}
+// index of the velocity m d, or -1 if the lattice does not have it
+template <class L>
+constexpr int velocity_index(Vel d, int m) {
+  for (int i = 0; i < L::Q; ++i)
+    if (same_vel(L::e(i), Vel{m * d.x, m * d.y, m * d.z})) return i;
+  return -1;
+}
+
 // static_for<N>(f) calls f(std::integral_constant<int, 0>) ... f(integral_constant<int, N-1>).
 // Inside nested lambdas, read a captured index as decltype(i)::value (a constant expression
 // whatever the capture); the constexpr helpers above are evaluated at compile time only.

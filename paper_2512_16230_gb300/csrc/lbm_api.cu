@@ -55,6 +55,7 @@ void make_step_params(const lbm_model* m, StepParams<CT>* p) {
     p->n[a] = a < L->d ? int(m->n[a]) : 1;
   }
   p->ncells = m->ncells;
+  for (int a = 0; a < 2; ++a) division_magic(unsigned(p->n[a] > 1 ? p->n[a] : 2), &p->div_m[a], &p->div_s[a]);
   const bool force = m->eq == LBM_NSE && m->force_A != 0.0;
   p->force_a = force ? m->force_a : 0;
   p->force_b = force ? m->force_b : -1;

@@ -73,9 +73,20 @@ struct StepParams {
   CT u_const[3];
   int n[3];
   int ncells;
+  unsigned div_m[2];     // cell index -> (x, y, z): q = umulhi(v, div_m) >> div_s exactly divides
+  int div_s[2];          // by n[0] (slot 0) and n[1] (slot 1) for every v < 2^31
   int force_a, force_b;  // force_b < 0: no body force
   const CT* force_tab;
 };
+
+// Multiply-high division by a runtime divisor 2 <= d < 2^31, exact for numerators below 2^31:
+// with s = ceil(log2 d) and m = ceil(2^(31+s) / d) < 2^32, floor(v / d) = (v m / 2^32) >> (s-1).
+inline void division_magic(unsigned d, unsigned* m, int* shift) {
+  int s = 0;
+  while ((1ull << s) < d) ++s;
+  *m = unsigned(((1ull << (31 + s)) + d - 1) / d);
+  *shift = s - 1;
+}
 
 // Parameters of the generic (lattice-agnostic, non-hot) kernels.
 struct GenParams {

@@ -76,25 +76,42 @@ __host__ __device__ constexpr int axis_n(Mono m, int n) {
   return n < m.a ? 0 : (n < m.a + m.b ? 1 : 2);
 }
 
-// Raw moments mu_k = sum_i mono_k(e_i) f_i, k < R, pairing e and -e.
+// Raw moments mu_k = sum_i mono_k(e_i) f_i, k < R. Per primitive direction d the populations of
+// +-m d are first combined per degree (s_deg = sum_m m^deg (f_md +- f_-md), + for even degree,
+// - for odd), then mu_k += mono_k(d) s_deg(k): zero products vanish at compile time and each
+// monomial product is shared by every speed of the direction.
+template <int DEG, class CT>
+__device__ __forceinline__ CT pick_degree(CT s0, CT s1, CT s2, CT s3) {
+  if constexpr (DEG == 0) return s0;
+  else if constexpr (DEG == 1) return s1;
+  else if constexpr (DEG == 2) return s2;
+  else return s3;
+}
+
 template <class L, class CT>
 __device__ __forceinline__ void raw_moments(const CT (&f)[L::Q], CT (&mu)[L::R]) {
   static_for<L::R>([&](auto k) { mu[decltype(k)::value] = CT(0); });
   mu[0] = f[0];
-  static_for<L::Q>([&](auto i) {
-    constexpr int I = decltype(i)::value;
-    if constexpr (I > 0 && I < opposite<L>(I)) {
-      const CT sp = f[I] + f[opposite<L>(I)];
-      const CT sm = f[I] - f[opposite<L>(I)];
-      static_for<L::R>([&](auto k) {
-        constexpr int K = decltype(k)::value;
-        constexpr int cv = mono_value(L::e(decltype(i)::value), mono<L::D>(K));
-        if constexpr (cv != 0) {
-          if constexpr (degree(mono<L::D>(K)) % 2 == 0) mu[K] = axpy_c<cv>(sp, mu[K]);
-          else mu[K] = axpy_c<cv>(sm, mu[K]);
-        }
-      });
-    }
+  static_for<num_directions<L>()>([&](auto dk) {
+    CT s0 = CT(0), s1 = CT(0), s2 = CT(0), s3 = CT(0);
+    static_for<3>([&](auto mm) {
+      constexpr int M = decltype(mm)::value + 1;
+      constexpr int ip = velocity_index<L>(direction<L>(decltype(dk)::value), M);
+      constexpr int im = velocity_index<L>(direction<L>(decltype(dk)::value), -M);
+      if constexpr (ip >= 0) {
+        const CT sp = f[ip] + f[im];
+        const CT sm = f[ip] - f[im];
+        s0 += sp;
+        s1 = axpy_c<M>(sm, s1);
+        s2 = axpy_c<M * M>(sp, s2);
+        s3 = axpy_c<M * M * M>(sm, s3);
+      }
+    });
+    static_for<L::R>([&](auto k) {
+      constexpr int K = decltype(k)::value;
+      constexpr int cv = mono_value(direction<L>(decltype(dk)::value), mono<L::D>(K));
+      if constexpr (cv != 0) mu[K] = axpy_c<cv>(pick_degree<degree(mono<L::D>(K))>(s0, s1, s2, s3), mu[K]);
+    });
   });
 }
 
@@ -162,27 +179,34 @@ __device__ __forceinline__ CT hermite_eq(const StepParams<CT>& p, const CT (&me)
   else return row_dot<L, CT, r>(p, me);
 }
 
-// f_i = (1 - s_h) f_i + w_i sum_k mono_k(e_i) h_k  (h already scaled by D_k), e/-e paired.
+// f_i = (1 - s_h) f_i + w_i sum_k mono_k(e_i) h_k  (h already scaled by D_k). Per primitive
+// direction d: E_deg = sum_{deg(k) = deg} mono_k(d) h_k, then for every speed m present
+// f_{+-md} = (1 - s_h) f + w (E_0 + m^2 E_2 +- (m E_1 + m^3 E_3)).
 template <class L, class CT>
 __device__ __forceinline__ void back_project(CT (&f)[L::Q], const StepParams<CT>& p,
                                              const CT (&h)[L::R], CT oms) {
   f[0] = fma(oms, f[0], p.w[0] * h[0]);
-  static_for<L::Q>([&](auto i) {
-    constexpr int I = decltype(i)::value;
-    if constexpr (I > 0 && I < opposite<L>(I)) {
-      CT E = CT(0), O = CT(0);
-      static_for<L::R>([&](auto k) {
-        constexpr int K = decltype(k)::value;
-        constexpr int cv = mono_value(L::e(decltype(i)::value), mono<L::D>(K));
-        if constexpr (cv != 0) {
-          if constexpr (degree(mono<L::D>(K)) % 2 == 0) E = axpy_c<cv>(h[K], E);
-          else O = axpy_c<cv>(h[K], O);
-        }
-      });
-      constexpr int J = opposite<L>(I);
-      f[I] = fma(oms, f[I], p.w[I] * (E + O));
-      f[J] = fma(oms, f[J], p.w[J] * (E - O));
-    }
+  static_for<num_directions<L>()>([&](auto dk) {
+    CT E1 = CT(0), E2 = CT(0), E3 = CT(0);
+    static_for<L::R>([&](auto k) {
+      constexpr int K = decltype(k)::value;
+      constexpr int cv = mono_value(direction<L>(decltype(dk)::value), mono<L::D>(K));
+      constexpr int deg = degree(mono<L::D>(K));
+      if constexpr (cv != 0 && deg == 1) E1 = axpy_c<cv>(h[K], E1);
+      if constexpr (cv != 0 && deg == 2) E2 = axpy_c<cv>(h[K], E2);
+      if constexpr (cv != 0 && deg == 3) E3 = axpy_c<cv>(h[K], E3);
+    });
+    static_for<3>([&](auto mm) {
+      constexpr int M = decltype(mm)::value + 1;
+      constexpr int ip = velocity_index<L>(direction<L>(decltype(dk)::value), M);
+      constexpr int im = velocity_index<L>(direction<L>(decltype(dk)::value), -M);
+      if constexpr (ip >= 0) {
+        const CT even = axpy_c<M * M>(E2, h[0]);
+        const CT odd = (M == 1) ? E1 + E3 : fma(CT(M * M * M), E3, CT(M) * E1);
+        f[ip] = fma(oms, f[ip], p.w[ip] * (even + odd));
+        f[im] = fma(oms, f[im], p.w[im] * (even - odd));
+      }
+    });
   });
 }
 
@@ -316,38 +340,32 @@ struct Neigh {
   static constexpr int RM = L::RMAX;
   int xo[2 * RM + 1], yo[2 * RM + 1], zo[2 * RM + 1];
   int x, y, z;
-  __device__ __forceinline__ Neigh(int cell, const int (&n)[3]) {
-    const int nx = n[0], ny = n[1];
+  template <class CT>
+  __device__ __forceinline__ Neigh(int cell, const StepParams<CT>& p) {
+    const int nx = p.n[0], ny = p.n[1];
+    // the velocity components are at most RM <= every extent, so one wrap suffices and only on
+    // the side a displacement can cross
+    const int t = int(__umulhi(unsigned(cell), p.div_m[0]) >> p.div_s[0]);
+    x = cell - t * nx;
     if constexpr (L::D == 2) {
-      y = cell / nx;
-      x = cell - y * nx;
+      y = t;
       z = 0;
     } else {
-      const int t = cell / nx;
-      x = cell - t * nx;
-      z = t / ny;
+      z = int(__umulhi(unsigned(t), p.div_m[1]) >> p.div_s[1]);
       y = t - z * ny;
     }
 #pragma unroll
     for (int s = -RM; s <= RM; ++s) {
-      int xs = x - s;
-      xs += xs < 0 ? nx : 0;
-      xs -= xs >= nx ? nx : 0;
-      xo[s + RM] = xs;
-      int ys = y - s;
-      ys += ys < 0 ? ny : 0;
-      ys -= ys >= ny ? ny : 0;
-      yo[s + RM] = ys * nx;
-      if constexpr (L::D == 3) {
-        const int nz = n[2];
-        int zs = z - s;
-        zs += zs < 0 ? nz : 0;
-        zs -= zs >= nz ? nz : 0;
-        zo[s + RM] = zs * nx * ny;
-      } else {
-        zo[s + RM] = 0;
-      }
+      xo[s + RM] = wrap1(x - s, s, nx);
+      yo[s + RM] = wrap1(y - s, s, ny) * nx;
+      if constexpr (L::D == 3) zo[s + RM] = wrap1(z - s, s, p.n[2]) * nx * ny;
+      else zo[s + RM] = 0;
     }
+  }
+  __device__ __forceinline__ static int wrap1(int v, int s, int n) {
+    if (s > 0) return v < 0 ? v + n : v;
+    if (s < 0) return v >= n ? v - n : v;
+    return v;
   }
   // cell index of x - e (pull source) for a compile-time velocity
   template <int I>
@@ -383,7 +401,7 @@ __global__ void __launch_bounds__(kBlock, LBM_K1_MIN_BLOCKS) k_step(const StepPa
                                                  ST* __restrict__ fout, CT* __restrict__ phi) {
   const int cell = blockIdx.x * kBlock + threadIdx.x;
   if (cell >= p.ncells) return;
-  const Neigh<L> nb(cell, p.n);
+  const Neigh<L> nb(cell, p);
   const size_t N = size_t(p.ncells);
   CT f[L::Q];
   static_for<L::Q>([&](auto i) {
@@ -412,7 +430,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const StepParams<CT> p, const d
                                                  CT* __restrict__ phi) {
   const int cell = blockIdx.x * kBlock + threadIdx.x;
   if (cell >= p.ncells) return;
-  const Neigh<L> nb(cell, p.n);
+  const Neigh<L> nb(cell, p);
   const size_t N = size_t(p.ncells);
   const CT r = CT(rho_or_phi[cell]);
   CT uu[3] = {CT(0), CT(0), CT(0)};
