@@ -381,11 +381,43 @@ def bench_ours(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
-        print(json.dumps(line), flush=True)
     model.close()
+    del model
+    torch.cuda.empty_cache()
+    if args.serving_requests > 0:
+        serving = run_serving(args.serving_requests)
+        if rank == 0:
+            line["serving"] = serving
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_serving(n_requests, rate_per_s=20.0, seed=0):
+    """Config 5 on a prefix of the seeded request stream: continuous batching (16-bit requests in
+    FP16 deviation storage, tiles from the autotuner) against the plain FP32 one-solve-at-a-time
+    path, same requests and arrival times."""
+    from paper_2512_16230_gb300 import autotune
+    from paper_2512_16230_gb300 import inputs as I
+    from paper_2512_16230_gb300 import serve as S
+    reqs = I.serving_requests(n_requests, seed=seed, rate_per_s=rate_per_s)
+    tiles = autotune.autotune()
+    eng = S.GpuEngine(tiles=tiles)
+    rec_b, t_b = S.serve_batched(reqs, eng, budget_bytes=150e9, max_resident=512, tick=64)
+    launches_b = eng.batch.counters()["launches"]
+    eng.batch.close()
+    rec_s, t_s = S.serve_sequential(reqs, S.GpuEngine(), store="f32")
+    return {
+        "requests": n_requests, "arrival_rate_per_s": rate_per_s, "seed": seed,
+        "mix": "2D rD2Q17/21/25 Taylor-Green + NCDE (32..1024 x 32..768), 3D rD3Q33/45/53 Kolmogorov "
+               "(32^3..160^3), 200..5000 steps, half FP32 half 16-bit, Poisson arrivals",
+        "batched": dict(S.summarize(rec_b, t_b), storage="FP32 or FP16 deviations", batched_launches=launches_b,
+                        hbm_budget_gb=150, peak_resident_gb=S.serve_batched.peak_bytes / 1e9),
+        "sequential_fp32": S.summarize(rec_s, t_s),
+        "tiles": {"|".join(k): v for k, v in tiles.items()},
+    }
 
 
 def main(argv=None):
@@ -395,6 +427,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=160,
+                    help="requests of the seeded serving mix (config 5) served after the step benchmark; 0 skips")
     ap.add_argument("--grid", type=int, nargs=3, default=list(GRID),
                     help="grid for a smaller profiling case (the benchmark workload is 256 256 192)")
     args = ap.parse_args(argv)

@@ -44,6 +44,7 @@ extern "C" {
 
 typedef struct lbm_lattice lbm_lattice; /* opaque, library-owned */
 typedef struct lbm_model lbm_model;     /* opaque, library-owned */
+typedef struct lbm_batch lbm_batch;     /* opaque, library-owned */
 
 typedef enum {
   LBM_OK = 0,
@@ -212,6 +213,51 @@ lbm_status lbm_model_counters(const lbm_model* m, int64_t* steps, int64_t* launc
 lbm_status lbm_model_synchronize(lbm_model* m);
 
 lbm_status lbm_model_destroy(lbm_model* m);
+
+/* ------------------------------------------------------------------------------------------
+ * Batches: many resident solves advanced together (the paper has no counterpart; this is the
+ * execution engine for serving many solves on one GPU)
+ * ------------------------------------------------------------------------------------------ */
+
+/* Create an empty batch on the current device. stream: the cudaStream_t every member's kernels
+ * run on while it is a member (must be a non-legacy stream so that steps can be captured in a CUDA
+ * graph); NULL makes the batch create and own a non-blocking stream. max_solves bounds membership. */
+lbm_status lbm_batch_create(void* stream, int max_solves, lbm_batch** out);
+
+/* Add a model (F32, F16_DEV or BF16_DEV storage). The model's stream is synchronized, then the
+ * model runs on the batch's stream until it is removed; while a member it is advanced only by
+ * lbm_batch_step (lbm_model_step returns LBM_ERR_ARG) but every other model call works (on the
+ * batch's stream). Members are grouped by (lattice handle, storage dtype, equation); share one
+ * lattice handle between solves of the same lattice setting so that they form one group. */
+lbm_status lbm_batch_add(lbm_batch* b, lbm_model* m);
+
+/* Remove a model (synchronizes the batch's stream; the model returns to its own stream). */
+lbm_status lbm_batch_remove(lbm_batch* b, lbm_model* m);
+
+/* Tile size (cells per thread block) of the batched kernel for one group type: 64, 128 or 256.
+ * Default 128. Set by the autotuner (paper_2512_16230_gb300/autotune.py). */
+lbm_status lbm_batch_set_tile(lbm_batch* b, lbm_kind kind, lbm_dtype store, lbm_eq eq,
+                              int cells_per_tile);
+
+/* Advance every member by nsteps time steps, asynchronously on the batch's stream. Each step is
+ * one persistent launch per group over a tile work-list that covers every cell of every solve of
+ * the group (the same per-cell collide-stream arithmetic as lbm_model_step); groups of 8 steps are
+ * replayed from a captured CUDA graph. The first call after a membership or parameter change
+ * rebuilds the work-lists and the graph (it allocates small device buffers and synchronizes). */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
+
+/* Steps taken, batched launches issued, current number of groups and of tiles. */
+lbm_status lbm_batch_counters(const lbm_batch* b, int64_t* steps, int64_t* launches, int* groups,
+                              int64_t* tiles);
+
+/* The batch's cudaStream_t (for events and ordering by the caller). */
+void* lbm_batch_stream(const lbm_batch* b);
+
+/* Wait for the batch's stream. */
+lbm_status lbm_batch_synchronize(lbm_batch* b);
+
+/* Destroy the batch (members are released, not destroyed). */
+lbm_status lbm_batch_destroy(lbm_batch* b);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,357 @@
+// Batched execution of many solves: the runtime behind lbm_batch_* (include/lbm_mrt.h).
+//
+// Members are grouped by (lattice object, storage dtype, equation). Each group gets its lattice
+// tables (kernel parameter), one descriptor per solve and a tile work-list covering every cell of
+// every solve; one persistent launch per group advances all its solves by one time step. The
+// launches of CHUNK consecutive steps are captured once in a CUDA graph and replayed; membership or
+// parameter changes mark the batch dirty and the next step rebuilds groups and graph.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+namespace {
+
+constexpr int kChunk = 8;  // steps per captured graph (even: each model's buffers return to place)
+
+struct GroupHost {
+  lbm::BatchGroup g;
+  lbm::BatchTables<float> tables;
+  std::vector<lbm::SolveDesc<float>> desc;
+  std::vector<lbm_model*> members;
+};
+
+}  // namespace
+
+struct lbm_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  int max_solves = 0;
+  int num_sms = 0;
+  std::vector<lbm_model*> members;
+  std::vector<GroupHost> groups;
+  std::map<std::tuple<int, int, int>, int> tile;  // (kind, store, eq) -> cells per tile
+  bool dirty = true;
+  cudaGraphExec_t graph = nullptr;
+  int64_t steps = 0, launches = 0;
+};
+
+namespace lbm {
+
+void batch_mark_dirty(lbm_batch* b) {
+  if (b) b->dirty = true;
+}
+
+namespace {
+
+template <class F>
+lbm_status dispatch_batch_kind(int kind, F&& f) {
+  switch (kind) {
+    case LBM_RD2Q13: return f(std::integral_constant<int, LBM_RD2Q13>{});
+    case LBM_RD2Q17: return f(std::integral_constant<int, LBM_RD2Q17>{});
+    case LBM_RD2Q21: return f(std::integral_constant<int, LBM_RD2Q21>{});
+    case LBM_RD2Q25: return f(std::integral_constant<int, LBM_RD2Q25>{});
+    case LBM_RD3Q33: return f(std::integral_constant<int, LBM_RD3Q33>{});
+    case LBM_RD3Q45: return f(std::integral_constant<int, LBM_RD3Q45>{});
+    case LBM_RD3Q53: return f(std::integral_constant<int, LBM_RD3Q53>{});
+  }
+  return set_error(LBM_ERR_ARG, "unknown lattice kind");
+}
+
+void free_groups(lbm_batch* b) {
+  for (auto& gh : b->groups) {
+    if (gh.g.d_desc) cudaFree(gh.g.d_desc);
+    if (gh.g.d_tiles) cudaFree(gh.g.d_tiles);
+  }
+  b->groups.clear();
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+void fill_desc(const lbm_model* m, SolveDesc<float>* d) {
+  StepParams<float> p;
+  make_step_params<float>(m, &p);
+  std::memset(d, 0, sizeof(*d));
+  for (int r = 0; r < kMaxR; ++r) {
+    d->sd[r] = p.sd[r];
+    d->half[r] = p.half[r];
+  }
+  d->s_high = p.s_high;
+  d->one_minus_sh = p.one_minus_sh;
+  d->sh_rho_ref = p.sh_rho_ref;
+  d->cs2_eq = p.cs2_eq;
+  d->nonlin_third = p.nonlin_third;
+  for (int a = 0; a < 3; ++a) {
+    d->u_const[a] = p.u_const[a];
+    d->n[a] = p.n[a];
+  }
+  d->ncells = p.ncells;
+  for (int a = 0; a < 2; ++a) {
+    d->div_m[a] = p.div_m[a];
+    d->div_s[a] = p.div_s[a];
+  }
+  d->force_a = p.force_a;
+  d->force_b = p.force_b;
+  d->force_tab = p.force_tab;
+  d->f[0] = m->f[m->cur];
+  d->f[1] = m->f[m->cur ^ 1];
+  d->phi = static_cast<float*>(m->phi_prev);
+}
+
+lbm_status launch_group(const GroupHost& gh, int parity, cudaStream_t stream) {
+  return dispatch_batch_kind(gh.g.kind, [&](auto kc) {
+    return BatchLaunch<decltype(kc)::value>::launch(gh.g, parity, stream);
+  });
+}
+
+lbm_status upload_desc(lbm_batch* b, GroupHost& gh) {
+  cudaError_t err = cudaMemcpyAsync(gh.g.d_desc, gh.desc.data(), gh.desc.size() * sizeof(SolveDesc<float>),
+                                    cudaMemcpyHostToDevice, b->stream);
+  return err == cudaSuccess ? LBM_OK : cuda_error(err, "batch descriptor upload");
+}
+
+lbm_status rebuild(lbm_batch* b) {
+  free_groups(b);
+  std::map<std::tuple<const lbm_lattice*, int, int>, size_t> index;
+  for (lbm_model* m : b->members) {
+    auto key = std::make_tuple(m->lat, m->store, m->eq);
+    auto it = index.find(key);
+    if (it == index.end()) {
+      index[key] = b->groups.size();
+      b->groups.emplace_back();
+      GroupHost& gh = b->groups.back();
+      std::memset(&gh.g, 0, sizeof(gh.g));
+      gh.g.kind = m->lat->kind;
+      gh.g.store = m->store;
+      gh.g.eq = m->eq;
+      gh.g.lat = m->lat;
+      auto t = b->tile.find(std::make_tuple(m->lat->kind, m->store, m->eq));
+      gh.g.block = t == b->tile.end() ? kBlock : t->second;
+      StepParams<float> p;
+      make_step_params<float>(m, &p);
+      std::memcpy(gh.tables.T, p.T, sizeof(p.T));
+      std::memcpy(gh.tables.D, p.D, sizeof(p.D));
+      std::memcpy(gh.tables.invN, p.invN, sizeof(p.invN));
+      std::memcpy(gh.tables.w, p.w, sizeof(p.w));
+      std::memcpy(gh.tables.wref, p.wref, sizeof(p.wref));
+      std::memcpy(gh.tables.wmom_ref, p.wmom_ref, sizeof(p.wmom_ref));
+      gh.members.push_back(m);
+    } else {
+      b->groups[it->second].members.push_back(m);
+    }
+  }
+  for (auto& gh : b->groups) {
+    gh.g.tables = &gh.tables;
+    gh.desc.resize(gh.members.size());
+    std::vector<Tile> tiles;
+    for (size_t j = 0; j < gh.members.size(); ++j) {
+      fill_desc(gh.members[j], &gh.desc[j]);
+      for (int c0 = 0; c0 < gh.members[j]->ncells; c0 += gh.g.block) tiles.push_back(Tile{int(j), c0});
+    }
+    gh.g.nsolves = int(gh.members.size());
+    gh.g.ntiles = int(tiles.size());
+    cudaError_t err = cudaMalloc(&gh.g.d_desc, gh.desc.size() * sizeof(SolveDesc<float>));
+    if (err == cudaSuccess) err = cudaMalloc(&gh.g.d_tiles, tiles.size() * sizeof(Tile));
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(gh.g.d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(b->stream);
+    if (err != cudaSuccess) return cuda_error(err, "batch work-list allocation");
+    lbm_status st = upload_desc(b, gh);
+    if (st != LBM_OK) return st;
+    int per_sm = 0;
+    st = dispatch_batch_kind(gh.g.kind, [&](auto kc) {
+      return BatchLaunch<decltype(kc)::value>::occupancy(gh.g.store, gh.g.eq, gh.g.block, &per_sm);
+    });
+    if (st != LBM_OK) return st;
+    gh.g.grid = std::max(1, std::min(gh.g.ntiles, std::max(1, per_sm) * b->num_sms));
+  }
+  if (!b->groups.empty()) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t err = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return cuda_error(err, "graph capture (the batch needs a non-legacy stream)");
+    lbm_status st = LBM_OK;
+    for (int s = 0; s < kChunk && st == LBM_OK; ++s)
+      for (auto& gh : b->groups)
+        if (st == LBM_OK) st = launch_group(gh, s & 1, b->stream);
+    err = cudaStreamEndCapture(b->stream, &graph);
+    if (st != LBM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (err != cudaSuccess) return cuda_error(err, "graph capture");
+    err = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) return cuda_error(err, "graph instantiation");
+  }
+  b->dirty = false;
+  return LBM_OK;
+}
+
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" {
+
+lbm_status lbm_batch_create(void* stream, int max_solves, lbm_batch** out) {
+  if (!out) return set_error(LBM_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (max_solves < 1) return set_error(LBM_ERR_ARG, "max_solves must be positive");
+  auto* b = new (std::nothrow) lbm_batch;
+  if (!b) return set_error(LBM_ERR_OOM, "host allocation failed");
+  cudaGetDevice(&b->device);
+  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  b->max_solves = max_solves;
+  if (stream) {
+    b->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    cudaError_t err = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (err != cudaSuccess) {
+      delete b;
+      return cuda_error(err, "batch stream");
+    }
+    b->owns_stream = true;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_add(lbm_batch* b, lbm_model* m) {
+  if (!b || !m) return set_error(LBM_ERR_ARG, "NULL argument");
+  if (m->batch) return set_error(LBM_ERR_ARG, "model is already in a batch");
+  if (m->device != b->device) return set_error(LBM_ERR_ARG, "model and batch are on different devices");
+  if (m->store == LBM_F64) return set_error(LBM_ERR_NOT_IMPLEMENTED, "batched execution supports F32 and 16-bit storage");
+  if (int(b->members.size()) >= b->max_solves) return set_error(LBM_ERR_ARG, "batch is full");
+  DeviceScope scope(b->device);
+  cudaError_t err = cudaStreamSynchronize(m->stream);
+  if (err != cudaSuccess) return cuda_error(err, "model stream");
+  m->own_stream = m->stream;
+  m->stream = b->stream;
+  m->batch = b;
+  b->members.push_back(m);
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_remove(lbm_batch* b, lbm_model* m) {
+  if (!b || !m) return set_error(LBM_ERR_ARG, "NULL argument");
+  auto it = std::find(b->members.begin(), b->members.end(), m);
+  if (it == b->members.end() || m->batch != b) return set_error(LBM_ERR_ARG, "model is not in this batch");
+  DeviceScope scope(b->device);
+  cudaError_t err = cudaStreamSynchronize(b->stream);
+  if (err != cudaSuccess) return cuda_error(err, "batch stream");
+  b->members.erase(it);
+  m->stream = m->own_stream;
+  m->batch = nullptr;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_tile(lbm_batch* b, lbm_kind kind, lbm_dtype store, lbm_eq eq, int cells_per_tile) {
+  if (!b) return set_error(LBM_ERR_ARG, "NULL batch");
+  if (cells_per_tile != 64 && cells_per_tile != 128 && cells_per_tile != 256)
+    return set_error(LBM_ERR_ARG, "cells per tile must be 64, 128 or 256");
+  b->tile[std::make_tuple(int(kind), int(store), int(eq))] = cells_per_tile;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+  if (!b) return set_error(LBM_ERR_ARG, "NULL batch");
+  if (nsteps < 0) return set_error(LBM_ERR_ARG, "nsteps must be non-negative");
+  if (b->members.empty() || nsteps == 0) return LBM_OK;
+  DeviceScope scope(b->device);
+  if (b->dirty) {
+    lbm_status st = rebuild(b);
+    if (st != LBM_OK) return st;
+  }
+  const int64_t chunks = nsteps / kChunk;
+  const int rem = int(nsteps % kChunk);
+  for (int64_t c = 0; c < chunks; ++c) {
+    cudaError_t err = cudaGraphLaunch(b->graph, b->stream);
+    if (err != cudaSuccess) return cuda_error(err, "batch graph launch");
+  }
+  for (int s = 0; s < rem; ++s)
+    for (auto& gh : b->groups) {
+      lbm_status st = launch_group(gh, s & 1, b->stream);
+      if (st != LBM_OK) return st;
+    }
+  if (rem & 1) {
+    // every model's current buffer flipped: swap the descriptors' buffers (the graph reads them)
+    for (auto& gh : b->groups) {
+      for (size_t j = 0; j < gh.members.size(); ++j) {
+        gh.members[j]->cur ^= 1;
+        std::swap(gh.desc[j].f[0], gh.desc[j].f[1]);
+      }
+      lbm_status st = upload_desc(b, gh);
+      if (st != LBM_OK) return st;
+    }
+  }
+  for (lbm_model* m : b->members) {
+    m->steps += nsteps;
+    m->launches += nsteps;
+  }
+  b->steps += nsteps;
+  b->launches += nsteps * int64_t(b->groups.size());
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_counters(const lbm_batch* b, int64_t* steps, int64_t* launches, int* groups, int64_t* tiles) {
+  if (!b) return set_error(LBM_ERR_ARG, "NULL batch");
+  if (steps) *steps = b->steps;
+  if (launches) *launches = b->launches;
+  if (groups) *groups = int(b->groups.size());
+  if (tiles) {
+    int64_t t = 0;
+    for (const auto& gh : b->groups) t += gh.g.ntiles;
+    *tiles = t;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_synchronize(lbm_batch* b) {
+  if (!b) return set_error(LBM_ERR_ARG, "NULL batch");
+  DeviceScope scope(b->device);
+  cudaError_t err = cudaStreamSynchronize(b->stream);
+  return err == cudaSuccess ? LBM_OK : cuda_error(err, "batch synchronize");
+}
+
+void* lbm_batch_stream(const lbm_batch* b) { return b ? static_cast<void*>(b->stream) : nullptr; }
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return LBM_OK;
+  DeviceScope scope(b->device);
+  cudaStreamSynchronize(b->stream);
+  for (lbm_model* m : b->members) {
+    m->stream = m->own_stream;
+    m->batch = nullptr;
+  }
+  free_groups(b);
+  if (b->owns_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return LBM_OK;
+}
+
+}  // extern "C"

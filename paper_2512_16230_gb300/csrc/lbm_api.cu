@@ -46,6 +46,20 @@ void make_step_params(const lbm_model* m, StepParams<CT>* p) {
     p->w[i] = CT(L->w[i]);
     p->wref[i] = dev ? CT(L->w[i] * m->rho_ref) : CT(0);
   }
+  const double rho_ref = dev ? m->rho_ref : 0.0;
+  for (int r = 0; r < R; ++r) {
+    const Mono mk = L->d == 2 ? kMono2[r] : kMono3[r];
+    double acc = 0.0;
+    for (int i = 0; i < L->Q; ++i) {
+      double v = L->w[i];
+      for (int q = 0; q < mk.a; ++q) v *= L->e[i * 3 + 0];
+      for (int q = 0; q < mk.b; ++q) v *= L->e[i * 3 + 1];
+      for (int q = 0; q < mk.c; ++q) v *= L->e[i * 3 + 2];
+      acc += v;
+    }
+    p->wmom_ref[r] = CT(rho_ref * acc);
+  }
+  p->sh_rho_ref = CT(m->s_high * rho_ref);
   p->s_high = CT(m->s_high);
   p->one_minus_sh = CT(1.0 - m->s_high);
   p->cs2_eq = CT(m->cs2_eq);
@@ -327,6 +341,7 @@ lbm_status lbm_model_set_relaxation(lbm_model* m, const double* s, double s_high
   if (!(s_high > 0.0 && s_high <= 2.0)) return set_error(LBM_ERR_ARG, "rates must lie in (0, 2]");
   for (int r = 0; r < m->lat->R; ++r) m->s[r] = s[r];
   m->s_high = s_high;
+  batch_mark_dirty(m->batch);
   return LBM_OK;
 }
 
@@ -334,6 +349,7 @@ lbm_status lbm_model_set_eos(lbm_model* m, double cs2_eq) {
   if (!m) return set_error(LBM_ERR_ARG, "NULL model");
   if (!(cs2_eq > 0.0) || !std::isfinite(cs2_eq)) return set_error(LBM_ERR_ARG, "cs2_eq must be positive");
   m->cs2_eq = cs2_eq;
+  batch_mark_dirty(m->batch);
   return LBM_OK;
 }
 
@@ -349,6 +365,7 @@ lbm_status lbm_model_set_force(lbm_model* m, int axis_a, int axis_b, double A, i
   m->force_A = A;
   m->force_k = k;
   m->force_phase = phase;
+  batch_mark_dirty(m->batch);
   return upload_force(m);
 }
 
@@ -357,6 +374,7 @@ lbm_status lbm_model_set_ncde(lbm_model* m, const double* u_const, double nonlin
   if (m->eq != LBM_NCDE) return set_error(LBM_ERR_ARG, "convection velocity applies to the NCDE model");
   for (int a = 0; a < 3; ++a) m->u_const[a] = a < m->lat->d ? u_const[a] : 0.0;
   m->nonlin = nonlin;
+  batch_mark_dirty(m->batch);
   return LBM_OK;
 }
 
@@ -438,6 +456,7 @@ lbm_status lbm_model_get_populations(lbm_model* m, double* f, int on_device) {
 
 lbm_status lbm_model_step(lbm_model* m, int64_t nsteps) {
   if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (m->batch) return set_error(LBM_ERR_ARG, "the model is in a batch: advance it with lbm_batch_step");
   if (nsteps < 0) return set_error(LBM_ERR_ARG, "nsteps must be non-negative");
   DeviceGuard guard(m->device);
   return dispatch_kind(m->lat->kind, [&](auto kc) { return Launch<decltype(kc)::value>::step(m, nsteps, true); });
@@ -445,6 +464,7 @@ lbm_status lbm_model_step(lbm_model* m, int64_t nsteps) {
 
 lbm_status lbm_model_stream_only(lbm_model* m, int64_t nsteps) {
   if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (m->batch) return set_error(LBM_ERR_ARG, "the model is in a batch: advance it with lbm_batch_step");
   if (nsteps < 0) return set_error(LBM_ERR_ARG, "nsteps must be non-negative");
   DeviceGuard guard(m->device);
   return dispatch_kind(m->lat->kind, [&](auto kc) { return Launch<decltype(kc)::value>::step(m, nsteps, false); });
@@ -513,6 +533,7 @@ lbm_status lbm_model_synchronize(lbm_model* m) {
 
 lbm_status lbm_model_destroy(lbm_model* m) {
   if (!m) return LBM_OK;
+  if (m->batch) lbm_batch_remove(m->batch, m);
   DeviceGuard guard(m->device);
   cudaStreamSynchronize(m->stream);
   if (m->owns_ws) cudaFree(m->ws);

@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <string>
+#include <type_traits>
 
 #include "lattices.cuh"
 #include "lbm_mrt.h"
@@ -47,6 +48,8 @@ struct lbm_model {
   double nonlin;
   int64_t steps, launches;
   int device;
+  lbm_batch* batch;         // batch the model belongs to (its kernels then run on the batch's stream)
+  cudaStream_t own_stream;  // the model's stream while it is not in a batch
 };
 
 namespace lbm {
@@ -69,6 +72,8 @@ struct StepParams {
   CT half[kMaxR];      // 1 - s_r / 2
   CT w[kMaxQ];
   CT wref[kMaxQ];      // w_i * rho_ref, the offset of deviation storage
+  CT wmom_ref[kMaxR];  // rho_ref sum_i w_i mono_k(e_i): moments of the reference state w_i rho_ref
+  CT sh_rho_ref;       // s_high * rho_ref
   CT s_high, one_minus_sh, cs2_eq, nonlin_third;
   CT u_const[3];
   int n[3];
@@ -138,11 +143,81 @@ struct Codec<__half> {
   }
 };
 
+// Deviation storage read and written as deviations (no reference offset).
+template <class ST>
+struct RawCodec;
+template <>
+struct RawCodec<__nv_bfloat16> {
+  __device__ __forceinline__ static float dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ __forceinline__ static __nv_bfloat16 enc(float v) { return __float2bfloat16_rn(v); }
+};
+template <>
+struct RawCodec<__half> {
+  __device__ __forceinline__ static float dec(__half v) { return __half2float(v); }
+  __device__ __forceinline__ static __half enc(float v) { return __float2half_rn(v); }
+};
+template <class ST>
+constexpr bool is_deviation_storage() {
+  return std::is_same<ST, __nv_bfloat16>::value || std::is_same<ST, __half>::value;
+}
+
 inline size_t dtype_bytes(int dt) { return dt == LBM_F64 ? 8 : dt == LBM_F32 ? 4 : 2; }
 
 // Error reporting (thread-local message behind lbm_last_error).
 lbm_status set_error(lbm_status st, const std::string& msg);
 lbm_status cuda_error(cudaError_t err, const char* what);
+
+// ---- Batched execution (one launch advances every solve of a group by one step) ----
+
+// Lattice tables shared by every solve of a group (kernel parameter: constant bank).
+template <class CT>
+struct BatchTables {
+  CT T[kMaxR][kMaxR];
+  CT D[kMaxR];
+  CT invN[kMaxR];
+  CT w[kMaxQ];
+  CT wref[kMaxQ];
+  CT wmom_ref[kMaxR];
+};
+
+// Per-solve data of a batched step (device array; each block stages its solve's entry in shared
+// memory). f[k] is the input of a step launched with parity k and f[k ^ 1] its output.
+template <class CT>
+struct __align__(16) SolveDesc {
+  CT sd[kMaxR];
+  CT half[kMaxR];
+  CT s_high, one_minus_sh, sh_rho_ref, cs2_eq, nonlin_third;
+  CT u_const[3];
+  int n[3];
+  int ncells;
+  unsigned div_m[2];
+  int div_s[2];
+  int force_a, force_b;
+  const CT* force_tab;
+  void* f[2];
+  CT* phi;
+};
+
+struct Tile {
+  int solve;  // index into the group's descriptor array
+  int cell0;  // first cell of the tile (tiles are blockDim cells long, the last one ragged)
+};
+
+// A group of solves advanced by one batched launch per step.
+struct BatchGroup {
+  int kind, store, eq, block;
+  const lbm_lattice* lat;
+  void* tables;     // host copy of BatchTables<CT>
+  void* d_desc;     // device SolveDesc<CT>[nsolves]
+  Tile* d_tiles;    // device work-list
+  int nsolves, ntiles, grid;
+};
+
+template <int KIND>
+struct BatchLaunch {
+  static lbm_status launch(const BatchGroup& g, int parity, cudaStream_t stream);
+  static lbm_status occupancy(int store, int eq, int block, int* blocks_per_sm);
+};
 
 // Per-lattice launchers, defined in the k_<lattice>.cu translation units.
 template <int KIND>
@@ -161,6 +236,9 @@ lbm_status launch_phi_from_populations(lbm_model* m);          // NCDE: phi_prev
 // The conservation-sum kernels with caller-provided reduction scratch (partial_slots x 4
 // doubles, at least kRedBlocks slots) and result (4 doubles, device memory).
 lbm_status launch_sums_into(lbm_model* m, double* partials, int partial_slots, double* out);
+
+// Batches (batch.cu): a parameter change of a member invalidates the batch's captured work.
+void batch_mark_dirty(lbm_batch* b);
 
 // FP64 lattice set-up on the GPU (setup_fp64.cu).
 lbm_status setup_lattice_fp64(lbm_lattice* lat);

@@ -145,8 +145,8 @@ __device__ __forceinline__ void eq_raw_nse(CT rho, const CT (&j)[3], const CT (&
 
 // Continuous raw moments of the NCDE equilibrium up to second order (Eq. (M-NCDE-6), M20 = 0):
 // M0 = phi, M1 = u phi, M2 = cs2_eq D(phi) I. Third-order entries are unused.
-template <class L, class CT>
-__device__ __forceinline__ void eq_raw_ncde(CT phi, CT Dphi, const StepParams<CT>& p,
+template <class L, class CT, class P>
+__device__ __forceinline__ void eq_raw_ncde(CT phi, CT Dphi, const P& p,
                                             CT (&me)[L::R]) {
   static_for<L::R>([&](auto k) {
     constexpr int K = decltype(k)::value;
@@ -160,8 +160,8 @@ __device__ __forceinline__ void eq_raw_ncde(CT phi, CT Dphi, const StepParams<CT
 }
 
 // sum_{k < r, same parity class as r} T_rk v_k + v_r   (T is monic: T_rr = 1)
-template <class L, class CT, int r>
-__device__ __forceinline__ CT row_dot(const StepParams<CT>& p, const CT (&v)[L::R]) {
+template <class L, class CT, int r, class P>
+__device__ __forceinline__ CT row_dot(const P& p, const CT (&v)[L::R]) {
   CT acc = v[r];
   static_for<r>([&](auto k) {
     constexpr int K = decltype(k)::value;
@@ -173,8 +173,8 @@ __device__ __forceinline__ CT row_dot(const StepParams<CT>& p, const CT (&v)[L::
 
 // Hermite moments of the equilibrium, m^eq_r = sum_k T_rk me_k.
 // For the NCDE the third-order Hermite moments of the equilibrium are zero.
-template <class L, class CT, int EQ, int r>
-__device__ __forceinline__ CT hermite_eq(const StepParams<CT>& p, const CT (&me)[L::R]) {
+template <class L, class CT, int EQ, int r, class P>
+__device__ __forceinline__ CT hermite_eq(const P& p, const CT (&me)[L::R]) {
   if constexpr (EQ == LBM_NCDE && degree(mono<L::D>(r)) == 3) return CT(0);
   else return row_dot<L, CT, r>(p, me);
 }
@@ -182,8 +182,8 @@ __device__ __forceinline__ CT hermite_eq(const StepParams<CT>& p, const CT (&me)
 // f_i = (1 - s_h) f_i + w_i sum_k mono_k(e_i) h_k  (h already scaled by D_k). Per primitive
 // direction d: E_deg = sum_{deg(k) = deg} mono_k(d) h_k, then for every speed m present
 // f_{+-md} = (1 - s_h) f + w (E_0 + m^2 E_2 +- (m E_1 + m^3 E_3)).
-template <class L, class CT>
-__device__ __forceinline__ void back_project(CT (&f)[L::Q], const StepParams<CT>& p,
+template <class L, class CT, class P>
+__device__ __forceinline__ void back_project(CT (&f)[L::Q], const P& p,
                                              const CT (&h)[L::R], CT oms) {
   f[0] = fma(oms, f[0], p.w[0] * h[0]);
   static_for<num_directions<L>()>([&](auto dk) {
@@ -211,8 +211,8 @@ __device__ __forceinline__ void back_project(CT (&f)[L::Q], const StepParams<CT>
 }
 
 // h_k = D_k sum_{r >= k, same parity class} T_rk gN_r   (the transpose contraction)
-template <class L, class CT>
-__device__ __forceinline__ void hermite_to_monomial(const StepParams<CT>& p, const CT (&gN)[L::R],
+template <class L, class CT, class P>
+__device__ __forceinline__ void hermite_to_monomial(const P& p, const CT (&gN)[L::R],
                                                     CT (&h)[L::R]) {
   static_for<L::R>([&](auto k) {
     constexpr int K = decltype(k)::value;
@@ -230,8 +230,8 @@ __device__ __forceinline__ void hermite_to_monomial(const StepParams<CT>& p, con
 
 // Hermite-row work of the collision for row r: g_r / N_r with
 // g_r = s_h m^eq_r - (s_r - s_h)(m_r - m^eq_r) + sigma_r.
-template <class L, class CT, int EQ, int r>
-__device__ __forceinline__ CT row_update(const StepParams<CT>& p, const CT (&mu)[L::R],
+template <class L, class CT, int EQ, int r, class P>
+__device__ __forceinline__ CT row_update(const P& p, const CT (&mu)[L::R],
                                          const CT (&me)[L::R], const CT (&u)[3], const CT (&F)[3],
                                          CT dphi) {
   constexpr int deg = degree(mono<L::D>(r));
@@ -265,12 +265,23 @@ __device__ __forceinline__ CT row_update(const StepParams<CT>& p, const CT (&mu)
 
 // One collision (Eq. (2-3)) of the populations f of one cell, in place.
 // F: body force at the cell (NSE); phi_prev / phi_now: the NCDE field at t_{n-1} and t_n.
-template <class L, class CT, int EQ>
-__device__ __forceinline__ void collide(CT (&f)[L::Q], const StepParams<CT>& p, const CT (&F)[3],
+// DEV: f holds deviations f - w rho_ref (16-bit storage). The moments of the reference state are
+// added back (only 1 and the squares c_a^2 have non-zero lattice moments), and the update
+// f* - w rho_ref = (1 - s_h)(f - w rho_ref) + w H(h) - s_h w rho_ref folds the last term into h_0.
+template <class L, class CT, int EQ, bool DEV = false, class P>
+__device__ __forceinline__ void collide(CT (&f)[L::Q], const P& p, const CT (&F)[3],
                                         CT phi_prev, CT& phi_now) {
   constexpr int R = L::R, D = L::D;
   CT mu[R];
   raw_moments<L>(f, mu);
+  if constexpr (DEV) {
+    static_for<R>([&](auto k) {
+      constexpr Mono mk = mono<L::D>(decltype(k)::value);
+      if constexpr ((mk.a & 1) == 0 && (mk.b & 1) == 0 && (mk.c & 1) == 0 && degree(mk) <= 2 &&
+                    (degree(mk) == 0 || mk.a == 2 || mk.b == 2 || mk.c == 2))
+        mu[decltype(k)::value] += p.wmom_ref[decltype(k)::value];
+    });
+  }
   static_for<R>([&](auto k) {
     constexpr int K = decltype(k)::value;
     if constexpr (K > 0) mu[K] *= p.D[K];
@@ -303,12 +314,13 @@ __device__ __forceinline__ void collide(CT (&f)[L::Q], const StepParams<CT>& p, 
   });
   CT h[R];
   hermite_to_monomial<L>(p, gN, h);
+  if constexpr (DEV) h[0] -= p.sh_rho_ref;
   back_project<L>(f, p, h, p.one_minus_sh);
 }
 
 // Equilibrium populations of given fields, Eq. (feq-1): f^eq_i = w_i sum_r H_ri m^eq_r / N_r.
-template <class L, class CT, int EQ>
-__device__ __forceinline__ void equilibrium(CT (&f)[L::Q], const StepParams<CT>& p, CT rho_or_phi,
+template <class L, class CT, int EQ, class P>
+__device__ __forceinline__ void equilibrium(CT (&f)[L::Q], const P& p, CT rho_or_phi,
                                             const CT (&uin)[3]) {
   constexpr int R = L::R;
   CT me[R];
@@ -341,24 +353,25 @@ struct Neigh {
   int xo[2 * RM + 1], yo[2 * RM + 1], zo[2 * RM + 1];
   int x, y, z;
   template <class CT>
-  __device__ __forceinline__ Neigh(int cell, const StepParams<CT>& p) {
-    const int nx = p.n[0], ny = p.n[1];
+  __device__ __forceinline__ Neigh(int cell, const StepParams<CT>& p) : Neigh(cell, p.n, p.div_m, p.div_s) {}
+  __device__ __forceinline__ Neigh(int cell, const int (&n)[3], const unsigned (&div_m)[2], const int (&div_s)[2]) {
+    const int nx = n[0], ny = n[1];
     // the velocity components are at most RM <= every extent, so one wrap suffices and only on
     // the side a displacement can cross
-    const int t = int(__umulhi(unsigned(cell), p.div_m[0]) >> p.div_s[0]);
+    const int t = int(__umulhi(unsigned(cell), div_m[0]) >> div_s[0]);
     x = cell - t * nx;
     if constexpr (L::D == 2) {
       y = t;
       z = 0;
     } else {
-      z = int(__umulhi(unsigned(t), p.div_m[1]) >> p.div_s[1]);
+      z = int(__umulhi(unsigned(t), div_m[1]) >> div_s[1]);
       y = t - z * ny;
     }
 #pragma unroll
     for (int s = -RM; s <= RM; ++s) {
       xo[s + RM] = wrap1(x - s, s, nx);
       yo[s + RM] = wrap1(y - s, s, ny) * nx;
-      if constexpr (L::D == 3) zo[s + RM] = wrap1(z - s, s, p.n[2]) * nx * ny;
+      if constexpr (L::D == 3) zo[s + RM] = wrap1(z - s, s, n[2]) * nx * ny;
       else zo[s + RM] = 0;
     }
   }
@@ -382,15 +395,15 @@ struct Neigh {
 };
 
 template <class CT>
-__device__ __forceinline__ void body_force(const StepParams<CT>& p, int x, int y, int z,
-                                           CT (&F)[3]) {
+__device__ __forceinline__ void body_force(int force_a, int force_b, const CT* force_tab, int x, int y,
+                                           int z, CT (&F)[3]) {
   F[0] = F[1] = F[2] = CT(0);
-  if (p.force_b >= 0) {
-    const int ib = p.force_b == 0 ? x : (p.force_b == 1 ? y : z);
-    const CT v = p.force_tab[ib];
-    F[0] = p.force_a == 0 ? v : CT(0);
-    F[1] = p.force_a == 1 ? v : CT(0);
-    F[2] = p.force_a == 2 ? v : CT(0);
+  if (force_b >= 0) {
+    const int ib = force_b == 0 ? x : (force_b == 1 ? y : z);
+    const CT v = force_tab[ib];
+    F[0] = force_a == 0 ? v : CT(0);
+    F[1] = force_a == 1 ? v : CT(0);
+    F[2] = force_a == 2 ? v : CT(0);
   }
 }
 
@@ -404,21 +417,24 @@ __global__ void __launch_bounds__(kBlock, LBM_K1_MIN_BLOCKS) k_step(const StepPa
   const Neigh<L> nb(cell, p);
   const size_t N = size_t(p.ncells);
   CT f[L::Q];
+  constexpr bool DEV = is_deviation_storage<ST>();
   static_for<L::Q>([&](auto i) {
     constexpr int I = decltype(i)::value;
-    f[I] = Codec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()), p.wref[I]);
+    if constexpr (DEV) f[I] = RawCodec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()));
+    else f[I] = Codec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()), p.wref[I]);
   });
   if constexpr (COLLIDE) {
     CT F[3];
-    body_force(p, nb.x, nb.y, nb.z, F);
+    body_force(p.force_a, p.force_b, p.force_tab, nb.x, nb.y, nb.z, F);
     CT phi_prev = CT(0), phi_now = CT(0);
     if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
-    collide<L, CT, EQ>(f, p, F, phi_prev, phi_now);
+    collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now);
     if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
   }
   static_for<L::Q>([&](auto i) {
     constexpr int I = decltype(i)::value;
-    k1_store(fout + size_t(I) * N + cell, Codec<ST>::enc(f[I], p.wref[I]));
+    if constexpr (DEV) k1_store(fout + size_t(I) * N + cell, RawCodec<ST>::enc(f[I]));
+    else k1_store(fout + size_t(I) * N + cell, Codec<ST>::enc(f[I], p.wref[I]));
   });
 }
 
@@ -444,6 +460,131 @@ __global__ void __launch_bounds__(kBlock) k_init(const StepParams<CT> p, const d
   static_for<L::Q>([&](auto i) {
     constexpr int I = decltype(i)::value;
     fout[size_t(I) * N + nb.template src<I>()] = Codec<ST>::enc(f[I], p.wref[I]);
+  });
+}
+
+// Parameter view of a batched step: lattice tables from the kernel parameter, per-solve values
+// from the shared-memory copy of the solve's descriptor (same member names as StepParams).
+template <class CT>
+struct BatchView {
+  const CT (&T)[kMaxR][kMaxR];
+  const CT (&D)[kMaxR];
+  const CT (&invN)[kMaxR];
+  const CT (&w)[kMaxQ];
+  const CT (&wref)[kMaxQ];
+  const CT (&wmom_ref)[kMaxR];
+  const CT (&sd)[kMaxR];
+  const CT (&half)[kMaxR];
+  const CT (&u_const)[3];
+  CT s_high, one_minus_sh, sh_rho_ref, cs2_eq, nonlin_third;
+  __device__ __forceinline__ BatchView(const BatchTables<CT>& t, const SolveDesc<CT>& d)
+      : T(t.T), D(t.D), invN(t.invN), w(t.w), wref(t.wref), wmom_ref(t.wmom_ref), sd(d.sd), half(d.half),
+        u_const(d.u_const), s_high(d.s_high), one_minus_sh(d.one_minus_sh), sh_rho_ref(d.sh_rho_ref),
+        cs2_eq(d.cs2_eq), nonlin_third(d.nonlin_third) {}
+};
+
+// K6: persistent batched collide-stream. The grid is the resident capacity of the GPU; each
+// block walks the tile work-list of the group (tiles of BLOCK cells from every solve), stages
+// the descriptor of the tile's solve in shared memory when it changes, and runs the same per-cell
+// gather / collide / store as k_step.
+template <int BLOCK>
+constexpr int batch_min_blocks() {
+  return BLOCK >= 256 ? 2 : (BLOCK >= 128 ? LBM_K1_MIN_BLOCKS : 10);
+}
+
+template <class L, class CT, class ST, int EQ, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, batch_min_blocks<BLOCK>())
+    k_step_batch(const BatchTables<CT> t, const SolveDesc<CT>* __restrict__ descs,
+                 const Tile* __restrict__ tiles, int ntiles, int parity) {
+  __shared__ SolveDesc<CT> sd;
+  constexpr int kWords = int(sizeof(SolveDesc<CT>) / sizeof(int4));
+  static_assert(sizeof(SolveDesc<CT>) % sizeof(int4) == 0, "descriptor must be a whole number of int4");
+  int staged = -1;
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const Tile tile = tiles[ti];
+    if (tile.solve != staged) {
+      __syncthreads();
+      const int4* src = reinterpret_cast<const int4*>(descs + tile.solve);
+      int4* dst = reinterpret_cast<int4*>(&sd);
+      for (int w = threadIdx.x; w < kWords; w += BLOCK) dst[w] = src[w];
+      __syncthreads();
+      staged = tile.solve;
+    }
+    const int cell = tile.cell0 + int(threadIdx.x);
+    if (cell >= sd.ncells) continue;
+    const Neigh<L> nb(cell, sd.n, sd.div_m, sd.div_s);
+    const size_t N = size_t(sd.ncells);
+    const ST* __restrict__ fin = static_cast<const ST*>(sd.f[parity]);
+    ST* __restrict__ fout = static_cast<ST*>(sd.f[parity ^ 1]);
+    const BatchView<CT> p(t, sd);
+    constexpr bool DEV = is_deviation_storage<ST>();
+    CT f[L::Q];
+    static_for<L::Q>([&](auto i) {
+      constexpr int I = decltype(i)::value;
+      if constexpr (DEV) f[I] = RawCodec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()));
+      else f[I] = Codec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()), p.wref[I]);
+    });
+    CT F[3];
+    body_force(sd.force_a, sd.force_b, sd.force_tab, nb.x, nb.y, nb.z, F);
+    CT phi_prev = CT(0), phi_now = CT(0);
+    if constexpr (EQ == LBM_NCDE) phi_prev = sd.phi[cell];
+    collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now);
+    if constexpr (EQ == LBM_NCDE) sd.phi[cell] = phi_now;
+    static_for<L::Q>([&](auto i) {
+      constexpr int I = decltype(i)::value;
+      if constexpr (DEV) k1_store(fout + size_t(I) * N + cell, RawCodec<ST>::enc(f[I]));
+      else k1_store(fout + size_t(I) * N + cell, Codec<ST>::enc(f[I], p.wref[I]));
+    });
+  }
+}
+
+template <class L, class CT, class ST, int EQ, class F>
+lbm_status batch_by_block(int block, F&& fn) {
+  switch (block) {
+    case 64: return fn(k_step_batch<L, CT, ST, EQ, 64>);
+    case 128: return fn(k_step_batch<L, CT, ST, EQ, 128>);
+    case 256: return fn(k_step_batch<L, CT, ST, EQ, 256>);
+  }
+  return set_error(LBM_ERR_ARG, "batched tile size must be 64, 128 or 256 cells");
+}
+
+template <class L, class F>
+lbm_status batch_kernel(int store, int eq, int block, F&& fn) {
+  if (store == LBM_F32) {
+    if (eq == LBM_NSE) return batch_by_block<L, float, float, LBM_NSE>(block, fn);
+    return batch_by_block<L, float, float, LBM_NCDE>(block, fn);
+  }
+  if (store == LBM_F16_DEV) {
+    if (eq == LBM_NSE) return batch_by_block<L, float, __half, LBM_NSE>(block, fn);
+    return batch_by_block<L, float, __half, LBM_NCDE>(block, fn);
+  }
+  if (store == LBM_BF16_DEV) {
+    if (eq == LBM_NSE) return batch_by_block<L, float, __nv_bfloat16, LBM_NSE>(block, fn);
+    return batch_by_block<L, float, __nv_bfloat16, LBM_NCDE>(block, fn);
+  }
+  return set_error(LBM_ERR_NOT_IMPLEMENTED, "batched execution supports F32, F16_DEV and BF16_DEV storage");
+}
+
+template <int KIND>
+lbm_status BatchLaunch<KIND>::launch(const BatchGroup& g, int parity, cudaStream_t stream) {
+  using L = Lat<KIND>;
+  return batch_kernel<L>(g.store, g.eq, g.block, [&](auto kernel) -> lbm_status {
+    using Kern = decltype(kernel);
+    (void)sizeof(Kern);
+    const BatchTables<float>& t = *static_cast<const BatchTables<float>*>(g.tables);
+    kernel<<<g.grid, g.block, 0, stream>>>(t, static_cast<const SolveDesc<float>*>(g.d_desc), g.d_tiles, g.ntiles,
+                                           parity);
+    cudaError_t err = cudaGetLastError();
+    return err == cudaSuccess ? LBM_OK : cuda_error(err, "batched step launch");
+  });
+}
+
+template <int KIND>
+lbm_status BatchLaunch<KIND>::occupancy(int store, int eq, int block, int* blocks_per_sm) {
+  using L = Lat<KIND>;
+  return batch_kernel<L>(store, eq, block, [&](auto kernel) -> lbm_status {
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, block, 0);
+    return err == cudaSuccess ? LBM_OK : cuda_error(err, "occupancy query");
   });
 }
 
@@ -517,4 +658,5 @@ lbm_status Launch<KIND>::init(lbm_model* m, const double* rho_or_phi, const doub
 }  // namespace lbm
 
 #define LBM_INSTANTIATE_LATTICE(KIND) \
-  template struct lbm::Launch<KIND>;
+  template struct lbm::Launch<KIND>;     \
+  template struct lbm::BatchLaunch<KIND>;

@@ -97,3 +97,35 @@ def random_populations(n, Q, seed, lo=0.5, hi=1.5):
 
 def random_scalar(n, seed, lo=-1.0, hi=1.0):
     return _rng(seed).uniform(lo, hi, size=tuple(reversed(n)))
+
+
+SERVING_2D = ("rD2Q17", "rD2Q21", "rD2Q25")
+SERVING_3D = ("rD3Q33", "rD3Q45", "rD3Q53-cubic")
+
+
+def serving_requests(n, seed=0, rate_per_s=50.0, steps=(200, 5000), side2d=(32, 1024), ny2d=(32, 768),
+                     side3d=(32, 160), frac_3d=0.5, frac_16bit=0.5):
+    """A seeded stream of LB solve requests: Poisson arrivals at ``rate_per_s``; half 2D
+    (rD2Q17/21/25, Taylor-Green or NCDE hill, n_x log-uniform in [32, 1024], n_y in [32, 768]),
+    half 3D Kolmogorov on cubic cells (rD3Q33/45/53, side log-uniform in [32, 160]); steps
+    uniform in [200, 5000]; storage FP32 or 16-bit. Each request is a dict."""
+    g = _rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(int(n)):
+        t += g.exponential(1.0 / rate_per_s)
+        three_d = g.random() < frac_3d
+        if three_d:
+            lat = SERVING_3D[int(g.integers(0, 3))]
+            side = int(round(np.exp(g.uniform(np.log(side3d[0]), np.log(side3d[1])))))
+            grid = (side, side, side)
+            flow = "kolmogorov"
+        else:
+            lat = SERVING_2D[int(g.integers(0, 3))]
+            grid = (int(round(np.exp(g.uniform(np.log(side2d[0]), np.log(side2d[1]))))),
+                    int(round(np.exp(g.uniform(np.log(ny2d[0]), np.log(ny2d[1]))))))
+            flow = "tgv2d" if g.random() < 0.5 else "ncde"
+        out.append(dict(rid=rid, arrival=t, lattice=lat, flow=flow, grid=grid,
+                        steps=int(g.integers(steps[0], steps[1] + 1)),
+                        store="16bit" if g.random() < frac_16bit else "f32", seed=int(seed * 100003 + rid)))
+    return out

@@ -55,6 +55,15 @@ SIGNATURES = {
     "lbm_model_counters": (c_int, [_P, _PI64, _PI64]),
     "lbm_model_synchronize": (c_int, [_P]),
     "lbm_model_destroy": (c_int, [_P]),
+    "lbm_batch_create": (c_int, [_P, c_int, POINTER(_P)]),
+    "lbm_batch_add": (c_int, [_P, _P]),
+    "lbm_batch_remove": (c_int, [_P, _P]),
+    "lbm_batch_set_tile": (c_int, [_P, c_int, c_int, c_int, c_int]),
+    "lbm_batch_step": (c_int, [_P, c_int64]),
+    "lbm_batch_counters": (c_int, [_P, _PI64, _PI64, POINTER(c_int), _PI64]),
+    "lbm_batch_stream": (c_void_p, [_P]),
+    "lbm_batch_synchronize": (c_int, [_P]),
+    "lbm_batch_destroy": (c_int, [_P]),
 }
 
 _lib = None
@@ -122,6 +131,15 @@ def _ptr(x):
         return x.data_ptr(), 1, x
     a = np.ascontiguousarray(x, dtype=np.float64)
     return a.ctypes.data, 0, a
+
+
+def workspace_bytes(lattice, eq, n, store):
+    """Device bytes a model of this lattice, equation, grid and storage needs."""
+    narr = (c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    nbytes = c_size_t()
+    _check(load().lbm_model_workspace_bytes(lattice.handle, EQS[eq], narr, DTYPES[store], byref(nbytes)),
+           "lbm_model_workspace_bytes")
+    return nbytes.value
 
 
 class Lattice:
@@ -291,6 +309,57 @@ class Model:
         if getattr(self, "handle", None):
             load().lbm_model_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many resident solves advanced together (lbm_batch_*): one persistent launch per group of
+    solves per step, steps replayed from a captured CUDA graph."""
+
+    def __init__(self, max_solves=4096, stream=None):
+        h = c_void_p()
+        _check(load().lbm_batch_create(c_void_p(stream) if stream else None, int(max_solves), byref(h)),
+               "lbm_batch_create")
+        self.handle = h
+        self.members = set()
+
+    @property
+    def stream(self):
+        return load().lbm_batch_stream(self.handle)
+
+    def add(self, model: Model):
+        _check(load().lbm_batch_add(self.handle, model.handle), "lbm_batch_add")
+        self.members.add(model)
+
+    def remove(self, model: Model):
+        _check(load().lbm_batch_remove(self.handle, model.handle), "lbm_batch_remove")
+        self.members.discard(model)
+
+    def set_tile(self, kind, store, eq, cells):
+        _check(load().lbm_batch_set_tile(self.handle, KINDS[kind], DTYPES[store], EQS[eq], int(cells)),
+               "lbm_batch_set_tile")
+
+    def step(self, nsteps=1):
+        _check(load().lbm_batch_step(self.handle, int(nsteps)), "lbm_batch_step")
+
+    def synchronize(self):
+        _check(load().lbm_batch_synchronize(self.handle), "lbm_batch_synchronize")
+
+    def counters(self):
+        s, l, g, t = c_int64(), c_int64(), c_int(), c_int64()
+        _check(load().lbm_batch_counters(self.handle, byref(s), byref(l), byref(g), byref(t)), "lbm_batch_counters")
+        return dict(steps=s.value, launches=l.value, groups=g.value, tiles=t.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().lbm_batch_destroy(self.handle)
+            self.handle = None
+            self.members = set()
 
     def __del__(self):
         try:

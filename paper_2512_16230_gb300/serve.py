@@ -1,0 +1,259 @@
+"""Serving many lattice-Boltzmann solves on one GPU.
+
+Two request loops over the same seeded request stream (``inputs.serving_requests``):
+
+* ``serve_batched`` -- continuous batching. Requests are admitted, in arrival order, as soon as
+  they have arrived and their device workspace fits the HBM budget and a slot is free; every
+  admitted solve stays resident and joins one ``lbm.Batch``, which advances all resident solves
+  together (one persistent launch per group of solves per step, steps replayed from a CUDA graph).
+  The loop advances the batch by ticks of at most ``tick`` steps, never past the earliest
+  completion, retires finished solves (their fields are read back to host memory), frees their
+  memory, and admits new arrivals between ticks. 16-bit requests are stored as FP16 deviations.
+* ``serve_sequential`` -- the plain path: one solve at a time in arrival order, FP32, each step one
+  launch of the single-solve kernel.
+
+Both record arrival, admission and completion times per request; ``summarize`` turns them into
+solves/s, latency percentiles and cell updates per second. The host logic (admission, ticks,
+retirement, accounting) is independent of the GPU: ``FakeEngine`` drives it on the CPU in tests.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import workloads as W
+
+STORE_OF = {"f32": "f32", "16bit": "f16_dev"}
+
+
+@dataclass
+class Record:
+    rid: int
+    arrival: float
+    admitted: float = float("nan")
+    finished: float = float("nan")
+    steps: int = 0
+    cells: int = 0
+    lattice: str = ""
+    store: str = ""
+    q: int = 0
+
+
+class GpuEngine:
+    """Creates, batches and retires models through the CUDA library."""
+
+    def __init__(self, max_solves=4096, tiles=None, keep_results=False):
+        from . import lbm
+        self.lbm = lbm
+        self.batch = lbm.Batch(max_solves)
+        self._lattices = {}
+        self.keep_results = keep_results
+        self.results = {}
+        for key, cells in (tiles or {}).items():
+            self.batch.set_tile(*key, cells)
+
+    def lattice(self, name):
+        if name not in self._lattices:
+            spec = W.LATTICES[name]
+            self._lattices[name] = self.lbm.Lattice(spec.kind, spec.c, spec.cs2, spec.free_w)
+        return self._lattices[name]
+
+    def nbytes(self, req, store):
+        wl = W.serving_workload(req, store)
+        return self.lbm.workspace_bytes(self.lattice(req["lattice"]), wl.eq, wl.n, store)
+
+    def create(self, req, store, stream=None):
+        wl = W.serving_workload(req, store)
+        lat = self.lattice(req["lattice"])
+        m = self.lbm.Model(lat, wl.eq, wl.n, store=store, stream=stream)
+        m.rid = req["rid"]
+        m.set_relaxation(wl.s, wl.s_high)
+        if wl.force is not None:
+            m.set_force(*wl.force)
+        if wl.u_const is not None:
+            m.set_ncde(wl.u_const, wl.nonlin)
+        rho, u = wl.fields()
+        m.init_fields(rho, u)
+        return m, m.workspace_bytes, lat.Q
+
+    def add(self, m):
+        self.batch.add(m)
+
+    def step(self, k):
+        self.batch.step(k)
+        self.batch.synchronize()
+
+    def finish(self, m):
+        self.batch.remove(m)
+        out = m.read_fields()
+        if self.keep_results:
+            self.results[m.rid] = out
+        m.close()
+
+    def run_alone(self, m, steps):
+        m.step(steps)
+        out = m.read_fields()
+        if self.keep_results:
+            self.results[m.rid] = out
+        m.close()
+
+
+class FakeEngine:
+    """CPU stand-in with the same interface: a step of the batch costs time proportional to the
+    resident cells (tests of the host logic)."""
+
+    def __init__(self, seconds_per_cell_step=1e-12, bytes_per_cell=400):
+        self.spc = seconds_per_cell_step
+        self.bpc = bytes_per_cell
+        self.resident = {}
+        self.serial = 0
+        self.steps_taken = collections.Counter()
+
+    def nbytes(self, req, store):
+        return int(np.prod(req["grid"])) * self.bpc
+
+    def create(self, req, store, stream=None):
+        self.serial += 1
+        m = self.serial
+        cells = int(np.prod(req["grid"]))
+        self.resident[m] = cells
+        return m, cells * self.bpc, 53
+
+    def add(self, m):
+        pass
+
+    def step(self, k):
+        for key in self.resident:
+            self.steps_taken[key] += k
+        time.sleep(self.spc * k * sum(self.resident.values()))
+
+    def finish(self, m):
+        self.resident.pop(m)
+
+    def run_alone(self, m, steps):
+        self.steps_taken[m] += steps
+        time.sleep(self.spc * steps * self.resident.pop(m))
+
+
+@dataclass
+class Running:
+    req: dict
+    model: object
+    nbytes: int
+    record: Record
+    done: int = 0
+
+
+def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=64, clock=time.perf_counter):
+    """Continuous batching over ``requests`` (sorted by arrival). Returns the records and the
+    elapsed wall time."""
+    pending = collections.deque(sorted(requests, key=lambda r: r["arrival"]))
+    running = []
+    records = []
+    used = 0
+    peak_used = [0]
+    t0 = clock()
+    while pending or running:
+        now = clock() - t0
+        while pending and pending[0]["arrival"] <= now and len(running) < max_resident:
+            req = pending[0]
+            store = STORE_OF[req["store"]]
+            if used + engine.nbytes(req, store) > budget_bytes and running:
+                break          # does not fit yet: admit after a retirement frees memory
+            pending.popleft()
+            m, nbytes, q = engine.create(req, store)
+            engine.add(m)
+            used += nbytes
+            rec = Record(req["rid"], req["arrival"], admitted=clock() - t0, steps=req["steps"],
+                         cells=int(np.prod(req["grid"])), lattice=req["lattice"], store=store, q=q)
+            running.append(Running(req, m, nbytes, rec))
+            peak_used[0] = max(peak_used[0], used)
+        if not running:
+            if pending:
+                time.sleep(max(0.0, pending[0]["arrival"] - (clock() - t0)))
+            continue
+        k = min(tick, min(r.req["steps"] - r.done for r in running))
+        engine.step(k)
+        for r in running:
+            r.done += k
+        still = []
+        for r in running:
+            if r.done >= r.req["steps"]:
+                engine.finish(r.model)
+                used -= r.nbytes
+                r.record.finished = clock() - t0
+                records.append(r.record)
+            else:
+                still.append(r)
+        running = still
+    serve_batched.peak_bytes = peak_used[0]
+    return records, clock() - t0
+
+
+def serve_sequential(requests, engine, store="f32", clock=time.perf_counter):
+    """One solve at a time in arrival order, FP32, one launch per step."""
+    records = []
+    t0 = clock()
+    for req in sorted(requests, key=lambda r: r["arrival"]):
+        now = clock() - t0
+        if req["arrival"] > now:
+            time.sleep(req["arrival"] - now)
+        m, nbytes, q = engine.create(req, store)
+        rec = Record(req["rid"], req["arrival"], admitted=clock() - t0, steps=req["steps"],
+                     cells=int(np.prod(req["grid"])), lattice=req["lattice"], store=store, q=q)
+        engine.run_alone(m, req["steps"])
+        rec.finished = clock() - t0
+        records.append(rec)
+    return records, clock() - t0
+
+
+def summarize(records, elapsed):
+    lat = np.array([r.finished - r.arrival for r in records])
+    cell_updates = float(sum(r.cells * r.steps for r in records))
+    # algorithmic bytes: every population read once and written once per cell update
+    nbytes = float(sum(r.cells * r.steps * 2 * r.q * (4 if r.store == "f32" else 2) for r in records))
+    return {
+        "solves": len(records),
+        "elapsed_s": elapsed,
+        "solves_per_s": len(records) / elapsed if elapsed > 0 else float("nan"),
+        "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else float("nan"),
+        "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else float("nan"),
+        "mlups": cell_updates / elapsed / 1e6 if elapsed > 0 else float("nan"),
+        "algorithmic_gb_per_s": nbytes / elapsed / 1e9 if elapsed > 0 else float("nan"),
+    }
+
+
+def main(argv=None):
+    """Serve the seeded request stream (config 5) and print one JSON object with both paths."""
+    import argparse
+    import json
+
+    from . import autotune
+    from . import inputs as I
+    ap = argparse.ArgumentParser(description="continuous-batching LB solve server vs the plain FP32 path")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=20.0, help="mean arrivals per second (Poisson)")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--tick", type=int, default=64)
+    ap.add_argument("--skip-sequential", action="store_true")
+    a = ap.parse_args(argv)
+    reqs = I.serving_requests(a.requests, seed=a.seed, rate_per_s=a.rate)
+    tiles = autotune.autotune()
+    eng = GpuEngine(tiles=tiles)
+    rec_b, t_b = serve_batched(reqs, eng, budget_bytes=a.budget_gb * 1e9, tick=a.tick)
+    out = {"requests": a.requests, "rate_per_s": a.rate, "seed": a.seed,
+           "batched": dict(summarize(rec_b, t_b), peak_resident_gb=serve_batched.peak_bytes / 1e9,
+                           batched_launches=eng.batch.counters()["launches"])}
+    eng.batch.close()
+    if not a.skip_sequential:
+        rec_s, t_s = serve_sequential(reqs, GpuEngine(), store="f32")
+        out["sequential_fp32"] = summarize(rec_s, t_s)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -149,3 +149,24 @@ def kolmogorov_3d(lattice="rD3Q53-cubic", n=(32, 32, 32), steps=200, store="f32"
     A = umax * nu * (2 * math.pi / ly) ** 2
     return Workload(f"{lat.kind} Kolmogorov 3D", lat, "nse", tuple(n), steps, rates_nse(3, nu, lat.cs2[0]),
                     store=store, force=(0, 1, A, 1, 0.0), init=dict(kind="rest"))
+
+
+def serving_workload(req, store):
+    """The Workload of one serving request (see inputs.serving_requests): 2D Taylor-Green at
+    Re = 100 and u0 = 0.05 c_s, 2D nonlinear CDE hill (D0 = 0.1, sigma = n_x / 8, u = (0.02, 0.01)),
+    or 3D Kolmogorov flow with nu = 0.05 and steady u_max = 0.05 c_s."""
+    n = tuple(req["grid"])
+    if req["flow"] == "kolmogorov":
+        wl = kolmogorov_3d(lattice=req["lattice"], n=n, steps=req["steps"], store=store)
+    elif req["flow"] == "tgv2d":
+        lat = LATTICES[req["lattice"]]
+        u0 = 0.05 * math.sqrt(lat.cs2[0])
+        nu = u0 * (n[0] * lat.c[0] / (2 * math.pi)) / 100.0
+        wl = Workload(f"{lat.kind} Taylor-Green 2D", lat, "nse", n, req["steps"], rates_nse(2, nu, lat.cs2[0]),
+                      store=store, init=dict(kind="tgv2d", u0=u0, nu=nu))
+    else:
+        lat = LATTICES[req["lattice"]]
+        wl = Workload(f"{lat.kind} nonlinear CDE", lat, "ncde", n, req["steps"], rates_ncde(2, 0.1, lat.cs2[0]),
+                      store=store, u_const=(0.02, 0.01), nonlin=1.0,
+                      init=dict(kind="hill", sigma=max(2.0, n[0] / 8.0), noise=1e-3, seed=req["seed"]))
+    return wl

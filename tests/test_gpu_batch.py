@@ -1,0 +1,156 @@
+"""The batched engine (lbm_batch_*, persistent kernel over a tile work-list, CUDA-graph steps)
+gives the same solves as the single-solve path and as the oracle, whatever the mix."""
+import numpy as np
+import pytest
+
+from paper_2512_16230_gb300 import inputs as I
+from paper_2512_16230_gb300 import workloads as W
+
+from _harness import gpu_model, oracle_model, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _lib(lbm_lib):
+    return lbm_lib
+
+
+# (lattice, eq, grid, store): several groups, ragged tiles, 2D and 3D, NSE with force and NCDE
+MIX = [
+    ("rD2Q25", "nse", (37, 29), "f32"),
+    ("rD2Q25", "nse", (20, 41), "f32"),
+    ("rD2Q17", "ncde", (33, 40), "f32"),
+    ("rD2Q21", "nse", (31, 17), "f16_dev"),
+    ("rD3Q53-cubic", "nse", (13, 11, 9), "f32"),
+    ("rD3Q45", "nse", (12, 10, 8), "f16_dev"),
+    ("rD3Q33", "nse", (10, 9, 8), "bf16_dev"),
+    ("rD3Q53", "nse", (9, 10, 11), "f32"),
+]
+
+
+def _make(lat_cache, name, eq, n, store, seed):
+    from paper_2512_16230_gb300 import lbm
+    spec = W.LATTICES[name]
+    if name not in lat_cache:
+        lat_cache[name] = lbm.Lattice(spec.kind, spec.c, spec.cs2, spec.free_w)
+    lat = lat_cache[name]
+    s = np.random.default_rng(seed).uniform(0.8, 1.8, spec.R)
+    d = spec.d
+    kw = {}
+    if eq == "nse":
+        kw["force"] = (0, d - 1, 2e-4, 1, 0.3)
+    else:
+        kw["u_const"] = tuple([0.03, 0.02, 0.01][:d])
+        kw["nonlin"] = 1.0
+    m = gpu_model(spec, eq, n, s, 1.1, store=store, lat=lat, **kw)
+    if eq == "nse":
+        rho, u = I.random_fields(n, d, seed=seed, rho_amp=0.01, u_amp=0.03)
+        m.init_fields(rho, u)
+    else:
+        m.init_fields(I.gaussian_hill(n, spec.c, max(2.0, n[0] / 6), 1.0, noise=1e-3, seed=seed))
+    return m
+
+
+def _compare(a, b, store):
+    ra, ua = a.read_fields()
+    rb, ub = b.read_fields()
+    tol = 1e-6 if store == "f32" else 2e-3
+    assert rel_l2(ra, rb) <= tol
+    if ua is not None:
+        assert rel_l2(ua, ub) <= tol
+    return np.array_equal(ra, rb) and (ua is None or np.array_equal(ua, ub))
+
+
+def test_batch_equals_single_solve_path():
+    from paper_2512_16230_gb300 import lbm
+    cache = {}
+    alone = [_make(cache, *spec, seed=i) for i, spec in enumerate(MIX)]
+    batched = [_make(cache, *spec, seed=i) for i, spec in enumerate(MIX)]
+    b = lbm.Batch(64)
+    for m in batched:
+        b.add(m)
+    b.step(13)          # one 8-step graph replay, then 5 direct launches (odd: buffers swap)
+    b.synchronize()
+    for m in alone:
+        m.step(13)
+    c = b.counters()
+    assert c["groups"] == len({(name, st) for name, _, _, st in MIX}) and c["steps"] == 13
+    exact = [_compare(x, y, spec[3]) for x, y, spec in zip(alone, batched, MIX)]
+    # membership changes: drop two solves, add a fresh one, keep stepping
+    b.remove(batched[1])
+    b.remove(batched[4])
+    extra_alone = _make(cache, "rD3Q33", "nse", (8, 8, 8), "f32", seed=99)
+    extra_batched = _make(cache, "rD3Q33", "nse", (8, 8, 8), "f32", seed=99)
+    b.add(extra_batched)
+    b.step(10)
+    b.synchronize()
+    for i, m in enumerate(alone):
+        if i not in (1, 4):
+            m.step(10)
+    extra_alone.step(10)
+    for i, (x, y, spec) in enumerate(zip(alone, batched, MIX)):
+        if i not in (1, 4):
+            _compare(x, y, spec[3])
+    _compare(extra_alone, extra_batched, "f32")
+    # the removed members kept their state and can be stepped alone again
+    batched[1].step(3)
+    alone[1].step(3)
+    _compare(alone[1], batched[1], "f32")
+    print("bit-identical to the single-solve path:", exact)
+    b.close()
+
+
+def test_model_in_batch_is_advanced_only_by_the_batch():
+    from paper_2512_16230_gb300 import lbm
+    m = _make({}, "rD2Q13", "nse", (16, 12), "f32", seed=1)
+    b = lbm.Batch(4)
+    b.add(m)
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        m.step(1)
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        b.add(m)
+    b.close()
+    m.step(1)
+
+
+def test_batched_solve_against_the_oracle():
+    """A Kolmogorov flow (rD3Q45, forced through M2G) advanced in a batch with other solves,
+    against the FP64 oracle: FP32 parity bound 1e-5."""
+    from paper_2512_16230_gb300 import lbm
+    wl = W.kolmogorov_3d(lattice="rD3Q45", n=(12, 16, 10), steps=40, store="f32")
+    om = oracle_model(wl.lattice, wl.eq, wl.n, wl.s, wl.s_high, force=wl.force)
+    gm = gpu_model(wl.lattice, wl.eq, wl.n, wl.s, wl.s_high, force=wl.force, store="f32")
+    rho, u = wl.fields()
+    om.init_fields(rho, u)
+    gm.init_fields(rho, u)
+    other = _make({}, "rD3Q45", "nse", (9, 9, 9), "f32", seed=5)
+    b = lbm.Batch(4)
+    b.add(gm)
+    b.add(other)
+    b.step(wl.steps)
+    b.synchronize()
+    om.step(wl.steps)
+    assert rel_l2(gm.get_populations(), om.f) <= 1e-5
+    b.close()
+
+
+def test_serving_results_same_alone_and_in_the_mix():
+    """Continuous batching: every request of a small seeded mix, served together with the others,
+    gives the same fields as the same request run alone (FP32 <= 1e-6, FP16 <= 2e-3 relative)."""
+    from paper_2512_16230_gb300 import serve as S
+    reqs = I.serving_requests(24, seed=11, rate_per_s=2000.0, steps=(20, 90), side2d=(16, 48), ny2d=(16, 40),
+                              side3d=(8, 20))
+    mixed = S.GpuEngine(keep_results=True)
+    recs, _ = S.serve_batched(reqs, mixed, tick=16)
+    assert len(recs) == len(reqs)
+    alone = S.GpuEngine(keep_results=True)
+    for req in reqs:
+        m, _, _ = alone.create(req, S.STORE_OF[req["store"]])
+        alone.run_alone(m, req["steps"])
+    for req in reqs:
+        a, b = alone.results[req["rid"]], mixed.results[req["rid"]]
+        tol = 1e-6 if req["store"] == "f32" else 2e-3
+        assert rel_l2(b[0], a[0]) <= tol, req
+        if a[1] is not None:
+            assert rel_l2(b[1], a[1]) <= tol, req

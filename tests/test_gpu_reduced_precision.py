@@ -33,8 +33,9 @@ def _report(key, value):
         json.dump(data, open(OUT, "w"), indent=1)
 
 
-@pytest.mark.parametrize("store,bound", [("bf16_dev", 5e-2), ("f16_dev", 5e-3), ("f32", 1e-5)])
-def test_taylor_green_3d_copy_per_dtype(store, bound):
+@pytest.mark.parametrize("store,bound,rho_bound", [("bf16_dev", 6e-3, 3e-4), ("f16_dev", 1e-3, 5e-5),
+                                                   ("f32", 1e-5, 1e-5)])
+def test_taylor_green_3d_copy_per_dtype(store, bound, rho_bound):
     """Config 4 error study: the rD3Q53 Taylor-Green copy (48 x 48 x 36, Ma 0.3, Re 1600, 188 steps)
     with each storage dtype against the FP64 oracle: relative L2 of u and rho."""
     wl = W.taylor_green_3d(n=(48, 48, 36), steps=188)
@@ -47,10 +48,10 @@ def test_taylor_green_3d_copy_per_dtype(store, bound):
     _report(f"tgv3d_48x48x36_188steps_{store}", {"u_rel_l2": eu, "rho_rel_l2": er})
     print(f"{store}: u rel L2 {eu:.3e}, rho rel L2 {er:.3e}")
     assert eu <= bound
-    assert er <= bound
+    assert er <= rho_bound
 
 
-@pytest.mark.parametrize("store,bound", [("bf16_dev", 1e-2), ("f16_dev", 2e-3)])
+@pytest.mark.parametrize("store,bound", [("bf16_dev", 5e-3), ("f16_dev", 7e-4)])
 def test_kolmogorov_serving_flow_per_dtype(store, bound):
     """A serving-mix flow (3D Kolmogorov on cubic rD3Q45 cells, forced through M2G) after 300
     steps: velocity error of reduced storage against the FP64 oracle."""
@@ -81,3 +82,43 @@ def test_deviation_roundtrip(store):
     rel, absl = (2.0 ** -8, 0.0) if store == "bf16_dev" else (2.0 ** -11, 2.0 ** -25)
     bound = rel * dev + absl + 2.0 ** -22 * np.abs(f0)
     assert np.all(np.abs(got - f0) <= bound)
+
+
+def _round_bf16(x32):
+    """float32 -> bfloat16 (round to nearest even) -> float64, on the host."""
+    b = np.ascontiguousarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return b.view(np.float32).astype(np.float64)
+
+
+def _stored_deviation(f, w, store):
+    """The deviation the library stores for f: FP32 difference f - w rounded to the format."""
+    dev32 = np.float32(f).astype(np.float32) - np.float32(w).astype(np.float32)
+    if store == "f16_dev":
+        return dev32.astype(np.float16).astype(np.float64)
+    return _round_bf16(dev32)
+
+
+@pytest.mark.parametrize("store,unit", [("bf16_dev", 2.0 ** -8), ("f16_dev", 2.0 ** -11)])
+@pytest.mark.parametrize("name", ["rD2Q25", "rD3Q53"])
+def test_deviation_storage_one_step(name, store, unit):
+    """One collide-stream step in deviation storage: the kernel collides the deviations directly
+    (reference moments added back, s_h rho_ref folded into h_0). Against the FP64 oracle from the
+    same stored input, the error of the new deviations f - w is bounded by the rounding of the
+    input and of the output (each <= unit relative), times the O(1) gain of the collision."""
+    spec = W.LATTICES[name]
+    d = spec.d
+    n = (37, 29) if d == 2 else (13, 11, 9)
+    s = np.random.default_rng(1).uniform(0.6, 1.9, spec.R)
+    gm = gpu_model(spec, "nse", n, s, 1.3, store=store, force=(0, d - 1, 1e-3, 1, 0.2))
+    om = oracle_model(spec, "nse", n, s, 1.3, force=(0, d - 1, 1e-3, 1, 0.2))
+    w = om.lat.w.reshape((-1,) + (1,) * d)
+    r = np.random.default_rng(5).uniform(-0.1, 0.1, size=(gm.Q,) + n[::-1])
+    f_in = w * (1.0 + r)
+    gm.set_populations(f_in)
+    om.set_populations(w + _stored_deviation(f_in, w, store))   # the value the GPU holds
+    gm.step(1)
+    om.step(1)
+    err = rel_l2(gm.get_populations() - w, om.f - w)
+    print(f"{name} {store}: deviation rel L2 after one step {err:.2e}")
+    assert err <= 4 * unit

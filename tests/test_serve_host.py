@@ -1,0 +1,67 @@
+"""Host logic of the serving loops (admission, ticks, retirement, accounting) on the CPU with the
+fake engine: every request runs exactly its steps, arrivals are admitted in order, the memory
+budget and the slot limit hold, and the summary is consistent."""
+import numpy as np
+
+from paper_2512_16230_gb300 import inputs as I
+from paper_2512_16230_gb300 import serve as S
+
+
+def _requests(n=40, rate=400.0):
+    return I.serving_requests(n, seed=3, rate_per_s=rate, steps=(5, 40), side2d=(8, 32), ny2d=(8, 32),
+                              side3d=(8, 16))
+
+
+def test_request_stream_is_seeded_and_shaped():
+    a = I.serving_requests(200, seed=7)
+    b = I.serving_requests(200, seed=7)
+    assert a == b
+    arr = np.array([r["arrival"] for r in a])
+    assert np.all(np.diff(arr) > 0)
+    assert {r["lattice"] for r in a} <= set(I.SERVING_2D + I.SERVING_3D)
+    for r in a:
+        assert 200 <= r["steps"] <= 5000
+        if len(r["grid"]) == 3:
+            assert 32 <= r["grid"][0] <= 160 and r["flow"] == "kolmogorov"
+        else:
+            assert 32 <= r["grid"][0] <= 1024 and 32 <= r["grid"][1] <= 768
+
+
+def test_batched_loop_runs_every_step_and_respects_limits():
+    reqs = _requests()
+    eng = S.FakeEngine(seconds_per_cell_step=2e-9, bytes_per_cell=100)
+    budget = 3 * 32 * 32 * 100
+    seen = []
+    orig_add = eng.add
+
+    def add(m):
+        seen.append(len(eng.resident))
+        orig_add(m)
+    eng.add = add
+    recs, elapsed = S.serve_batched(reqs, eng, budget_bytes=budget, max_resident=4, tick=7)
+    assert sorted(r.rid for r in recs) == [r["rid"] for r in reqs]
+    assert max(seen) <= 4
+    largest = max(eng.nbytes(r, "f32") for r in reqs)
+    # over-budget requests are only admitted alone (otherwise they would starve)
+    assert S.serve_batched.peak_bytes <= max(budget, largest)
+    for r in recs:
+        assert r.arrival <= r.admitted <= r.finished <= elapsed
+    by_rid = {r["rid"]: r for r in reqs}
+    # every model ran exactly its requested number of steps
+    assert sorted(eng.steps_taken.values()) == sorted(by_rid[r.rid]["steps"] for r in recs)
+    # admission follows arrival order
+    adm = sorted(recs, key=lambda r: r.admitted)
+    assert [r.rid for r in adm] == sorted(r.rid for r in recs)
+
+
+def test_sequential_loop_and_summary():
+    reqs = _requests(n=12)
+    eng = S.FakeEngine(seconds_per_cell_step=1e-9)
+    recs, elapsed = S.serve_sequential(reqs, eng)
+    assert [r.rid for r in recs] == [r["rid"] for r in reqs]
+    s = S.summarize(recs, elapsed)
+    assert s["solves"] == 12
+    assert s["latency_p50_s"] <= s["latency_p99_s"]
+    assert s["solves_per_s"] == 12 / elapsed
+    cells = sum(np.prod(r["grid"]) * r["steps"] for r in reqs)
+    assert abs(s["mlups"] - cells / elapsed / 1e6) < 1e-9 * s["mlups"]
