@@ -27,6 +27,13 @@ struct GroupHost {
 
 }  // namespace
 
+struct DeviceBuffers {
+  void* desc = nullptr;
+  size_t desc_cap = 0;
+  void* tiles = nullptr;
+  size_t tiles_cap = 0;
+};
+
 struct lbm_batch {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -37,8 +44,11 @@ struct lbm_batch {
   std::vector<GroupHost> groups;
   std::map<std::tuple<int, int, int>, int> tile;  // (kind, store, eq) -> cells per tile
   bool dirty = true;
+  bool stable = false;  // no change since the last step call: capture a graph
   cudaGraphExec_t graph = nullptr;
-  int64_t steps = 0, launches = 0;
+  // work-list buffers by group key, kept across rebuilds and grown geometrically
+  std::map<std::tuple<const lbm_lattice*, int, int>, DeviceBuffers> buffers;
+  int64_t steps = 0, launches = 0, rebuilds = 0, captures = 0;
 };
 
 namespace lbm {
@@ -63,16 +73,34 @@ lbm_status dispatch_batch_kind(int kind, F&& f) {
   return set_error(LBM_ERR_ARG, "unknown lattice kind");
 }
 
-void free_groups(lbm_batch* b) {
-  for (auto& gh : b->groups) {
-    if (gh.g.d_desc) cudaFree(gh.g.d_desc);
-    if (gh.g.d_tiles) cudaFree(gh.g.d_tiles);
-  }
-  b->groups.clear();
+void drop_graph(lbm_batch* b) {
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
+}
+
+void free_groups(lbm_batch* b) {
+  b->groups.clear();
+  drop_graph(b);
+}
+
+void free_buffers(lbm_batch* b) {
+  for (auto& kv : b->buffers) {
+    if (kv.second.desc) cudaFree(kv.second.desc);
+    if (kv.second.tiles) cudaFree(kv.second.tiles);
+  }
+  b->buffers.clear();
+}
+
+cudaError_t ensure(void** ptr, size_t* cap, size_t bytes) {
+  if (bytes <= *cap) return cudaSuccess;
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  size_t want = std::max(bytes, *cap * 2);
+  cudaError_t err = cudaMalloc(ptr, want);
+  *cap = err == cudaSuccess ? want : 0;
+  return err;
 }
 
 void fill_desc(const lbm_model* m, SolveDesc<float>* d) {
@@ -157,8 +185,12 @@ lbm_status rebuild(lbm_batch* b) {
     }
     gh.g.nsolves = int(gh.members.size());
     gh.g.ntiles = int(tiles.size());
-    cudaError_t err = cudaMalloc(&gh.g.d_desc, gh.desc.size() * sizeof(SolveDesc<float>));
-    if (err == cudaSuccess) err = cudaMalloc(&gh.g.d_tiles, tiles.size() * sizeof(Tile));
+    DeviceBuffers& buf = b->buffers[std::make_tuple(gh.g.lat, gh.g.store, gh.g.eq)];
+    cudaError_t err = cudaStreamSynchronize(b->stream);   // the previous work-list may still be read
+    if (err == cudaSuccess) err = ensure(&buf.desc, &buf.desc_cap, gh.desc.size() * sizeof(SolveDesc<float>));
+    if (err == cudaSuccess) err = ensure(&buf.tiles, &buf.tiles_cap, tiles.size() * sizeof(Tile));
+    gh.g.d_desc = buf.desc;
+    gh.g.d_tiles = static_cast<Tile*>(buf.tiles);
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(gh.g.d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
                             b->stream);
@@ -173,6 +205,14 @@ lbm_status rebuild(lbm_batch* b) {
     if (st != LBM_OK) return st;
     gh.g.grid = std::max(1, std::min(gh.g.ntiles, std::max(1, per_sm) * b->num_sms));
   }
+  b->dirty = false;
+  b->stable = false;
+  b->rebuilds += 1;
+  return LBM_OK;
+}
+
+lbm_status capture(lbm_batch* b) {
+  drop_graph(b);
   if (!b->groups.empty()) {
     cudaGraph_t graph = nullptr;
     cudaError_t err = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
@@ -191,7 +231,7 @@ lbm_status rebuild(lbm_batch* b) {
     cudaGraphDestroy(graph);
     if (err != cudaSuccess) return cuda_error(err, "graph instantiation");
   }
-  b->dirty = false;
+  b->captures += 1;
   return LBM_OK;
 }
 
@@ -286,9 +326,14 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
   if (b->dirty) {
     lbm_status st = rebuild(b);
     if (st != LBM_OK) return st;
+  } else if (b->stable && !b->graph && nsteps >= kChunk) {
+    // membership unchanged over a whole call: capture the steps in a graph from now on
+    lbm_status st = capture(b);
+    if (st != LBM_OK) return st;
   }
-  const int64_t chunks = nsteps / kChunk;
-  const int rem = int(nsteps % kChunk);
+  const bool use_graph = b->graph != nullptr;
+  const int64_t chunks = use_graph ? nsteps / kChunk : 0;
+  const int rem = int(nsteps - chunks * kChunk);
   for (int64_t c = 0; c < chunks; ++c) {
     cudaError_t err = cudaGraphLaunch(b->graph, b->stream);
     if (err != cudaSuccess) return cuda_error(err, "batch graph launch");
@@ -315,6 +360,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
   }
   b->steps += nsteps;
   b->launches += nsteps * int64_t(b->groups.size());
+  b->stable = true;
   return LBM_OK;
 }
 
@@ -349,6 +395,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
     m->batch = nullptr;
   }
   free_groups(b);
+  free_buffers(b);
   if (b->owns_stream) cudaStreamDestroy(b->stream);
   delete b;
   return LBM_OK;

@@ -147,8 +147,11 @@ class Running:
     done: int = 0
 
 
-def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=64, clock=time.perf_counter):
-    """Continuous batching over ``requests`` (sorted by arrival). Returns the records and the
+def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=64, clock=time.perf_counter,
+                  store_policy="as_requested"):
+    """Continuous batching over ``requests`` (sorted by arrival). ``store_policy``: "as_requested"
+    (FP32 requests in FP32, 16-bit ones as FP16 deviations) or a storage name applied to every
+    request (e.g. "f16_dev": the reduced-precision serving path). Returns the records and the
     elapsed wall time."""
     pending = collections.deque(sorted(requests, key=lambda r: r["arrival"]))
     running = []
@@ -160,7 +163,7 @@ def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=6
         now = clock() - t0
         while pending and pending[0]["arrival"] <= now and len(running) < max_resident:
             req = pending[0]
-            store = STORE_OF[req["store"]]
+            store = STORE_OF[req["store"]] if store_policy == "as_requested" else store_policy
             if used + engine.nbytes(req, store) > budget_bytes and running:
                 break          # does not fit yet: admit after a retirement frees memory
             pending.popleft()
@@ -240,15 +243,18 @@ def main(argv=None):
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--tick", type=int, default=64)
     ap.add_argument("--skip-sequential", action="store_true")
+    ap.add_argument("--policies", default="f16_dev,as_requested",
+                    help="comma-separated storage policies of the batched path")
     a = ap.parse_args(argv)
     reqs = I.serving_requests(a.requests, seed=a.seed, rate_per_s=a.rate)
     tiles = autotune.autotune()
-    eng = GpuEngine(tiles=tiles)
-    rec_b, t_b = serve_batched(reqs, eng, budget_bytes=a.budget_gb * 1e9, tick=a.tick)
-    out = {"requests": a.requests, "rate_per_s": a.rate, "seed": a.seed,
-           "batched": dict(summarize(rec_b, t_b), peak_resident_gb=serve_batched.peak_bytes / 1e9,
-                           batched_launches=eng.batch.counters()["launches"])}
-    eng.batch.close()
+    out = {"requests": a.requests, "rate_per_s": a.rate, "seed": a.seed}
+    for policy in a.policies.split(","):
+        eng = GpuEngine(tiles=tiles)
+        rec_b, t_b = serve_batched(reqs, eng, budget_bytes=a.budget_gb * 1e9, tick=a.tick, store_policy=policy)
+        out[f"batched_{policy}"] = dict(summarize(rec_b, t_b), peak_resident_gb=serve_batched.peak_bytes / 1e9,
+                                        batched_launches=eng.batch.counters()["launches"])
+        eng.batch.close()
     if not a.skip_sequential:
         rec_s, t_s = serve_sequential(reqs, GpuEngine(), store="f32")
         out["sequential_fp32"] = summarize(rec_s, t_s)
