@@ -116,6 +116,18 @@ lbm_status lbm_lattice_create(lbm_kind kind, const double* c, const double* cs2,
 lbm_status lbm_lattice_query(const lbm_lattice* lat, int* d, int* Q, int* R, int8_t* e,
                              double* w, double* H, double* N, double* T);
 
+/* Rows of order >= 4 that complete the Q x Q Hermite matrix (the paper leaves them to the
+ * designer, Sec. 5 / App. D): monomials of degree 4, 5, ... kept in graded order when they raise
+ * the rank, each W-orthogonalised against every earlier row, so that the rows of order k span
+ * the W-orthogonal complement of the orders < k within the lattice functions of degree <= k.
+ * Built in FP64 by lbm_lattice_create. Every output pointer may be NULL.
+ *   n_high        Q - R;   orders[n_high]: the order of each row (even orders first, then odd)
+ *   H[n_high*Q]   the rows on the lattice (row-major, each scaled to unit max);  N[n_high]: W-norms
+ * Errors: LBM_ERR_ARG (NULL lattice), LBM_ERR_LATTICE_INFEASIBLE (a row has zero W-norm because
+ *         some weights are zero, or the monomials do not reach rank Q). */
+lbm_status lbm_lattice_query_high(const lbm_lattice* lat, int* n_high, int* orders, double* H,
+                                  double* N);
+
 lbm_status lbm_lattice_destroy(lbm_lattice* lat);
 
 /* ------------------------------------------------------------------------------------------
@@ -145,6 +157,23 @@ lbm_status lbm_model_create(const lbm_lattice* lat, lbm_eq eq, const int64_t* n,
  * nu = cs2_eq (1/s_2 - 1/2) (Eq. (4-29), compressible, k = 0); the NCDE diffusivity is
  * K = cs2_eq (1/s_1 - 1/2) (Eq. (ME-NCDE-3)). */
 lbm_status lbm_model_set_relaxation(lbm_model* m, const double* s, double s_high);
+
+/* Independent bulk viscosity (NSE): the normal second-order moments relax with the inverse of
+ * S2^(1) = diag(1/s_sa) + a 1^T / d, a_a = 1/s_bulk - 1/s_sa (Eq. (4-27) read for the multispeed
+ * lattices, k = 0), where s_sa are the rates set for the normal rows c_a^2 - c_sa^2; then
+ * mu = (1/s_s - 1/2) p dt and mu_b = (2/d)(1/s_bulk - 1/2) p dt (Eq. (4-29)). The same block
+ * enters (I - S2/2) M2G. s_bulk <= 0 restores the diagonal relaxation (mu_b = 2 mu / d). */
+lbm_status lbm_model_set_bulk(lbm_model* m, double s_bulk);
+
+/* Rates of the rows of order >= 4, one per order (Eq. (H-MRT-LB) with the full Q x Q Hermite
+ * matrix; the higher rows as in lbm_lattice_query_high): s_order[k] is the rate of order 4 + k,
+ * k < n_orders <= 9; the orders not given relax with s_high. Rates must lie in (0, 2]. Since the
+ * equilibrium and the sources have no moments of order >= 4, the update adds
+ * -w_i sum_r (s_r - s_high) H_r(c_i) (sum_j H_r(c_j) f_j) / N_r over those rows, which costs the
+ * step two more contractions with them. n_orders = 0 restores the shared rate.
+ * Errors: LBM_ERR_ARG, LBM_ERR_LATTICE_INFEASIBLE (lattice without complete higher rows),
+ *         LBM_ERR_NOT_IMPLEMENTED (the model is in a batch). */
+lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_orders);
 
 /* Equation of state p = rho * cs2_eq (NSE, Eq. (M-NSEs-6-1)) or the prefactor of the diffusion
  * moment M2 = cs2_eq D(phi) I (NCDE, Eq. (M-NCDE-6)). */

@@ -16,7 +16,9 @@ Parity status of each function (pins live in ``tests/test_oracle_*.py``):
 * equilibrium (Eq. (feq-1)): pinned by the continuous moments up to third order and f^eq(rho,0)
   = w rho;
 * collision (Eq. (2-3), Eq. (H-MRT-LB)): pinned by exact mass and momentum conservation, the
-  block form Eq. (H-MRT-LB-1), S = I and the BGK special case;
+  block form Eq. (H-MRT-LB-1), S = I and the BGK special case; distinct rates of the orders >= 4
+  by projectors built independently from all monomials of each degree; the bulk block of
+  Eq. (4-27) by the sound-wave damping of Eq. (4-29) and its diagonal special case;
 * streaming (Eq. (2-2b)): pinned by delta transport and reversibility;
 * dynamics: pinned by Taylor-Green decay at nu = cs2 (1/s - 1/2), Kolmogorov steady flow, and
   Gaussian-hill diffusion of the linear NCDE.

@@ -18,8 +18,9 @@ Everything here follows Sec. 5 and Appendices C/D of Shi, Yuan & Chai (arXiv 251
   (2D) and App. D (3D);
 * rows of order >= 4 (left to the modeller by App. C/D) taken from the paper's own lists where it
   prints one (rD2Q13: Eq. (TransM); rD3Q33: the symbolic rows M21..M33 of App. D), otherwise
-  graded monomials kept greedily when they raise the rank, each W-orthogonalised against H0..H3
-  so that HWH^T is block diagonal as Sec. 4 requires.
+  graded monomials kept greedily when they raise the rank; the rows of degree k are
+  W-orthogonalised against every row of lower degree, so that HWH^T is block diagonal as Sec. 4
+  requires and each order k >= 4 is a block that can carry its own rate.
 
 Polynomials are dicts {exponent tuple: coefficient} in the physical velocity c = diag(c_a) e.
 """
@@ -333,6 +334,7 @@ class Lattice:
     corr: dict             # rectangular-correction projection coefficients
     Hfull: np.ndarray      # (Q, Q) full Hermite matrix: H0..H3 then W-orthogonalised higher rows
     high_monomials: list = field(default_factory=list)
+    full_orders: list = field(default_factory=list)   # order (degree) of every row of Hfull
 
     @property
     def Q(self):
@@ -366,30 +368,55 @@ def build_from(kind, d, c, cs2, e, w, correct=True, high_rows=None) -> Lattice:
     H = np.stack([poly_eval(p, cvel) for p in polys])
     orders = row_orders(d)
     Q = e.shape[0]
-    # Higher rows: W-orthogonal to H0..H3 (so HWH^T is block diagonal, Sec. 4), kept when
-    # they raise the rank of the full matrix.
-    norms = np.sum(w[None, :] * H * H, axis=1)
+    # Higher rows, graded by degree: the order-k block is the W-orthogonal complement of all rows of
+    # lower degree inside the span of the monomials of degree <= k on the lattice (a subspace fixed
+    # by the lattice alone, so a rate per order is well defined whichever monomials are listed).
+    # Candidates come from the paper's lists where printed, otherwise graded monomials; a
+    # candidate is kept when it raises the rank.
     cands = high_rows if high_rows is not None else HIGH_ROWS_PRINTED.get(kind)
     cands = list(cands) if cands is not None else list(graded_monomials(d, 4))
-    high, chosen = [], []
-    for ex in cands:
-        v = poly_eval({tuple(ex): 1.0}, cvel)
-        v = v - sum((np.sum(w * v * H[r]) / norms[r]) * H[r] for r in range(H.shape[0]))
-        trial = np.vstack([H] + high + [v[None, :]])
-        if np.linalg.matrix_rank(trial, tol=1e-9 * np.abs(trial).max()) == trial.shape[0]:
-            high.append((v / np.abs(v).max())[None, :])
-            chosen.append(tuple(ex))
-        if H.shape[0] + len(high) == Q:
+    cands = sorted(cands, key=sum)
+    rows = [H[r] for r in range(H.shape[0])]
+    degs = list(orders)
+    chosen = []
+    for deg in sorted({sum(ex) for ex in cands}):
+        block = []
+        for ex in [c for c in cands if sum(c) == deg]:
+            v = poly_eval({tuple(ex): 1.0}, cvel)
+            v = v / np.abs(v).max()
+            trial = np.vstack(rows + block + [v[None, :]])
+            if np.linalg.matrix_rank(trial, tol=1e-9 * np.abs(trial).max()) == trial.shape[0]:
+                block.append(v)
+                chosen.append(tuple(ex))
+            if len(rows) + len(block) == Q:
+                break
+        if not block:
+            continue
+        # W-orthogonalise the block against every lower-degree row (block-diagonal H W H^T, Sec. 4),
+        # then take an orthonormal basis of its span (any basis of the block gives the same
+        # collision when the block shares one rate)
+        prev = np.vstack(rows)
+        G = (prev * w) @ prev.T
+        B = np.vstack(block)
+        # (pseudo-inverse: G is singular when a weight class is zero and the rows outnumber the
+        # velocities of non-zero weight; the projection is then still W-orthogonal)
+        # (applied twice: one projection in floating point leaves O(eps cond) overlap)
+        Gi = np.linalg.pinv(G, rcond=1e-13)
+        for _ in range(2):
+            B = B - ((B * w) @ prev.T) @ Gi @ prev
+        qmat, _ = np.linalg.qr(B.T)
+        for q in qmat.T:
+            rows.append(q)
+            degs.append(deg)
+        if len(rows) == Q:
             break
-    if H.shape[0] + len(high) != Q:
-        raise ValueError(f"{kind}: could not complete the Hermite matrix ({H.shape[0] + len(high)} of {Q})")
-    # Any basis of the higher block gives the same collision when those rows share one rate;
-    # an orthonormal one (plain Euclidean QR of the rows) keeps H well conditioned. Linear
-    # combinations of rows W-orthogonal to H0..H3 stay W-orthogonal to them.
-    qmat, _ = np.linalg.qr(np.vstack(high).T)
-    Hfull = np.vstack([H, qmat.T])
+    if len(rows) != Q:
+        raise ValueError(f"{kind}: could not complete the Hermite matrix ({len(rows)} of {Q})")
+    Hfull = np.vstack(rows)
+    high_orders = degs
     return Lattice(kind=kind, d=d, c=np.asarray(c), cs2=np.asarray(cs2), e=e, cvel=cvel, w=w,
-                   polys=polys, H=H, orders=orders, corr=coefs, Hfull=Hfull, high_monomials=chosen)
+                   polys=polys, H=H, orders=orders, corr=coefs, Hfull=Hfull, high_monomials=chosen,
+                   full_orders=high_orders)
 
 
 def hermite_inverse(lat: Lattice) -> np.ndarray:

@@ -23,7 +23,11 @@ Readings of points the paper leaves open (each is listed in the design notes):
 * NCDE (App. A): S = 0, M1F = 0, G carries only M1G = (I - S1/2) d_t(u phi) with constant u
   and d_t phi by the backward difference (phi^n - phi^{n-1}) / dt, phi^{-1} = phi^0;
   the third-order Hermite moments of the NCDE equilibrium are zero.
-* rows of order >= 4 relax with one shared rate s_high.
+* rows of order >= 4 (left to the designer by the paper) relax with one shared rate s_high, or
+  with ``s_orders`` one rate per order k on the graded block: the W-orthogonal complement of the
+  lower orders inside the lattice functions spanned by the monomials of degree <= k.
+* bulk viscosity (Eq. (4-27), k = 0): with ``s_bulk`` the normal second-order rows relax through
+  the inverse of S2^(1) = diag(1/s_s) + (1/s_b - 1/s_s) 1 1^T / d.
 
 Arrays use the grid in C order with x fastest: a field has shape (n_z, n_y, n_x) in 3D and
 (n_y, n_x) in 2D; populations have a leading Q axis; velocity fields a leading d axis (u[0]=u_x).
@@ -142,6 +146,8 @@ class Model:
     force: tuple | None = None               # (a, b, A, k[, phase]): F = A sin(2 pi k x_b / L_b + phase) e_a
     u_const: np.ndarray | None = None        # NCDE convection velocity
     nonlin: float = 0.0                      # NCDE: D(phi) = phi + nonlin phi^3 / 3
+    s_bulk: float | None = None              # NSE: bulk rate s_b of Eq. (4-27) (None: diagonal S)
+    s_orders: dict | None = None             # rate of each order >= 4 ({4: s4, 5: s5, ...}; else s_high)
     f: np.ndarray = field(default=None, repr=False)          # f-bar, shape (Q, *grid)
     phi_prev: np.ndarray = field(default=None, repr=False)   # NCDE: phi at the previous step
     step_count: int = 0
@@ -152,12 +158,28 @@ class Model:
         if self.cs2_eq is None:
             self.cs2_eq = float(self.lat.cs2[0])
         Q = self.lat.Q
-        S = np.diag(np.concatenate([self.s, np.full(Q - self.lat.R, self.s_high)]))
+        high = [(self.s_orders or {}).get(o, self.s_high) for o in self.lat.full_orders[self.lat.R:]]
+        S = np.diag(np.concatenate([self.s, np.array(high, dtype=np.float64)]))
+        self.normal = [r for r, p in enumerate(self.lat.polys)
+                       if self.lat.orders[r] == 2 and max(max(p, key=sum)) == 2]
+        if self.s_bulk is not None:
+            S[np.ix_(self.normal, self.normal)] = self.normal_block()
+        self.S = S
         self.Hinv = L.hermite_inverse(self.lat)
         self.Lam = self.Hinv @ S @ self.lat.Hfull       # Lambda = H^{-1} S H
         self.shape = grid_shape(self.n)
         if self.u_const is not None:
             self.u_const = np.asarray(self.u_const, dtype=np.float64)
+
+    def normal_block(self):
+        """Eq. (4-27) with k = 0: the relaxation of the normal second moments is the inverse of
+        S2^(1) = diag(1/s_sa) + a b^T / d with a_a = 1/s_b - 1/s_sa and b = 1, so that the trace
+        relaxes with s_b and the deviatoric part with s_s (Eq. (4-29): mu = (1/s_s - 1/2) p dt,
+        mu_b = (2/d)(1/s_b - 1/2) p dt)."""
+        d = self.lat.d
+        ss = self.s[self.normal]
+        a = 1.0 / self.s_bulk - 1.0 / ss
+        return np.linalg.inv(np.diag(1.0 / ss) + np.outer(a, np.ones(d)) / d)
 
     # -- body force ---------------------------------------------------------------------------
     def force_field(self):
@@ -223,6 +245,13 @@ class Model:
                 return mF, mG
             F = self.force_field().reshape(lat.d, -1)
             u = fields[1].reshape(lat.d, -1)
+            S2 = self.S[:R, :R]
+            raw = np.zeros((R, ncell))          # uF + Fu on the second-order rows
+            for r, poly in enumerate(lat.polys):
+                if lat.orders[r] == 2:
+                    axes = [a for a, k in enumerate(max(poly, key=sum)) for _ in range(k)]
+                    a, b = axes
+                    raw[r] = u[a] * F[b] + F[a] * u[b]
             for r, poly in enumerate(lat.polys):
                 o = lat.orders[r]
                 if o == 1:
@@ -231,10 +260,10 @@ class Model:
                     mF[r] = F[ex.index(1)]
                 elif o == 2:
                     # M2G = (I - S2/2)(uF + Fu) (Eq. (M2Ga-1), S = 0), M0G = 0 so the H2
-                    # Hermite moment equals the raw second moment
-                    axes = [a for a, k in enumerate(max(poly, key=sum)) for _ in range(k)]
-                    a, b = axes
-                    mG[r] = (1.0 - 0.5 * self.s[r]) * (u[a] * F[b] + F[a] * u[b])
+                    # Hermite moment equals the raw second moment; S2 is the second-order block
+                    # of S (diagonal, or with the bulk coupling of Eq. (4-27))
+                    rows2 = [q for q in range(R) if lat.orders[q] == 2]
+                    mG[r] = raw[r] - 0.5 * (S2[r, rows2] @ raw[rows2])
             return mF, mG
         # NCDE: M1G = (I - S1/2) u d_t phi (Eq. (M-NCDE-6) with M20 = 0, A1 = A2 = 0)
         phi = fields[0].reshape(-1)

@@ -111,6 +111,11 @@ void fill_desc(const lbm_model* m, SolveDesc<float>* d) {
     d->sd[r] = p.sd[r];
     d->half[r] = p.half[r];
   }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      d->sdn[i][j] = p.sdn[i][j];
+      d->halfn[i][j] = p.halfn[i][j];
+    }
   d->s_high = p.s_high;
   d->one_minus_sh = p.one_minus_sh;
   d->sh_rho_ref = p.sh_rho_ref;
@@ -283,6 +288,9 @@ lbm_status lbm_batch_add(lbm_batch* b, lbm_model* m) {
   if (m->batch) return set_error(LBM_ERR_ARG, "model is already in a batch");
   if (m->device != b->device) return set_error(LBM_ERR_ARG, "model and batch are on different devices");
   if (m->store == LBM_F64) return set_error(LBM_ERR_NOT_IMPLEMENTED, "batched execution supports F32 and 16-bit storage");
+  for (int k = 4; k <= kMaxOrder; ++k)
+    if (m->s_order[k] > 0.0)
+      return set_error(LBM_ERR_NOT_IMPLEMENTED, "distinct higher-order rates are not available inside a batch");
   if (int(b->members.size()) >= b->max_solves) return set_error(LBM_ERR_ARG, "batch is full");
   DeviceScope scope(b->device);
   cudaError_t err = cudaStreamSynchronize(m->stream);

@@ -114,6 +114,21 @@ constexpr int max_component() {
   return m;
 }
 
+// Index (axis) of a normal second-order row c_a^2 - c_sa^2 among the d normal rows, or -1.
+template <int D>
+constexpr int normal_index(int r) {
+  const Mono m = mono<D>(r);
+  return (degree(m) == 2 && (m.a == 2 || m.b == 2 || m.c == 2)) ? (m.a == 2 ? 0 : (m.b == 2 ? 1 : 2)) : -1;
+}
+// Row of the normal second moment along axis a (2D: rows 3, 5; 3D: rows 4, 5, 6).
+template <int D>
+constexpr int normal_row(int a) {
+  int found = -1;
+  for (int r = 0; r < (D == 2 ? 10 : 20); ++r)
+    if (normal_index<D>(r) == a) found = r;
+  return found;
+}
+
 // Primitive directions: every velocity is e = m d with d primitive (components coprime, first
 // non-zero component positive) and m in {+-1, +-2, +-3}. Since mono_k(m d) = m^deg(k) mono_k(d),
 // the populations of one direction can be combined per degree before the monomial products.
@@ -159,6 +174,41 @@ constexpr int velocity_index(Vel d, int m) {
   return -1;
 }
 
+// +-e pairs: the p-th pair is (pair_plus(p), opposite(pair_plus(p))), pair_plus(p) being the p-th
+// velocity i >= 1 (in table order) whose opposite has a larger index.
+template <class L>
+constexpr int num_pairs() {
+  return (L::Q - 1) / 2;
+}
+template <class L>
+constexpr int pair_plus(int p) {
+  int n = 0;
+  for (int i = 1; i < L::Q; ++i)
+    if (opposite<L>(i) > i) {
+      if (n == p) return i;
+      ++n;
+    }
+  return -1;
+}
+// Rows of order >= 4 of the complete Q x Q Hermite matrix, split by parity under e -> -e: the
+// even lattice functions span the rest velocity and one function per pair (num_pairs + 1), the
+// odd ones one per pair; the orders <= 3 take the even rows of degree 0, 2 and the odd ones of
+// degree 1, 3.
+template <class L>
+constexpr int low_rows_even() {
+  int n = 0;
+  for (int r = 0; r < L::R; ++r) n += (degree(mono<L::D>(r)) % 2 == 0) ? 1 : 0;
+  return n;
+}
+template <class L>
+constexpr int high_even() {
+  return num_pairs<L>() + 1 - low_rows_even<L>();
+}
+template <class L>
+constexpr int high_odd() {
+  return num_pairs<L>() - (L::R - low_rows_even<L>());
+}
+
 // static_for<N>(f) calls f(std::integral_constant<int, 0>) ... f(integral_constant<int, N-1>).
 // Inside nested lambdas, read a captured index as decltype(i)::value (a constant expression
 // whatever the capture); the constexpr helpers above are evaluated at compile time only.
@@ -186,9 +236,27 @@ inline int lattice_q(int kind) {
   return 0;
 }
 inline Vel lattice_e(int kind, int j) { return lattice_dims(kind) == 2 ? kQ25[j] : q53(j); }
+// Host view of the pair order above: plus[p] for p < (Q - 1) / 2.
+inline void lattice_pairs(int kind, int* plus) {
+  const int Q = lattice_q(kind);
+  int n = 0;
+  for (int i = 1; i < Q; ++i) {
+    const Vel a = lattice_e(kind, i);
+    int opp = -1;
+    for (int j = 0; j < Q; ++j) {
+      const Vel b = lattice_e(kind, j);
+      if (a.x == -b.x && a.y == -b.y && a.z == -b.z) opp = j;
+    }
+    if (opp > i) plus[n++] = i;
+  }
+}
 inline int lattice_rmax(int kind) { return (kind == LBM_RD2Q17 || kind == LBM_RD2Q21 || kind == LBM_RD2Q25) ? 3 : 2; }
 
 constexpr int kMaxQ = 53;
 constexpr int kMaxR = 20;
+constexpr int kMaxPairs = 26;  // rD3Q53
+constexpr int kMaxHighEven = 20;
+constexpr int kMaxHighOdd = 13;
+constexpr int kMaxOrder = 12;  // highest monomial degree tried when completing the Hermite matrix
 
 }  // namespace lbm

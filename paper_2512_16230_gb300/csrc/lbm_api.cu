@@ -41,6 +41,47 @@ void make_step_params(const lbm_model* m, StepParams<CT>* p) {
     p->sd[r] = CT(m->s[r] - m->s_high);
     p->half[r] = CT(1.0 - 0.5 * m->s[r]);
   }
+  // normal second-order block: S_n = inverse of diag(1/s_sa) + a 1^T / d, a_a = 1/s_b - 1/s_sa
+  // (Eq. (4-27) with k = 0), or diag(s_sa) without a bulk rate
+  {
+    const int d = L->d;
+    int rows[3] = {0, 0, 0};
+    for (int r = 0, k = 0; r < R; ++r) {
+      const Mono mk = d == 2 ? kMono2[r] : kMono3[r];
+      if (mk.a + mk.b + mk.c == 2 && (mk.a == 2 || mk.b == 2 || mk.c == 2)) rows[k++] = r;
+    }
+    double Sn[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (m->s_bulk > 0.0 && m->eq == LBM_NSE) {
+      double A[3][6];  // [M | I] Gauss-Jordan
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+          A[i][j] = (i == j ? 1.0 / m->s[rows[i]] : 0.0) + (1.0 / m->s_bulk - 1.0 / m->s[rows[i]]) / d;
+          A[i][d + j] = i == j ? 1.0 : 0.0;
+        }
+      for (int c = 0; c < d; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < d; ++r)
+          if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+        for (int q = 0; q < 2 * d; ++q) std::swap(A[c][q], A[piv][q]);
+        const double inv = 1.0 / A[c][c];
+        for (int q = 0; q < 2 * d; ++q) A[c][q] *= inv;
+        for (int r = 0; r < d; ++r)
+          if (r != c) {
+            const double f = A[r][c];
+            for (int q = 0; q < 2 * d; ++q) A[r][q] -= f * A[c][q];
+          }
+      }
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) Sn[i][j] = A[i][d + j];
+    } else {
+      for (int i = 0; i < d; ++i) Sn[i][i] = m->s[rows[i]];
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        p->sdn[i][j] = CT(Sn[i][j] - (i == j && i < d ? m->s_high : 0.0));
+        p->halfn[i][j] = CT((i == j && i < d ? 1.0 : 0.0) - 0.5 * Sn[i][j]);
+      }
+  }
   const bool dev = m->store == LBM_BF16_DEV || m->store == LBM_F16_DEV;
   for (int i = 0; i < L->Q; ++i) {
     p->w[i] = CT(L->w[i]);
@@ -78,6 +119,43 @@ void make_step_params(const lbm_model* m, StepParams<CT>* p) {
 
 template void make_step_params<float>(const lbm_model*, StepParams<float>*);
 template void make_step_params<double>(const lbm_model*, StepParams<double>*);
+
+double high_rate(const lbm_model* m, int order) {
+  const double s = order <= kMaxOrder ? m->s_order[order] : 0.0;
+  return s > 0.0 ? s : m->s_high;
+}
+
+bool has_high_rates(const lbm_model* m) {
+  const lbm_lattice* L = m->lat;
+  for (int r = 0; r < L->nhigh; ++r)
+    if (high_rate(m, L->h_order[r]) != m->s_high) return true;
+  return false;
+}
+
+template <class CT>
+void make_high_params(const lbm_model* m, HighParams<CT>* hp) {
+  const lbm_lattice* L = m->lat;
+  std::memset(hp, 0, sizeof(*hp));
+  int plus[kMaxPairs];
+  lattice_pairs(L->kind, plus);
+  const int np = (L->Q - 1) / 2;
+  int ne = 0, no = 0;
+  for (int r = 0; r < L->nhigh; ++r) {
+    const double* h = L->Hh + size_t(r) * L->Q;
+    const double a = -(high_rate(m, L->h_order[r]) - m->s_high) / L->Nh[r];
+    if ((L->h_order[r] & 1) == 0) {
+      hp->he[ne][0] = CT(h[0]);
+      for (int q = 0; q < np; ++q) hp->he[ne][q + 1] = CT(h[plus[q]]);
+      hp->ae[ne++] = CT(a);
+    } else {
+      for (int q = 0; q < np; ++q) hp->ho[no][q] = CT(h[plus[q]]);
+      hp->ao[no++] = CT(a);
+    }
+  }
+}
+
+template void make_high_params<float>(const lbm_model*, HighParams<float>*);
+template void make_high_params<double>(const lbm_model*, HighParams<double>*);
 
 namespace {
 
@@ -253,6 +331,19 @@ lbm_status lbm_lattice_query(const lbm_lattice* L, int* d, int* Q, int* R, int8_
   return LBM_OK;
 }
 
+lbm_status lbm_lattice_query_high(const lbm_lattice* L, int* n_high, int* orders, double* H, double* N) {
+  if (!L) return set_error(LBM_ERR_ARG, "NULL lattice");
+  if (L->high_status == 1)
+    return set_error(LBM_ERR_LATTICE_INFEASIBLE, "the graded monomials do not complete the Hermite matrix");
+  if (L->high_status == 2)
+    return set_error(LBM_ERR_LATTICE_INFEASIBLE, "a higher-order row has zero W-norm (zero weights)");
+  if (n_high) *n_high = L->nhigh;
+  if (orders) std::memcpy(orders, L->h_order, sizeof(int) * L->nhigh);
+  if (H) std::memcpy(H, L->Hh, sizeof(double) * L->nhigh * L->Q);
+  if (N) std::memcpy(N, L->Nh, sizeof(double) * L->nhigh);
+  return LBM_OK;
+}
+
 lbm_status lbm_lattice_destroy(lbm_lattice* L) {
   delete L;
   return LBM_OK;
@@ -342,6 +433,38 @@ lbm_status lbm_model_set_relaxation(lbm_model* m, const double* s, double s_high
   for (int r = 0; r < m->lat->R; ++r) m->s[r] = s[r];
   m->s_high = s_high;
   batch_mark_dirty(m->batch);
+  return LBM_OK;
+}
+
+lbm_status lbm_model_set_bulk(lbm_model* m, double s_bulk) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (m->eq != LBM_NSE) return set_error(LBM_ERR_ARG, "the bulk rate applies to the NSE model");
+  if (!(s_bulk <= 2.0) || !std::isfinite(s_bulk)) return set_error(LBM_ERR_ARG, "bulk rate must be <= 2");
+  m->s_bulk = s_bulk;
+  batch_mark_dirty(m->batch);
+  return LBM_OK;
+}
+
+lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_orders) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (n_orders < 0 || n_orders > kMaxOrder - 3 || (n_orders > 0 && !s_order))
+    return set_error(LBM_ERR_ARG, "n_orders must lie in [0, " + std::to_string(kMaxOrder - 3) + "]");
+  for (int k = 0; k < n_orders; ++k)
+    if (!(s_order[k] > 0.0 && s_order[k] <= 2.0)) return set_error(LBM_ERR_ARG, "rates must lie in (0, 2]");
+  if (m->batch && n_orders > 0)
+    return set_error(LBM_ERR_NOT_IMPLEMENTED, "distinct higher-order rates are not available inside a batch");
+  double next[kMaxOrder + 1] = {};
+  for (int k = 0; k < n_orders; ++k) next[4 + k] = s_order[k];
+  bool differ = false;
+  for (int r = 0; r < m->lat->nhigh; ++r) {
+    const double s = next[m->lat->h_order[r]];
+    differ = differ || (s > 0.0 && s != m->s_high);
+  }
+  if (differ && m->lat->high_status != 0)
+    return set_error(LBM_ERR_LATTICE_INFEASIBLE, m->lat->high_status == 1
+                                                     ? "the graded monomials do not complete the Hermite matrix"
+                                                     : "a higher-order row has zero W-norm (zero weights)");
+  for (int k = 0; k <= kMaxOrder; ++k) m->s_order[k] = next[k];
   return LBM_OK;
 }
 

@@ -21,6 +21,14 @@ struct lbm_lattice {
   double H[lbm::kMaxR * lbm::kMaxQ];
   double N[lbm::kMaxR];
   double T[lbm::kMaxR * lbm::kMaxR];
+  // Rows of order >= 4 completing the Q x Q Hermite matrix, W-orthogonal to every row of lower
+  // order (graded blocks): even-degree rows first, then odd, each group by order. Values on the
+  // lattice, h_order[r] the order and Nh[r] = sum_i w_i Hh_ri^2. high_status: 0 complete,
+  // 1 the graded monomials do not reach rank Q, 2 a W-norm vanishes (zero weights).
+  int nhigh, high_status;
+  int h_order[lbm::kMaxQ];
+  double Hh[lbm::kMaxQ * lbm::kMaxQ];
+  double Nh[lbm::kMaxQ];
   int device;
 };
 
@@ -42,6 +50,9 @@ struct lbm_model {
   double* sums;     // 4 doubles
   double s[lbm::kMaxR];
   double s_high, cs2_eq, rho_ref;
+  double s_bulk;  // bulk relaxation rate of Eq. (4-27); <= 0: normal rows relax with their own rates
+  double s_order[lbm::kMaxOrder + 1];  // rate of the rows of each order >= 4 (defaults to s_high)
+  bool high_explicit;                  // some order >= 4 has a rate other than s_high
   int force_a, force_b, force_k;
   double force_A, force_phase;
   double u_const[3];
@@ -70,6 +81,8 @@ struct StepParams {
   CT invN[kMaxR];      // 1 / N_r
   CT sd[kMaxR];        // s_r - s_high
   CT half[kMaxR];      // 1 - s_r / 2
+  CT sdn[3][3];        // normal second-order block: S_n - s_high I (S_n diagonal unless a bulk rate is set)
+  CT halfn[3][3];      // I - S_n / 2
   CT w[kMaxQ];
   CT wref[kMaxQ];      // w_i * rho_ref, the offset of deviation storage
   CT wmom_ref[kMaxR];  // rho_ref sum_i w_i mono_k(e_i): moments of the reference state w_i rho_ref
@@ -82,6 +95,18 @@ struct StepParams {
   int div_s[2];          // by n[0] (slot 0) and n[1] (slot 1) for every v < 2^31
   int force_a, force_b;  // force_b < 0: no body force
   const CT* force_tab;
+};
+
+// Rows of order >= 4 that relax with their own rates (the full Q x Q collision). The kernel
+// adds w_i sum_r h_r(c_i) a_r y_r with y_r = sum_j h_r(c_j) f_j and a_r = -(s_r - s_high) / N_r
+// to the reduced-form update; even rows are read at the rest velocity and at the + member of
+// each +-e pair, odd rows at the + members (their value at -e is the negative).
+template <class CT>
+struct HighParams {
+  CT he[kMaxHighEven][kMaxPairs + 1];
+  CT ho[kMaxHighOdd][kMaxPairs];
+  CT ae[kMaxHighEven];
+  CT ao[kMaxHighOdd];
 };
 
 // Multiply-high division by a runtime divisor 2 <= d < 2^31, exact for numerators below 2^31:
@@ -186,6 +211,8 @@ template <class CT>
 struct __align__(16) SolveDesc {
   CT sd[kMaxR];
   CT half[kMaxR];
+  CT sdn[3][3];
+  CT halfn[3][3];
   CT s_high, one_minus_sh, sh_rho_ref, cs2_eq, nonlin_third;
   CT u_const[3];
   int n[3];
@@ -246,5 +273,9 @@ lbm_status setup_lattice_fp64(lbm_lattice* lat);
 // Host-side construction of the step parameters from a model.
 template <class CT>
 void make_step_params(const lbm_model* m, StepParams<CT>* p);
+template <class CT>
+void make_high_params(const lbm_model* m, HighParams<CT>* hp);
+// true when some row of order >= 4 relaxes with a rate other than s_high
+bool has_high_rates(const lbm_model* m);
 
 }  // namespace lbm

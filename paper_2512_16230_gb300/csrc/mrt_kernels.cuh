@@ -228,16 +228,12 @@ __device__ __forceinline__ void hermite_to_monomial(const P& p, const CT (&gN)[L
   });
 }
 
-// Hermite-row work of the collision for row r: g_r / N_r with
-// g_r = s_h m^eq_r - (s_r - s_h)(m_r - m^eq_r) + sigma_r.
+// Hermite moments of row r: the equilibrium m^eq_r and the non-equilibrium m_r - m^eq_r.
 template <class L, class CT, int EQ, int r, class P>
-__device__ __forceinline__ CT row_update(const P& p, const CT (&mu)[L::R],
-                                         const CT (&me)[L::R], const CT (&u)[3], const CT (&F)[3],
-                                         CT dphi) {
-  constexpr int deg = degree(mono<L::D>(r));
-  const CT meq = hermite_eq<L, CT, EQ, r>(p, me);
-  CT neq;
-  if constexpr (EQ == LBM_NCDE && deg == 3) {
+__device__ __forceinline__ void row_moments(const P& p, const CT (&mu)[L::R], const CT (&me)[L::R], CT& meq,
+                                            CT& neq) {
+  meq = hermite_eq<L, CT, EQ, r>(p, me);
+  if constexpr (EQ == LBM_NCDE && degree(mono<L::D>(r)) == 3) {
     neq = row_dot<L, CT, r>(p, mu);
   } else {
     CT dm[L::R];
@@ -248,19 +244,88 @@ __device__ __forceinline__ CT row_update(const P& p, const CT (&mu)[L::R],
     });
     neq = row_dot<L, CT, r>(p, dm);
   }
-  // source moments sigma_r: NSE (I - S/2) M1F = (1 - s/2) F on order 1 and
-  // M2G = (I - S2/2)(uF + Fu) on order 2; NCDE M1G = (I - S1/2) u d_t phi on order 1
-  CT sig = CT(0);
-  if constexpr (deg == 1) {
-    constexpr int a = axis_n(mono<L::D>(r), 0);
-    if constexpr (EQ == LBM_NSE) sig = p.half[r] * F[a];
-    else sig = p.half[r] * p.u_const[a] * dphi;
-  } else if constexpr (deg == 2 && EQ == LBM_NSE) {
-    constexpr int a = axis_n(mono<L::D>(r), 0), b = axis_n(mono<L::D>(r), 1);
-    sig = p.half[r] * fma(u[a], F[b], u[b] * F[a]);
+}
+
+// g_r / N_r with g = s_h m^eq - (S - s_h I)(m - m^eq) + sigma. S is diagonal except on the normal
+// second-order rows, where the d x d block S_n carries the bulk coupling of Eq. (4-27).
+// sigma: NSE (I - S/2) M1F = (1 - s/2) F on order 1 and M2G = (I - S2/2)(uF + Fu) on order 2;
+// NCDE M1G = (I - S1/2) u d_t phi on order 1.
+template <class L, class CT, int EQ, int r, class P>
+__device__ __forceinline__ CT row_update(const P& p, const CT (&meq)[L::R], const CT (&neq)[L::R],
+                                         const CT (&u)[3], const CT (&F)[3], CT dphi) {
+  constexpr int deg = degree(mono<L::D>(r));
+  constexpr int na = normal_index<L::D>(r);
+  CT relax, sig = CT(0);
+  if constexpr (na >= 0) {
+    relax = CT(0);
+    static_for<L::D>([&](auto b) {
+      constexpr int B = decltype(b)::value;
+      relax = fma(p.sdn[na][B], neq[normal_row<L::D>(B)], relax);
+      if constexpr (EQ == LBM_NSE) sig = fma(p.halfn[na][B], CT(2) * u[B] * F[B], sig);
+    });
+  } else {
+    relax = p.sd[r] * neq[r];
+    if constexpr (deg == 1) {
+      constexpr int a = axis_n(mono<L::D>(r), 0);
+      if constexpr (EQ == LBM_NSE) sig = p.half[r] * F[a];
+      else sig = p.half[r] * p.u_const[a] * dphi;
+    } else if constexpr (deg == 2 && EQ == LBM_NSE) {
+      constexpr int a = axis_n(mono<L::D>(r), 0), b = axis_n(mono<L::D>(r), 1);
+      sig = p.half[r] * fma(u[a], F[b], u[b] * F[a]);
+    }
   }
-  const CT g = fma(p.s_high, meq, fma(-p.sd[r], neq, sig));
+  const CT g = fma(p.s_high, meq[r], sig - relax);
   return g * p.invN[r];
+}
+
+// Rows of order >= 4 with their own rates: z_r = a_r sum_j h_r(c_j) f_j, a_r = -(s_r - s_h) / N_r.
+// Pairs outermost, so each +-e pair is summed once and feeds every row: even rows take
+// f_+ + f_-, odd rows f_+ - f_- (h_r(-c) = +-h_r(c)). For deviation storage the reference state
+// drops out (every such row is W-orthogonal to H_0).
+template <class L, class CT>
+__device__ __forceinline__ void high_moments(const CT (&f)[L::Q], const HighParams<CT>& hp,
+                                             CT (&ze)[high_even<L>()], CT (&zo)[high_odd<L>() > 0 ? high_odd<L>() : 1]) {
+  constexpr int HE = high_even<L>(), HO = high_odd<L>();
+  static_for<HE>([&](auto r) { ze[decltype(r)::value] = hp.he[decltype(r)::value][0] * f[0]; });
+  static_for<HO>([&](auto r) { zo[decltype(r)::value] = CT(0); });
+  static_for<num_pairs<L>()>([&](auto q) {
+    constexpr int P = decltype(q)::value;
+    constexpr int ip = pair_plus<L>(P);
+    constexpr int im = opposite<L>(ip);
+    const CT sp = f[ip] + f[im];
+    const CT sm = f[ip] - f[im];
+    static_for<HE>([&](auto r) {
+      constexpr int Rr = decltype(r)::value;
+      ze[Rr] = fma(hp.he[Rr][P + 1], sp, ze[Rr]);
+    });
+    static_for<HO>([&](auto r) {
+      constexpr int Rr = decltype(r)::value;
+      zo[Rr] = fma(hp.ho[Rr][P], sm, zo[Rr]);
+    });
+  });
+  static_for<HE>([&](auto r) { ze[decltype(r)::value] *= hp.ae[decltype(r)::value]; });
+  static_for<HO>([&](auto r) { zo[decltype(r)::value] *= hp.ao[decltype(r)::value]; });
+}
+
+// f_i += w_i sum_r h_r(c_i) z_r over the rows of order >= 4 (the weights of a +-e pair are equal).
+template <class L, class CT, class P>
+__device__ __forceinline__ void high_back(CT (&f)[L::Q], const P& p, const HighParams<CT>& hp,
+                                          const CT (&ze)[high_even<L>()],
+                                          const CT (&zo)[high_odd<L>() > 0 ? high_odd<L>() : 1]) {
+  constexpr int HE = high_even<L>(), HO = high_odd<L>();
+  CT e0 = CT(0);
+  static_for<HE>([&](auto r) { e0 = fma(hp.he[decltype(r)::value][0], ze[decltype(r)::value], e0); });
+  f[0] = fma(p.w[0], e0, f[0]);
+  static_for<num_pairs<L>()>([&](auto q) {
+    constexpr int Pq = decltype(q)::value;
+    constexpr int ip = pair_plus<L>(Pq);
+    constexpr int im = opposite<L>(ip);
+    CT ev = CT(0), od = CT(0);
+    static_for<HE>([&](auto r) { ev = fma(hp.he[decltype(r)::value][Pq + 1], ze[decltype(r)::value], ev); });
+    static_for<HO>([&](auto r) { od = fma(hp.ho[decltype(r)::value][Pq], zo[decltype(r)::value], od); });
+    f[ip] = fma(p.w[ip], ev + od, f[ip]);
+    f[im] = fma(p.w[im], ev - od, f[im]);
+  });
 }
 
 // One collision (Eq. (2-3)) of the populations f of one cell, in place.
@@ -268,10 +333,14 @@ __device__ __forceinline__ CT row_update(const P& p, const CT (&mu)[L::R],
 // DEV: f holds deviations f - w rho_ref (16-bit storage). The moments of the reference state are
 // added back (only 1 and the squares c_a^2 have non-zero lattice moments), and the update
 // f* - w rho_ref = (1 - s_h)(f - w rho_ref) + w H(h) - s_h w rho_ref folds the last term into h_0.
-template <class L, class CT, int EQ, bool DEV = false, class P>
+// HI: rows of order >= 4 relax with the rates of hp (the full Q x Q collision); hp may be null
+// otherwise.
+template <class L, class CT, int EQ, bool DEV = false, bool HI = false, class P>
 __device__ __forceinline__ void collide(CT (&f)[L::Q], const P& p, const CT (&F)[3],
-                                        CT phi_prev, CT& phi_now) {
+                                        CT phi_prev, CT& phi_now, const HighParams<CT>* hp = nullptr) {
   constexpr int R = L::R, D = L::D;
+  CT ze[high_even<L>()], zo[high_odd<L>() > 0 ? high_odd<L>() : 1];
+  if constexpr (HI) high_moments<L>(f, *hp, ze, zo);
   CT mu[R];
   raw_moments<L>(f, mu);
   if constexpr (DEV) {
@@ -307,15 +376,21 @@ __device__ __forceinline__ void collide(CT (&f)[L::Q], const P& p, const CT (&F)
     dphi = phi - phi_prev;
     eq_raw_ncde<L>(phi, fma(p.nonlin_third, phi * phi * phi, phi), p, me);
   }
+  CT meq[R], neq[R];
+  static_for<R>([&](auto r) {
+    constexpr int Rr = decltype(r)::value;
+    row_moments<L, CT, EQ, Rr>(p, mu, me, meq[Rr], neq[Rr]);
+  });
   CT gN[R];
   static_for<R>([&](auto r) {
     constexpr int Rr = decltype(r)::value;
-    gN[Rr] = row_update<L, CT, EQ, Rr>(p, mu, me, u, F, dphi);
+    gN[Rr] = row_update<L, CT, EQ, Rr>(p, meq, neq, u, F, dphi);
   });
   CT h[R];
   hermite_to_monomial<L>(p, gN, h);
   if constexpr (DEV) h[0] -= p.sh_rho_ref;
   back_project<L>(f, p, h, p.one_minus_sh);
+  if constexpr (HI) high_back<L>(f, p, *hp, ze, zo);
 }
 
 // Equilibrium populations of given fields, Eq. (feq-1): f^eq_i = w_i sum_r H_ri m^eq_r / N_r.
@@ -438,6 +513,38 @@ __global__ void __launch_bounds__(kBlock, LBM_K1_MIN_BLOCKS) k_step(const StepPa
   });
 }
 
+// K1 with distinct rates for the orders >= 4: the same gather / collide / store plus the two
+// contractions with the higher rows (about 2 (Q - 1) (Q - R) / 2 more FMAs per cell, so the
+// kernel is bound by the FMA pipe rather than HBM; fewer resident blocks leave it the registers).
+template <class L, class CT, class ST, int EQ>
+__global__ void __launch_bounds__(kBlock, 2) k_step_high(const StepParams<CT> p,
+                                                          const __grid_constant__ HighParams<CT> hp,
+                                                          const ST* __restrict__ fin,
+                                                          ST* __restrict__ fout, CT* __restrict__ phi) {
+  const int cell = blockIdx.x * kBlock + threadIdx.x;
+  if (cell >= p.ncells) return;
+  const Neigh<L> nb(cell, p);
+  const size_t N = size_t(p.ncells);
+  CT f[L::Q];
+  constexpr bool DEV = is_deviation_storage<ST>();
+  static_for<L::Q>([&](auto i) {
+    constexpr int I = decltype(i)::value;
+    if constexpr (DEV) f[I] = RawCodec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()));
+    else f[I] = Codec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()), p.wref[I]);
+  });
+  CT F[3];
+  body_force(p.force_a, p.force_b, p.force_tab, nb.x, nb.y, nb.z, F);
+  CT phi_prev = CT(0), phi_now = CT(0);
+  if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
+  collide<L, CT, EQ, DEV, true>(f, p, F, phi_prev, phi_now, &hp);
+  if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
+  static_for<L::Q>([&](auto i) {
+    constexpr int I = decltype(i)::value;
+    if constexpr (DEV) k1_store(fout + size_t(I) * N + cell, RawCodec<ST>::enc(f[I]));
+    else k1_store(fout + size_t(I) * N + cell, Codec<ST>::enc(f[I], p.wref[I]));
+  });
+}
+
 // Initialisation: f-bar(t=0) = f^eq(fields), written to the stored array at x - e_i so that the
 // next pull gather yields it; the NCDE previous-step field starts at phi^0.
 template <class L, class CT, class ST, int EQ>
@@ -475,11 +582,13 @@ struct BatchView {
   const CT (&wmom_ref)[kMaxR];
   const CT (&sd)[kMaxR];
   const CT (&half)[kMaxR];
+  const CT (&sdn)[3][3];
+  const CT (&halfn)[3][3];
   const CT (&u_const)[3];
   CT s_high, one_minus_sh, sh_rho_ref, cs2_eq, nonlin_third;
   __device__ __forceinline__ BatchView(const BatchTables<CT>& t, const SolveDesc<CT>& d)
       : T(t.T), D(t.D), invN(t.invN), w(t.w), wref(t.wref), wmom_ref(t.wmom_ref), sd(d.sd), half(d.half),
-        u_const(d.u_const), s_high(d.s_high), one_minus_sh(d.one_minus_sh), sh_rho_ref(d.sh_rho_ref),
+        sdn(d.sdn), halfn(d.halfn), u_const(d.u_const), s_high(d.s_high), one_minus_sh(d.one_minus_sh), sh_rho_ref(d.sh_rho_ref),
         cs2_eq(d.cs2_eq), nonlin_third(d.nonlin_third) {}
 };
 
@@ -595,10 +704,18 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
   make_step_params<CT>(m, &p);
   const int grid = (m->ncells + kBlock - 1) / kBlock;
   CT* phi = static_cast<CT*>(m->phi_prev);
+  const bool high = collide_on && has_high_rates(m);
+  HighParams<CT> hp;
+  if (high) make_high_params<CT>(m, &hp);
   for (int64_t s = 0; s < nsteps; ++s) {
     const ST* fin = static_cast<const ST*>(m->f[m->cur]);
     ST* fout = static_cast<ST*>(m->f[m->cur ^ 1]);
-    if (!collide_on) {
+    if (high) {
+      if (m->eq == LBM_NSE)
+        k_step_high<L, CT, ST, LBM_NSE><<<grid, kBlock, 0, m->stream>>>(p, hp, fin, fout, phi);
+      else
+        k_step_high<L, CT, ST, LBM_NCDE><<<grid, kBlock, 0, m->stream>>>(p, hp, fin, fout, phi);
+    } else if (!collide_on) {
       k_step<L, CT, ST, LBM_NSE, false><<<grid, kBlock, 0, m->stream>>>(p, fin, fout, phi);
     } else if (m->eq == LBM_NSE) {
       k_step<L, CT, ST, LBM_NSE, true><<<grid, kBlock, 0, m->stream>>>(p, fin, fout, phi);

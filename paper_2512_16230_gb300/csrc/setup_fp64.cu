@@ -17,6 +17,12 @@
 //    Eq. (CorrectQ25) and App. D. The result is kept as the monic lower-triangular factor T
 //    (H_r = sum_k T_rk mono_k) together with H on the lattice and the norms N_r.
 // 3. Checks: N_r > 0 and |<H_r, H_s>_W| <= 1e-12 sqrt(N_r N_s) for r != s.
+// 4. Rows of order >= 4 (the paper leaves them to the designer): monomials of degree 4, 5, ...
+//    are tried in graded order and kept when they raise the rank of the rows so far (Euclidean
+//    test against an orthonormal basis of their span); each kept one is W-orthogonalised against
+//    every earlier row, lower orders and its own, so that the order-k rows span the W-orthogonal
+//    complement of the orders < k within the monomials of degree <= k, a block that can carry
+//    one rate per order.
 #include <cmath>
 #include <cstring>
 
@@ -237,6 +243,135 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(const SetupIn in, Setup
   }
 }
 
+// Completion of the Hermite matrix by rows of order >= 4 (one block, global scratch).
+struct HighWork {
+  double U[kMaxQ][kMaxQ];   // Euclidean orthonormal basis of the span of the rows so far
+  double Hh[kMaxQ][kMaxQ];  // W-orthogonal rows (H0..H3 first, then the higher ones)
+  double N[kMaxQ];
+  int order[kMaxQ];
+  int nrows, status;
+};
+
+__global__ void __launch_bounds__(kSetupThreads) k_setup_high(const SetupIn in, const SetupOut* low,
+                                                              HighWork* hw) {
+  __shared__ double v[kMaxQ], coef[kMaxQ];
+  __shared__ double red[2];
+  __shared__ int nu;
+  const int tid = threadIdx.x;
+  const int Q = in.Q, R = in.R;
+  auto euclid_project_out = [&](int count) {  // v -= U U^T v over the first count basis vectors
+    for (int pass = 0; pass < 2; ++pass) {
+      if (tid < count) {
+        double dot = 0.0;
+        for (int i = 0; i < Q; ++i) dot += hw->U[tid][i] * v[i];
+        coef[tid] = dot;
+      }
+      __syncthreads();
+      if (tid < Q) {
+        double acc = v[tid];
+        for (int j = 0; j < count; ++j) acc -= coef[j] * hw->U[j][tid];
+        v[tid] = acc;
+      }
+      __syncthreads();
+    }
+  };
+  auto w_project_out = [&](int count) {  // v -= sum_j <v, H_j>_W / N_j H_j
+    for (int pass = 0; pass < 2; ++pass) {
+      if (tid < count) {
+        double dot = 0.0;
+        for (int i = 0; i < Q; ++i) dot += low->w[i] * hw->Hh[tid][i] * v[i];
+        coef[tid] = dot / hw->N[tid];
+      }
+      __syncthreads();
+      if (tid < Q) {
+        double acc = v[tid];
+        for (int j = 0; j < count; ++j) acc -= coef[j] * hw->Hh[j][tid];
+        v[tid] = acc;
+      }
+      __syncthreads();
+    }
+  };
+  auto append_basis = [&](int slot) {  // U[slot] = v / |v| (v already orthogonal to U[0..slot))
+    const double nrm = sqrt(block_sum64(tid < Q ? v[tid] * v[tid] : 0.0, red));
+    if (tid < Q) hw->U[slot][tid] = v[tid] / nrm;
+    __syncthreads();
+  };
+  // H0..H3 seed both bases
+  if (tid == 0) {
+    nu = 0;
+    hw->status = 0;
+  }
+  __syncthreads();
+  for (int r = 0; r < R; ++r) {
+    if (tid < Q) {
+      v[tid] = low->H[r][tid];
+      hw->Hh[r][tid] = low->H[r][tid];
+    }
+    if (tid == 0) {
+      hw->N[r] = low->N[r];
+      hw->order[r] = in.mono[r][0] + in.mono[r][1] + in.mono[r][2];
+    }
+    __syncthreads();
+    euclid_project_out(r);
+    append_basis(r);
+  }
+  int n = R;
+  for (int deg = 4; deg <= kMaxOrder && n < Q; ++deg) {
+    for (int a = deg; a >= 0 && n < Q; --a) {
+      for (int b = deg - a; b >= 0 && n < Q; --b) {
+        const int c = deg - a - b;
+        if (in.d == 2 && c != 0) continue;
+        if (tid < Q) {
+          double x = 1.0;
+          for (int q = 0; q < a; ++q) x *= in.c[0] * double(in.e[tid][0]);
+          for (int q = 0; q < b; ++q) x *= in.c[1] * double(in.e[tid][1]);
+          for (int q = 0; q < c; ++q) x *= in.c[2] * double(in.e[tid][2]);
+          v[tid] = x;
+        }
+        __syncthreads();
+        const double n0 = sqrt(block_sum64(tid < Q ? v[tid] * v[tid] : 0.0, red));
+        euclid_project_out(n);
+        const double n1 = sqrt(block_sum64(tid < Q ? v[tid] * v[tid] : 0.0, red));
+        if (!(n1 > 1e-9 * n0)) continue;  // already in the span
+        append_basis(n);
+        // the new row: the monomial, W-orthogonal to every earlier row, scaled to unit max
+        if (tid < Q) {
+          double x = 1.0;
+          for (int q = 0; q < a; ++q) x *= in.c[0] * double(in.e[tid][0]);
+          for (int q = 0; q < b; ++q) x *= in.c[1] * double(in.e[tid][1]);
+          for (int q = 0; q < c; ++q) x *= in.c[2] * double(in.e[tid][2]);
+          v[tid] = x;
+        }
+        __syncthreads();
+        w_project_out(n);
+        if (tid == 0) {
+          double m = 0.0;
+          for (int i = 0; i < Q; ++i) m = fabs(v[i]) > m ? fabs(v[i]) : m;
+          coef[0] = m;
+        }
+        __syncthreads();
+        const double scale = coef[0];
+        __syncthreads();
+        if (tid < Q) hw->Hh[n][tid] = v[tid] / scale;
+        __syncthreads();
+        const double nn = block_sum64(tid < Q ? low->w[tid] * hw->Hh[n][tid] * hw->Hh[n][tid] : 0.0, red);
+        const double na = block_sum64(tid < Q ? fabs(low->w[tid]) * hw->Hh[n][tid] * hw->Hh[n][tid] : 0.0, red);
+        if (tid == 0) {
+          hw->N[n] = nn;
+          hw->order[n] = deg;
+          if (!(fabs(nn) > 1e-10 * na)) hw->status = 2;
+        }
+        __syncthreads();
+        ++n;
+      }
+    }
+  }
+  if (tid == 0) {
+    hw->nrows = n;
+    if (n < Q && hw->status == 0) hw->status = 1;
+  }
+}
+
 }  // namespace
 
 lbm_status setup_lattice_fp64(lbm_lattice* lat) {
@@ -260,14 +395,32 @@ lbm_status setup_lattice_fp64(lbm_lattice* lat) {
   }
   for (int k = 0; k < 4; ++k) in.free_w[k] = lat->free_w[k];
   SetupOut* dout = nullptr;
+  HighWork* dhigh = nullptr;
   cudaError_t err = cudaMalloc(&dout, sizeof(SetupOut));
-  if (err != cudaSuccess) return cuda_error(err, "set-up allocation");
+  if (err == cudaSuccess) err = cudaMalloc(&dhigh, sizeof(HighWork));
+  if (err != cudaSuccess) {
+    cudaFree(dout);
+    return cuda_error(err, "set-up allocation");
+  }
   k_setup<<<1, kSetupThreads>>>(in, dout);
   err = cudaGetLastError();
   SetupOut out;
   if (err == cudaSuccess) err = cudaMemcpy(&out, dout, sizeof(SetupOut), cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess && out.status == 0) {
+    k_setup_high<<<1, kSetupThreads>>>(in, dout, dhigh);
+    err = cudaGetLastError();
+  }
+  HighWork* high = nullptr;
+  if (err == cudaSuccess && out.status == 0) {
+    high = new HighWork;
+    err = cudaMemcpy(high, dhigh, sizeof(HighWork), cudaMemcpyDeviceToHost);
+  }
   cudaFree(dout);
-  if (err != cudaSuccess) return cuda_error(err, "set-up kernel");
+  cudaFree(dhigh);
+  if (err != cudaSuccess) {
+    delete high;
+    return cuda_error(err, "set-up kernel");
+  }
   if (out.status == 1) return set_error(LBM_ERR_LATTICE_INFEASIBLE, "weight moment system is singular");
   if (out.status == 2) return set_error(LBM_ERR_LATTICE_INFEASIBLE, "a Hermite norm N_r is not positive");
   if (out.status == 3)
@@ -279,6 +432,18 @@ lbm_status setup_lattice_fp64(lbm_lattice* lat) {
     lat->N[r] = out.N[r];
     for (int k = 0; k < lat->R; ++k) lat->T[r * lat->R + k] = out.T[r][k];
   }
+  // higher rows: even degrees first, then odd, each by order (stable)
+  lat->high_status = high->status;
+  lat->nhigh = 0;
+  for (int odd = 0; odd < 2; ++odd)
+    for (int r = lat->R; r < high->nrows; ++r) {
+      if ((high->order[r] & 1) != odd) continue;
+      const int t = lat->nhigh++;
+      lat->h_order[t] = high->order[r];
+      lat->Nh[t] = high->N[r];
+      for (int j = 0; j < lat->Q; ++j) lat->Hh[t * lat->Q + j] = high->Hh[r][j];
+    }
+  delete high;
   return LBM_OK;
 }
 

@@ -37,11 +37,14 @@ SIGNATURES = {
     "lbm_lattice_create": (c_int, [c_int, _PD, _PD, _PD, c_int, POINTER(_P)]),
     "lbm_lattice_query": (c_int, [_P, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int8),
                                   _PD, _PD, _PD, _PD]),
+    "lbm_lattice_query_high": (c_int, [_P, POINTER(c_int), POINTER(c_int), _PD, _PD]),
     "lbm_lattice_destroy": (c_int, [_P]),
     "lbm_model_workspace_bytes": (c_int, [_P, c_int, _PI64, c_int, POINTER(c_size_t)]),
     "lbm_model_create": (c_int, [_P, c_int, _PI64, c_int, c_int, _P, _P, c_size_t, POINTER(_P)]),
     "lbm_model_set_relaxation": (c_int, [_P, _PD, c_double]),
     "lbm_model_set_eos": (c_int, [_P, c_double]),
+    "lbm_model_set_bulk": (c_int, [_P, c_double]),
+    "lbm_model_set_high_rates": (c_int, [_P, _PD, c_int]),
     "lbm_model_set_force": (c_int, [_P, c_int, c_int, c_double, c_int, c_double]),
     "lbm_model_set_ncde": (c_int, [_P, _PD, c_double]),
     "lbm_model_init_fields": (c_int, [_P, _P, _P, c_int]),
@@ -175,6 +178,19 @@ class Lattice:
         return dict(d=d, Q=Q, R=R, e=e.reshape(Q, d).astype(np.int64), w=w, H=H.reshape(R, Q), N=N,
                     T=T.reshape(R, R))
 
+    def query_high(self):
+        """Rows of order >= 4 (lbm_lattice_query_high): orders, rows on the lattice, W-norms."""
+        lb = load()
+        nh = c_int()
+        _check(lb.lbm_lattice_query_high(self.handle, byref(nh), None, None, None), "lbm_lattice_query_high")
+        nh = nh.value
+        orders = (c_int * max(nh, 1))()
+        H = np.zeros(nh * self.Q)
+        N = np.zeros(nh)
+        _check(lb.lbm_lattice_query_high(self.handle, None, orders, H.ctypes.data_as(_PD), N.ctypes.data_as(_PD)),
+               "lbm_lattice_query_high")
+        return dict(orders=np.array(orders[:nh], dtype=np.int64), H=H.reshape(nh, self.Q), N=N)
+
     def close(self):
         if getattr(self, "handle", None):
             load().lbm_lattice_destroy(self.handle)
@@ -225,6 +241,15 @@ class Model:
         if len(s) != self.lattice.R:
             raise ValueError(f"need {self.lattice.R} rates")
         _check(load().lbm_model_set_relaxation(self.handle, _dbuf(s), float(s_high)), "lbm_model_set_relaxation")
+
+    def set_bulk(self, s_bulk):
+        _check(load().lbm_model_set_bulk(self.handle, float(s_bulk)), "lbm_model_set_bulk")
+
+    def set_high_rates(self, s_order):
+        """Rates of the orders 4, 5, ... (one per order); the orders not given relax with s_high."""
+        s_order = [float(v) for v in s_order]
+        _check(load().lbm_model_set_high_rates(self.handle, _dbuf(s_order) if s_order else None, len(s_order)),
+               "lbm_model_set_high_rates")
 
     def set_eos(self, cs2_eq):
         _check(load().lbm_model_set_eos(self.handle, float(cs2_eq)), "lbm_model_set_eos")

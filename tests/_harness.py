@@ -29,14 +29,16 @@ def gpu_lattice(spec):
     return lbm.Lattice(spec.kind, spec.c, spec.cs2, spec.free_w)
 
 
-def oracle_model(spec, eq, n, s, s_high=1.0, force=None, u_const=None, nonlin=0.0, cs2_eq=None, lat=None):
+def oracle_model(spec, eq, n, s, s_high=1.0, force=None, u_const=None, nonlin=0.0, cs2_eq=None, lat=None,
+                 s_bulk=None, s_orders=None):
     lat = lat or oracle_lattice(spec)
     return OM.Model(lat, eq, n, np.asarray(s, dtype=float), s_high, cs2_eq=cs2_eq, force=force,
-                    u_const=None if u_const is None else np.asarray(u_const, dtype=float), nonlin=nonlin)
+                    u_const=None if u_const is None else np.asarray(u_const, dtype=float), nonlin=nonlin,
+                    s_bulk=s_bulk, s_orders=s_orders)
 
 
 def gpu_model(spec, eq, n, s, s_high=1.0, force=None, u_const=None, nonlin=0.0, cs2_eq=None, store="f32",
-              lat=None):
+              lat=None, s_bulk=None, s_orders=None):
     from paper_2512_16230_gb300 import lbm
     lat = lat or gpu_lattice(spec)
     m = lbm.Model(lat, eq, n, store=store)
@@ -47,6 +49,10 @@ def gpu_model(spec, eq, n, s, s_high=1.0, force=None, u_const=None, nonlin=0.0, 
         m.set_force(*force)
     if u_const is not None:
         m.set_ncde(u_const, nonlin)
+    if s_bulk is not None:
+        m.set_bulk(s_bulk)
+    if s_orders:
+        m.set_high_rates([s_orders.get(k, s_high) for k in range(4, max(s_orders) + 1)])
     return m
 
 

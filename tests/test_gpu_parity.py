@@ -242,3 +242,109 @@ def test_steps_are_deterministic():
         runs.append((gm.get_populations(), gm.conserved_sums()))
     assert np.array_equal(runs[0][0], runs[1][0])
     assert np.array_equal(runs[0][1], runs[1][1])
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["rD2Q25", "rD2Q13", "rD3Q53", "rD3Q45", "rD3Q53-aniso"])
+def test_bulk_viscosity_step(name, store):
+    """Independent bulk viscosity (Eq. (4-27), k = 0): the normal second-order block of S couples
+    the rows through s_b, also inside (I - S2/2) M2G (body force on)."""
+    spec = ALL_SPECS[name]
+    d = spec.d
+    n = RAGGED[d]
+    s = _random_rates(spec.R, 8)
+    kw = dict(s_high=1.2, force=(d - 1, 0, 2e-3, 1, 0.1), s_bulk=0.9)
+    om = oracle_model(spec, "nse", n, s, **kw)
+    gm = gpu_model(spec, "nse", n, s, store=store, **kw)
+    f0 = round_to_store(I.random_populations(n, om.lat.Q, seed=21), store)
+    om.set_populations(f0)
+    gm.set_populations(f0)
+    om.step(2)
+    gm.step(2)
+    assert rel_l2(gm.get_populations(), om.f) <= TOL[store]
+
+
+def _order_projectors(H, N, orders, w):
+    """W H_k^T N_k^-1 H_k for every order k of the given rows."""
+    out = {}
+    for k in sorted(set(orders)):
+        sel = [r for r, o in enumerate(orders) if o == k]
+        Hk = H[sel]
+        out[k] = (w[:, None] * Hk.T) @ np.diag(1.0 / N[sel]) @ Hk
+    return out
+
+
+@pytest.mark.parametrize("name", sorted(ALL_SPECS))
+def test_high_rows_match_oracle_blocks(name):
+    """The GPU set-up completes the Hermite matrix with graded rows of order >= 4. Any basis of an
+    order block gives the same collision, so the comparison is of the W-projector of each order,
+    against the oracle's full matrix (built by its own selection and orthogonalisation)."""
+    spec = ALL_SPECS[name]
+    glat = gpu_lattice(spec)
+    hi = glat.query_high()
+    olat = oracle_lattice(spec)
+    R = olat.R
+    assert len(hi["orders"]) == olat.Q - R
+    assert sorted(hi["orders"]) == sorted(olat.full_orders[R:])
+    N_o = np.einsum("ri,i,ri->r", olat.Hfull[R:], olat.w, olat.Hfull[R:])
+    Pg = _order_projectors(hi["H"], hi["N"], list(hi["orders"]), glat.tables["w"])
+    Po = _order_projectors(olat.Hfull[R:], N_o, olat.full_orders[R:], olat.w)
+    for k in Po:
+        assert np.abs(Pg[k] - Po[k]).max() < 1e-10, k
+    # W-orthogonal to the rows of order <= 3
+    G = (hi["H"] * glat.tables["w"]) @ glat.tables["H"].T
+    assert np.abs(G).max() < 1e-12 * np.sqrt(np.abs(hi["N"])).max() * np.sqrt(glat.tables["N"]).max()
+
+
+def test_high_rows_need_nonzero_weights():
+    """With w45 = 0 the eight (+-2)^3 velocities of rD3Q53 carry no weight, so a higher row living on
+    them has zero W-norm: the lattice builds, but distinct higher-order rates are refused."""
+    from paper_2512_16230_gb300 import lbm
+    lat = lbm.Lattice("rD3Q53", (1.0, 1.0, 1.0), (0.6, 0.6, 0.6), (0.0,))
+    with pytest.raises(lbm.LBMError, match="LATTICE_INFEASIBLE"):
+        lat.query_high()
+    m = lbm.Model(lat, "nse", (4, 4, 4), store="f64")
+    m.set_high_rates([])                 # shared rate: nothing to refuse
+    with pytest.raises(lbm.LBMError, match="LATTICE_INFEASIBLE"):
+        m.set_high_rates([1.3])
+
+
+HIGH_RATES = {4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25}
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["rD2Q25", "rD2Q17", "rD2Q13", "rD3Q53", "rD3Q45", "rD3Q33", "rD3Q53-aniso"])
+def test_high_order_rates_step(name, store):
+    """The full Q x Q collision with one rate per order >= 4 (explicit higher rows in the kernel)
+    against the oracle's Lambda = H^{-1} S H with the same per-order rates, body force on."""
+    spec = ALL_SPECS[name]
+    d = spec.d
+    n = RAGGED[d]
+    s = _random_rates(spec.R, 9)
+    kw = dict(s_high=1.15, force=(d - 1, 0, 2e-3, 1, 0.1), s_orders=HIGH_RATES)
+    om = oracle_model(spec, "nse", n, s, **kw)
+    gm = gpu_model(spec, "nse", n, s, store=store, **kw)
+    f0 = round_to_store(I.random_populations(n, om.lat.Q, seed=23), store)
+    om.set_populations(f0)
+    gm.set_populations(f0)
+    om.step(2)
+    gm.step(2)
+    assert rel_l2(gm.get_populations(), om.f) <= TOL[store]
+
+
+@pytest.mark.parametrize("store", ["f32", "f16_dev"])
+def test_high_order_rates_flow(store):
+    """A Taylor-Green flow on rD3Q53 with distinct higher-order rates over 40 steps: the explicit
+    rows also work on deviation storage (the reference state has no moment of order >= 4)."""
+    wl = W.taylor_green_3d(n=(24, 24, 18), steps=40, re=100.0)
+    spec = wl.lattice
+    kw = dict(force=wl.force, u_const=wl.u_const, nonlin=wl.nonlin, s_orders=HIGH_RATES)
+    om = oracle_model(spec, wl.eq, wl.n, wl.s, wl.s_high, **kw)
+    gm = gpu_model(spec, wl.eq, wl.n, wl.s, wl.s_high, store=store, **kw)
+    rho, u = wl.fields()
+    om.init_fields(rho, u)
+    gm.init_fields(rho, u)
+    om.step(wl.steps)
+    gm.step(wl.steps)
+    eu = rel_l2(gm.read_fields()[1], om.fields()[1])
+    assert eu <= (1e-5 if store == "f32" else 1e-3)

@@ -431,3 +431,92 @@ def test_ncde_nonlinear_diffusivity(background):
     (1 + phi0^2) times its rate in the linear model."""
     ratio = _sine_decay_rate(1.0, background) / _sine_decay_rate(0.0, background)
     assert abs(ratio / (1 + background ** 2) - 1) < 2e-3
+
+
+def _sound_damping(s_bulk, axis, nu=0.05):
+    c, cs2, fw = LATS["rD2Q25"]
+    lat = L.build("rD2Q25", c, cs2, fw)
+    s = np.ones(lat.R)
+    s[3:6] = 1.0 / (nu / cs2[0] + 0.5)
+    n = (48, 4) if axis == 0 else (4, 36)
+    m = M.Model(lat, "nse", n, s, 1.0, s_bulk=s_bulk)
+    xs = I.coords(n, c)
+    k = 2 * math.pi / (n[axis] * c[axis])
+    m.init_fields(1.0 + 1e-4 * np.cos(k * xs[axis]), np.zeros((2,) + xs[0].shape))
+
+    def energy():
+        r, u = m.fields()
+        return np.sum((r - 1.0) ** 2 * cs2[0] + r * (u ** 2).sum(0))
+
+    m.step(40)
+    e0 = energy()
+    m.step(400)
+    gamma = math.log(e0 / energy()) / 400 / 2
+    mu_b = (1.0 / s_bulk - 0.5) * cs2[0] if s_bulk else nu     # (2/d)(1/s_b - 1/2) p, d = 2
+    return gamma / (k * k * (nu + mu_b) / 2)                    # 2 (1 - 1/d) mu + mu_b = mu + mu_b
+
+
+@pytest.mark.parametrize("s_bulk", [None, 1.0, 1.5])
+def test_bulk_viscosity_sound_damping(s_bulk):
+    """Eq. (4-27)/(4-29), k = 0: a standing sound wave decays at k^2 (2(1 - 1/d) mu + mu_b)/(2 rho)
+    with mu = (1/s_nu - 1/2) p, mu_b = (2/d)(1/s_b - 1/2) p; the same along both axes of the
+    rectangular rD2Q25 (dy/dx = 4/3)."""
+    rx, ry = _sound_damping(s_bulk, 0), _sound_damping(s_bulk, 1)
+    assert abs(rx - 1) < 2e-2 and abs(ry - 1) < 2e-2
+    assert abs(rx / ry - 1) < 1e-2
+
+
+def test_bulk_block_with_equal_rates_is_diagonal():
+    """s_b = s_s makes S2^(1) = diag(1/s_s) (a = 0): the collision is the diagonal one."""
+    lat = lattice("rD3Q53")
+    s = np.random.default_rng(4).uniform(0.7, 1.8, lat.R)
+    s[4:7] = 1.37
+    a = M.Model(lat, "nse", (3, 3, 3), s, 1.2)
+    b = M.Model(lat, "nse", (3, 3, 3), s, 1.2, s_bulk=1.37)
+    assert np.abs(a.Lam - b.Lam).max() < 1e-13
+
+
+def _graded_projector(lat, k):
+    """W-orthogonal projector onto the lattice functions spanned by every monomial of degree <= k,
+    built without the oracle's row selection or Gram-Schmidt: with A the monomials evaluated on
+    the lattice (rows scaled to unit max) and U an orthonormal basis of range(W^1/2 A^T) from an
+    SVD, Pi = W A^T (A W A^T)^+ A = W^1/2 U U^T W^-1/2."""
+    rows = [_mono(lat.cvel, [a for a in range(lat.d) for _ in range(ex[a])])
+            for deg in range(k + 1) for ex in itertools.product(range(deg + 1), repeat=lat.d) if sum(ex) == deg]
+    A = np.array([r / np.abs(r).max() for r in rows])
+    sw = np.sqrt(lat.w)
+    u, sv, _ = np.linalg.svd(sw[:, None] * A.T, full_matrices=False)
+    U = u[:, sv > 1e-9 * sv[0]]
+    return (sw[:, None] * U) @ (U.T / sw[None, :])
+
+
+@pytest.mark.parametrize("kind", ["rD2Q25", "rD2Q13", "rD3Q53", "rD3Q33"])
+def test_distinct_high_order_rates(kind):
+    """Rows of order >= 4 with one rate per order (the paper leaves them to the designer; reading:
+    the order-k block is the W-orthogonal complement of the lower orders in the monomials of
+    degree <= k). The collision then changes by -sum_k (s_k - s_h) Pi_k (f - f^eq) with
+    Pi_k = Pi_{<=k} - Pi_{<=k-1}; f^eq and the sources lie in orders <= 3, so Pi_k f^eq = 0.
+    Mass and momentum stay exact."""
+    lat = lattice(kind)
+    d = lat.d
+    n = (4,) * d
+    orders = sorted(set(lat.full_orders[lat.R:]))
+    rates = {o: 0.6 + 0.17 * i for i, o in enumerate(orders)}
+    s = np.random.default_rng(8).uniform(0.7, 1.8, lat.R)
+    force = (0, d - 1, 2e-3, 1, 0.3)
+    f = I.random_populations(n, lat.Q, seed=12)
+    base = M.Model(lat, "nse", n, s, 1.1, force=force)
+    dist = M.Model(lat, "nse", n, s, 1.1, force=force, s_orders=rates)
+    base.set_populations(f)
+    dist.set_populations(f)
+    diff = (dist.collide() - base.collide()).reshape(lat.Q, -1)
+    want = np.zeros_like(diff)
+    prev = _graded_projector(lat, 3)
+    for k in range(4, max(orders) + 1):
+        cur = _graded_projector(lat, k)
+        want -= (rates.get(k, 1.1) - 1.1) * ((cur - prev) @ f.reshape(lat.Q, -1))
+        prev = cur
+    assert np.abs(prev - np.eye(lat.Q)).max() < 1e-9          # the orders exhaust the lattice
+    assert np.abs(diff - want).max() < 1e-12 * np.abs(f).max()
+    assert np.abs(diff.sum(0)).max() < 1e-15
+    assert np.abs(lat.cvel.T @ diff).max() < 1e-15
