@@ -41,6 +41,8 @@ PROFILE = os.path.join(ROOT, "profiles", "k_step_rd3q53_f32_tgv3d_256x256x192.md
 CPU_SAMPLE_GRID = (256, 256, 16)    # cpu_baseline: ~10-30 s of oracle work on the GPU machine
 CPU_SAMPLE_STEPS = 8
 REF_BUDGET_S = 150.0                  # --impl reference: wall-clock budget for W + K sample steps
+HIGH_RATES = {4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25}   # variant: one rate per order >= 4
+VARIANT_STEPS = 100
 
 
 def _workload(grid=GRID):
@@ -355,6 +357,19 @@ def bench_ours(args):
     e2e_value = job_throughput(cells, args.steps, ws, reduce_max(e2e_s, ws, dev))
     io_bytes = (rho_h.numel() + u_h.numel()) * 8
 
+    # the full Q x Q collision with one rate per order >= 4 (k_step_high) on the same solve
+    model.set_high_rates([HIGH_RATES[k] for k in sorted(HIGH_RATES)])
+    model.step(3)
+    vsteps = min(args.steps, VARIANT_STEPS)
+    v0 = torch.cuda.Event(enable_timing=True)
+    v1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    v0.record(stream)
+    model.step(vsteps)
+    v1.record(stream)
+    barrier()
+    high_ms = v0.elapsed_time(v1) / vsteps
+
     if rank == 0:
         peak, peak_src = _peaks()
         algo_bytes = 2 * Q * STORE_BYTES * cells
@@ -378,6 +393,13 @@ def bench_ours(args):
                     "definition": "one solve through the C ABI: pinned host fields in, K steps, pinned host fields out"},
             "gpu_launches": int(launches1 - launches0),
             "mass_sum": float(sums[0]),
+            "variants": {
+                "high_order_rates": {
+                    "kernel": "k_step_high<rD3Q53, f32, NSE> (explicit rows of order >= 4, one rate per order)",
+                    "rates": {str(k): v for k, v in HIGH_RATES.items()}, "steps": vsteps,
+                    "ms_per_step": high_ms, "mlups": cells / high_ms / 1e3,
+                    "hbm_frac": algo_bytes / (high_ms / 1e3) / 1e9 / peak},
+            },
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu

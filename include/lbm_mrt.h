@@ -53,7 +53,8 @@ typedef enum {
   LBM_ERR_OOM = 3,                /* device allocation failed or workspace too small */
   LBM_ERR_CUDA = 4,               /* a CUDA runtime call failed (message has the CUDA error) */
   LBM_ERR_NONFINITE = 5,          /* a conservation sum is NaN or infinite */
-  LBM_ERR_NOT_IMPLEMENTED = 6
+  LBM_ERR_NOT_IMPLEMENTED = 6,
+  LBM_ERR_TIMEOUT = 7             /* a device-side bounded wait ran out (reported by syncing calls) */
 } lbm_status;
 
 /* Lattices of Sec. 5 and App. D, velocity columns in the paper's printed order. */
@@ -78,6 +79,12 @@ typedef enum {
   LBM_NSE = 0, /* isothermal Navier-Stokes, Sec. 3 with the multispeed choices of Sec. 3.4 */
   LBM_NCDE = 1 /* nonlinear convection-diffusion, App. A */
 } lbm_eq;
+
+typedef enum {
+  LBM_NCDE_MOMENT = 0, /* nonlinearity in M2 = cs2_eq D(phi) I, constant S1 (default)          */
+  LBM_NCDE_RATE = 1,   /* D(phi) = phi, per-cell S1(phi) giving K(phi) = K0 (1 + nonlin phi^2) */
+  LBM_NCDE_CDE = 2     /* diffusion-based CDE, App. A special case (3)                        */
+} lbm_ncde_variant;
 
 int lbm_abi_version(void);
 
@@ -175,6 +182,18 @@ lbm_status lbm_model_set_bulk(lbm_model* m, double s_bulk);
  *         LBM_ERR_NOT_IMPLEMENTED (the model is in a batch). */
 lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_orders);
 
+/* Tensor-core collision for 16-bit deviation storage (BF16_DEV / F16_DEV): the two contractions
+ * of the Hermite-moment collision (Eq. (H-MRT-LB-1)) run as tcgen05 matrix products over tiles
+ * of 128 cells with the integer monomial table mono_k(e_i) as the other operand (exact in 16 bits);
+ * the per-cell moment-space arithmetic stays in FP32. enable = 0 selects the CUDA-core kernel.
+ * Device-side waits are bounded; a timeout is latched in the model's status word and returned as
+ * LBM_ERR_TIMEOUT by the next lbm_model_synchronize / read / get / sums call.
+ * enable = 2 is a test hook for that path: the kernel issues no matrix product, every wait runs
+ * out after a short limit, the CTAs free their tensor memory and return, and the populations
+ * are left undefined.
+ * Errors: LBM_ERR_ARG (storage is not 16-bit, enable not in {0, 1, 2}). */
+lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable);
+
 /* Equation of state p = rho * cs2_eq (NSE, Eq. (M-NSEs-6-1)) or the prefactor of the diffusion
  * moment M2 = cs2_eq D(phi) I (NCDE, Eq. (M-NCDE-6)). */
 lbm_status lbm_model_set_eos(lbm_model* m, double cs2_eq);
@@ -190,6 +209,24 @@ lbm_status lbm_model_set_force(lbm_model* m, int axis_a, int axis_b, double A, i
  * D(phi) = phi + nonlin * phi^3 / 3, i.e. grad D = (1 + nonlin phi^2) grad phi. The auxiliary
  * moment is M1G = (I - S1/2) u (phi^n - phi^{n-1}) (Eq. (M-NCDE-6), M20 = 0). */
 lbm_status lbm_model_set_ncde(lbm_model* m, const double* u_const, double nonlin);
+
+/* NCDE variants of App. A (default LBM_NCDE_MOMENT, a1 = 0):
+ *   LBM_NCDE_MOMENT  as lbm_model_set_ncde describes;
+ *   LBM_NCDE_RATE    M2 = cs2_eq phi I and the first-order rates taken per cell,
+ *                    s_a(phi) = 1 / ((1/s_a - 1/2)(1 + nonlin phi^2) + 1/2), so that the
+ *                    diffusivity K = cs2_eq (1/s_a(phi) - 1/2) (Eq. (GNCDE-0) read with S1^-1)
+ *                    carries the nonlinearity; M1G uses the same per-cell rates;
+ *   LBM_NCDE_CDE     the diffusion-based model for d_t phi + u . grad phi = div(K grad phi):
+ *                    M1 = 0, M2 = cs2_eq phi I, lambda = 1, S_G = -u . grad phi with the local
+ *                    gradient grad_a phi = -s_a M1_a^ne / (dt cs2_eq) (Eq. (M-NCDE-3-00)),
+ *                    M0G = (1 - s0/2) S_G (Eq. (M-NCDE-4)), M1G = 0, and phi = sum f + S_G / 2
+ *                    (Eq. (2-4-1)); read_fields returns that phi.
+ * a1: the mixed-derivative term of Eq. (GNCDE) with A1 = a1 I and B-bar = u phi, i.e. M1G gains
+ *     -S1 A1 d_t(u phi) and the equation gains div(a1 dt d_t(u phi)) (moment and rate variants;
+ *     must be 0 for the CDE).
+ * Errors: LBM_ERR_ARG (not an NCDE model, unknown variant, a1 with the CDE, non-finite a1),
+ *         LBM_ERR_NOT_IMPLEMENTED (rate or CDE variant inside a batch). */
+lbm_status lbm_model_set_ncde_variant(lbm_model* m, lbm_ncde_variant variant, double a1);
 
 /* f-bar(t = 0) = f^eq of the given fields (Eq. (feq-1)); for the NCDE phi^{-1} = phi^0.
  * rho_or_phi[ncells], u[d*ncells] (NSE only; ignored and may be NULL for the NCDE). Resets

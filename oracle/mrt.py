@@ -23,6 +23,13 @@ Readings of points the paper leaves open (each is listed in the design notes):
 * NCDE (App. A): S = 0, M1F = 0, G carries only M1G = (I - S1/2) d_t(u phi) with constant u
   and d_t phi by the backward difference (phi^n - phi^{n-1}) / dt, phi^{-1} = phi^0;
   the third-order Hermite moments of the NCDE equilibrium are zero.
+* NCDE variants of App. A: ``ncde_mode="rate"`` puts the nonlinearity into per-cell first-order
+  rates, K(phi) = K0 (1 + nonlin phi^2) = cs2_eq (1/s1(phi) - 1/2), with D(phi) = phi in M2;
+  ``ncde_mode="cde"`` is special case (3), the diffusion-based CDE (M1 = 0, M2 = cs2_eq phi I,
+  lambda = 1, S_G = -u . grad phi from the local gradient of Eq. (M-NCDE-3-00), M0G =
+  (1 - s0/2) S_G); ``a1`` adds the mixed-derivative term of Eq. (GNCDE) with A1 = a1 I and
+  B-bar = u phi, whose coefficient is dt A1 by the derivation (the printed K1 = dt S1 A1 carries
+  the same slip as the printed K).
 * rows of order >= 4 (left to the designer by the paper) relax with one shared rate s_high, or
   with ``s_orders`` one rate per order k on the graded block: the W-orthogonal complement of the
   lower orders inside the lattice functions spanned by the monomials of degree <= k.
@@ -93,10 +100,13 @@ def hermite_moments_eq_nse(lat: L.Lattice, rho, j, cs2_eq):
     return np.stack(out)
 
 
-def hermite_moments_eq_ncde(lat: L.Lattice, phi, u_const, cs2_eq, nonlin):
+def hermite_moments_eq_ncde(lat: L.Lattice, phi, u_const, cs2_eq, nonlin, mode="moment"):
     """App. A, Eq. (M-NCDE-6): M0 = phi, M1 = B = u phi, M2 = cs2_eq D(phi) I (+ M20 = 0) with
-    D(phi) = phi + nonlin * phi^3 / 3; third-order Hermite moments zero."""
-    Dphi = phi + nonlin * phi ** 3 / 3.0
+    D(phi) = phi + nonlin * phi^3 / 3 ("moment"), D(phi) = phi ("rate": the nonlinearity sits in
+    the relaxation rate instead); the diffusion-based CDE of App. A special case (3) ("cde") has
+    M1 = 0 and M2 = cs2_eq phi I. Third-order Hermite moments zero."""
+    Dphi = phi + nonlin * phi ** 3 / 3.0 if mode == "moment" else phi
+    flux = 0.0 if mode == "cde" else 1.0
     out = []
     for poly, order in zip(lat.polys, lat.orders):
         if order == 3:
@@ -108,7 +118,7 @@ def hermite_moments_eq_ncde(lat: L.Lattice, phi, u_const, cs2_eq, nonlin):
             if len(axes) == 0:
                 term = phi
             elif len(axes) == 1:
-                term = u_const[axes[0]] * phi
+                term = flux * u_const[axes[0]] * phi
             else:
                 term = cs2_eq * Dphi if axes[0] == axes[1] else np.zeros_like(phi)
             m = m + coef * term
@@ -148,6 +158,8 @@ class Model:
     nonlin: float = 0.0                      # NCDE: D(phi) = phi + nonlin phi^3 / 3
     s_bulk: float | None = None              # NSE: bulk rate s_b of Eq. (4-27) (None: diagonal S)
     s_orders: dict | None = None             # rate of each order >= 4 ({4: s4, 5: s5, ...}; else s_high)
+    ncde_mode: str = "moment"                # NCDE: "moment", "rate" (per-cell s1(phi)) or "cde"
+    a1: float = 0.0                          # NCDE: A1 = a1 I of Eq. (GNCDE) with B-bar = u phi
     f: np.ndarray = field(default=None, repr=False)          # f-bar, shape (Q, *grid)
     phi_prev: np.ndarray = field(default=None, repr=False)   # NCDE: phi at the previous step
     step_count: int = 0
@@ -203,12 +215,36 @@ class Model:
         Eq. (2-4-1) (NCDE, S = 0): phi = sum f."""
         f = self.f if f is None else f
         if self.eq == "ncde":
+            if self.ncde_mode == "cde":
+                # Eq. (2-4-1) with lambda = 1, S_F = 0: phi = sum f + S_G / 2
+                return np.sum(f, axis=0) + 0.5 * self.cde_source(f), None
             return np.sum(f, axis=0), None
         rho = np.sum(f, axis=0)
         F = self.force_field()
         j = np.stack([np.tensordot(self.lat.cvel[:, a], f, axes=(0, 0)) for a in range(self.lat.d)])
         u = (j + 0.5 * F) / rho
         return rho, u
+
+    def cde_source(self, f):
+        """App. A special case (3): S_G = -u . grad phi with the local gradient of
+        Eq. (M-NCDE-3-00a), grad_a phi = -s_a M1_a^ne / (dt cs2_eq), where M1^ne = sum_j c_j f_j
+        (M1 = 0; the printed sum of f_j is read as the first moment)."""
+        lat = self.lat
+        out = np.zeros(f.shape[1:])
+        for r, poly in enumerate(lat.polys):
+            if lat.orders[r] == 1:
+                (ex,) = poly.keys()
+                a = ex.index(1)
+                m1 = np.tensordot(lat.cvel[:, a], f, axes=(0, 0))
+                out = out + self.u_const[a] * self.s[r] * m1 / self.cs2_eq
+        return out
+
+    def rate_of(self, r, phi):
+        """Order-1 rate of row r in the "rate" reading: K(phi) = K0 (1 + nonlin phi^2) with
+        K0 = cs2_eq (1/s_r - 1/2), and s_r(phi) = 1 / (K(phi) / cs2_eq + 1/2) (Eq. (GNCDE-0)
+        read with S1^-1)."""
+        K0 = self.cs2_eq * (1.0 / self.s[r] - 0.5)
+        return 1.0 / (K0 * (1.0 + self.nonlin * phi ** 2) / self.cs2_eq + 0.5)
 
     def equilibrium(self, rho_or_phi, u=None):
         """Eq. (feq-1) for the fields given."""
@@ -217,7 +253,7 @@ class Model:
             j = (u * rho_or_phi[None]).reshape(self.lat.d, -1)
             m = hermite_moments_eq_nse(self.lat, flat, j, self.cs2_eq)
         else:
-            m = hermite_moments_eq_ncde(self.lat, flat, self.u_const, self.cs2_eq, self.nonlin)
+            m = hermite_moments_eq_ncde(self.lat, flat, self.u_const, self.cs2_eq, self.nonlin, self.ncde_mode)
         return from_hermite_moments(self.lat, m).reshape((self.lat.Q,) + self.shape)
 
     def init_fields(self, rho_or_phi, u=None):
@@ -265,14 +301,20 @@ class Model:
                     rows2 = [q for q in range(R) if lat.orders[q] == 2]
                     mG[r] = raw[r] - 0.5 * (S2[r, rows2] @ raw[rows2])
             return mF, mG
-        # NCDE: M1G = (I - S1/2) u d_t phi (Eq. (M-NCDE-6) with M20 = 0, A1 = A2 = 0)
+        if self.ncde_mode == "cde":
+            # App. A special case (3): M0G = (1 - s0/2) S_G (Eq. (M-NCDE-4), lambda = 1), M1G = 0
+            mG[0] = (1.0 - 0.5 * self.s[0]) * self.cde_source(self.f).reshape(-1)
+            return mF, mG
+        # NCDE: M1G = (I - S1/2) u d_t phi - S1 A1 d_t(u phi) (Eq. (M-NCDE-6) with M20 = 0,
+        # B-bar = u phi, A2 = 0); S1 per cell in the "rate" reading
         phi = fields[0].reshape(-1)
         dphi = phi - self.phi_prev.reshape(-1)
         for r, poly in enumerate(lat.polys):
             if lat.orders[r] == 1:
                 (ex,) = poly.keys()
                 a = ex.index(1)
-                mG[r] = (1.0 - 0.5 * self.s[r]) * self.u_const[a] * dphi
+                s1 = self.rate_of(r, phi) if self.ncde_mode == "rate" else self.s[r]
+                mG[r] = (1.0 - 0.5 * s1 - s1 * self.a1) * self.u_const[a] * dphi
         return mF, mG
 
     # -- one step --------------------------------------------------------------------------------
@@ -287,6 +329,13 @@ class Model:
         f = self.f.reshape(lat.Q, -1)
         fne = f - feq.reshape(lat.Q, -1)
         ft = f - self.Lam @ fne + Gd + Fd - 0.5 * (self.Lam @ Fd)
+        if self.eq == "ncde" and self.ncde_mode == "rate":
+            # per-cell S: Lambda(x) = Lambda + sum_r (s_r(phi(x)) - s_r) H^-1[:, r] H[r, :] over the
+            # first-order rows (a change of S on those rows only)
+            phi = rho_or_phi.reshape(-1)
+            for r in lat.block(1):
+                ds = self.rate_of(r, phi) - self.s[r]
+                ft = ft - np.outer(self.Hinv[:, r], lat.Hfull[r] @ fne) * ds[None, :]
         if self.eq == "ncde":
             self.phi_prev = rho_or_phi.copy()
         return ft.reshape(self.f.shape)

@@ -66,7 +66,8 @@ __global__ void k_scatter(const GenParams p, const GenTables<CT> t, const double
   }
 }
 
-// Eq. (2-4-2): rho = sum f, u = (sum c f + F/2) / rho; Eq. (2-4-1): phi = sum f.
+// Eq. (2-4-2): rho = sum f, u = (sum c f + F/2) / rho; Eq. (2-4-1): phi = sum f (+ S_G / 2 for
+// the CDE variant).
 // Computed in the model's compute dtype from the gathered f-bar.
 template <class ST, class CT>
 __global__ void k_fields(const GenParams p, const GenTables<CT> t, const ST* __restrict__ A, int nse,
@@ -84,6 +85,10 @@ __global__ void k_fields(const GenParams p, const GenTables<CT> t, const ST* __r
     j[0] = fma(t.ce[i][0], f, j[0]);
     j[1] = fma(t.ce[i][1], f, j[1]);
     j[2] = fma(t.ce[i][2], f, j[2]);
+  }
+  if (!nse) {
+    // Eq. (2-4-1) with lambda = 1 for the CDE variant: phi = sum f + S_G / 2 (zero otherwise)
+    for (int a = 0; a < 3; ++a) rho = fma(CT(p.cde_half[a]), j[a], rho);
   }
   rho_out[cell] = double(rho);
   if (!nse || u_out == nullptr) return;
@@ -202,6 +207,10 @@ lbm_status gen_params(const lbm_model* m, GenParams* gp) {
     gp->wref[i] = (m->store == LBM_BF16_DEV || m->store == LBM_F16_DEV) ? L->w[i] * m->rho_ref : 0.0;
   }
   for (int a = 0; a < 3; ++a) gp->c[a] = a < L->d ? L->c[a] : 0.0;
+  for (int a = 0; a < 3; ++a)
+    gp->cde_half[a] = (m->eq == LBM_NCDE && m->ncde_variant == LBM_NCDE_CDE && a < L->d)
+                          ? 0.5 * m->u_const[a] * m->s[1 + a] / m->cs2_eq
+                          : 0.0;
   gp->force_a = m->force_a;
   gp->force_b = (m->eq == LBM_NSE && m->force_A != 0.0) ? m->force_b : -1;
   gp->force_tab = m->force_tab;

@@ -100,13 +100,27 @@ void make_step_params(const lbm_model* m, StepParams<CT>* p) {
     }
     p->wmom_ref[r] = CT(rho_ref * acc);
   }
+  // NCDE variants (App. A): a1 folds into the first-order factor of M1G (moment variant);
+  // the rate variant takes its per-cell factors in the kernel; the CDE has no M1 and no M1G
+  p->ncde_variant = m->eq == LBM_NCDE ? m->ncde_variant : LBM_NCDE_MOMENT;
+  if (m->eq == LBM_NCDE) {
+    for (int a = 0; a < L->d; ++a) {
+      const double s1 = m->s[1 + a];
+      p->half[1 + a] = CT(1.0 - 0.5 * s1 - s1 * m->a1);
+      p->kfac[a] = CT(1.0 / s1 - 0.5);
+      p->cde_coef[a] = m->ncde_variant == LBM_NCDE_CDE ? CT(m->u_const[a] * s1 / m->cs2_eq) : CT(0);
+    }
+    p->nonlin_rate = m->ncde_variant == LBM_NCDE_RATE ? CT(m->nonlin) : CT(0);
+    p->a1 = CT(m->a1);
+    p->half0 = CT(1.0 - 0.5 * m->s[0]);
+  }
   p->sh_rho_ref = CT(m->s_high * rho_ref);
   p->s_high = CT(m->s_high);
   p->one_minus_sh = CT(1.0 - m->s_high);
   p->cs2_eq = CT(m->cs2_eq);
-  p->nonlin_third = CT(m->nonlin / 3.0);
+  p->nonlin_third = CT(m->ncde_variant == LBM_NCDE_MOMENT ? m->nonlin / 3.0 : 0.0);
   for (int a = 0; a < 3; ++a) {
-    p->u_const[a] = CT(m->u_const[a]);
+    p->u_const[a] = CT(m->ncde_variant == LBM_NCDE_CDE ? 0.0 : m->u_const[a]);
     p->n[a] = a < L->d ? int(m->n[a]) : 1;
   }
   p->ncells = m->ncells;
@@ -154,6 +168,35 @@ void make_high_params(const lbm_model* m, HighParams<CT>* hp) {
   }
 }
 
+void make_tc_params(const lbm_model* m, TcParams* tp) {
+  const lbm_lattice* L = m->lat;
+  std::memset(tp, 0, sizeof(*tp));
+  for (int i = 0; i < L->Q; ++i)
+    for (int r = 0; r < L->R; ++r) {
+      const Mono mk = L->d == 2 ? kMono2[r] : kMono3[r];
+      int v = 1;
+      for (int q = 0; q < mk.a; ++q) v *= L->e[i * 3 + 0];
+      for (int q = 0; q < mk.b; ++q) v *= L->e[i * 3 + 1];
+      for (int q = 0; q < mk.c; ++q) v *= L->e[i * 3 + 2];
+      tp->mono[i][r] = int8_t(v);
+    }
+  tp->ntiles = (m->ncells + 127) / 128;
+  tp->status = m->status;
+  tp->no_issue = m->tc_no_issue ? 1 : 0;
+  tp->wait_limit = m->tc_no_issue ? (1u << 10) : (1u << 22);
+}
+
+// Persistent grid of the tensor-core kernel: resident CTAs per SM (at most 4, so that their
+// 128 TMEM columns each fit the SM's 512) times the SM count, capped by the tile count.
+int tc_grid(const lbm_model* m, int ntiles, const void* kernel) {
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
+  per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+  const int g = (sms > 0 ? sms : 1) * per_sm;
+  return ntiles < g ? ntiles : g;
+}
+
 template void make_high_params<float>(const lbm_model*, HighParams<float>*);
 template void make_high_params<double>(const lbm_model*, HighParams<double>*);
 
@@ -163,7 +206,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t f_bytes, phi_off, force_off, part_off, sums_off, total;
+  size_t f_bytes, phi_off, force_off, part_off, sums_off, status_off, total;
 };
 
 Layout layout(const lbm_lattice* L, int eq, const int64_t* n, int store) {
@@ -180,7 +223,8 @@ Layout layout(const lbm_lattice* L, int eq, const int64_t* n, int store) {
   lo.force_off = lo.phi_off + phi_bytes;
   lo.part_off = lo.force_off + align_up(size_t(nmax) * cbytes);
   lo.sums_off = lo.part_off + align_up(size_t(kRedBlocks) * 4 * sizeof(double));
-  lo.total = lo.sums_off + align_up(4 * sizeof(double));
+  lo.status_off = lo.sums_off + align_up(4 * sizeof(double));
+  lo.total = lo.status_off + align_up(sizeof(int));
   return lo;
 }
 
@@ -228,6 +272,20 @@ lbm_status upload_force(lbm_model* m) {
   }
   if (err == cudaSuccess) err = cudaStreamSynchronize(m->stream);
   return err == cudaSuccess ? LBM_OK : cuda_error(err, "force upload");
+}
+
+// Read and clear the model's device status word (the stream must allow a synchronisation).
+lbm_status take_status(lbm_model* m) {
+  int s = 0;
+  cudaError_t err = cudaMemcpyAsync(&s, m->status, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(m->stream);
+  if (err != cudaSuccess) return cuda_error(err, "status word");
+  if (s == 0) return LBM_OK;
+  err = cudaMemsetAsync(m->status, 0, sizeof(int), m->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(m->stream);
+  if (err != cudaSuccess) return cuda_error(err, "status word");
+  return set_error(LBM_ERR_TIMEOUT,
+                   "a tensor-core step gave up waiting for its matrix products; the populations are invalid");
 }
 
 template <class F>
@@ -407,6 +465,7 @@ lbm_status lbm_model_create(const lbm_lattice* L, lbm_eq eq, const int64_t* n, l
     m->force_tab = base + lo.force_off;
     m->partials = reinterpret_cast<double*>(base + lo.part_off);
     m->sums = reinterpret_cast<double*>(base + lo.sums_off);
+    m->status = reinterpret_cast<int*>(base + lo.status_off);
     cudaError_t err = cudaMemsetAsync(m->ws, 0, lo.total, m->stream);
     if (err != cudaSuccess) {
       if (m->owns_ws) cudaFree(m->ws);
@@ -468,6 +527,16 @@ lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_o
   return LBM_OK;
 }
 
+lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (enable < 0 || enable > 2) return set_error(LBM_ERR_ARG, "enable must be 0, 1 or 2");
+  if (enable && m->store != LBM_BF16_DEV && m->store != LBM_F16_DEV)
+    return set_error(LBM_ERR_ARG, "the tensor-core collision needs 16-bit deviation storage");
+  m->tensor_cores = enable != 0;
+  m->tc_no_issue = enable == 2;
+  return LBM_OK;
+}
+
 lbm_status lbm_model_set_eos(lbm_model* m, double cs2_eq) {
   if (!m) return set_error(LBM_ERR_ARG, "NULL model");
   if (!(cs2_eq > 0.0) || !std::isfinite(cs2_eq)) return set_error(LBM_ERR_ARG, "cs2_eq must be positive");
@@ -497,6 +566,20 @@ lbm_status lbm_model_set_ncde(lbm_model* m, const double* u_const, double nonlin
   if (m->eq != LBM_NCDE) return set_error(LBM_ERR_ARG, "convection velocity applies to the NCDE model");
   for (int a = 0; a < 3; ++a) m->u_const[a] = a < m->lat->d ? u_const[a] : 0.0;
   m->nonlin = nonlin;
+  batch_mark_dirty(m->batch);
+  return LBM_OK;
+}
+
+lbm_status lbm_model_set_ncde_variant(lbm_model* m, lbm_ncde_variant variant, double a1) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (m->eq != LBM_NCDE) return set_error(LBM_ERR_ARG, "the variants apply to the NCDE model");
+  if (int(variant) < LBM_NCDE_MOMENT || int(variant) > LBM_NCDE_CDE) return set_error(LBM_ERR_ARG, "unknown NCDE variant");
+  if (!std::isfinite(a1)) return set_error(LBM_ERR_ARG, "a1 must be finite");
+  if (variant == LBM_NCDE_CDE && a1 != 0.0) return set_error(LBM_ERR_ARG, "the CDE variant has no mixed-derivative term");
+  if (m->batch && variant != LBM_NCDE_MOMENT)
+    return set_error(LBM_ERR_NOT_IMPLEMENTED, "the rate and CDE variants are not available inside a batch");
+  m->ncde_variant = variant;
+  m->a1 = a1;
   batch_mark_dirty(m->batch);
   return LBM_OK;
 }
@@ -573,6 +656,7 @@ lbm_status lbm_model_get_populations(lbm_model* m, double* f, int on_device) {
   if (!on_device) {
     cudaError_t err = cudaStreamSynchronize(m->stream);
     if (err != cudaSuccess) return cuda_error(err, "population download");
+    return take_status(m);
   }
   return LBM_OK;
 }
@@ -617,6 +701,7 @@ lbm_status lbm_model_read_fields(lbm_model* m, double* rho_or_phi, double* u, in
   if (!on_device) {
     cudaError_t err = cudaStreamSynchronize(m->stream);
     if (err != cudaSuccess) return cuda_error(err, "field download");
+    return take_status(m);
   }
   return LBM_OK;
 }
@@ -630,6 +715,8 @@ lbm_status lbm_model_conserved_sums(lbm_model* m, double* out_host) {
   cudaError_t err = cudaMemcpyAsync(s, m->sums, sizeof(s), cudaMemcpyDeviceToHost, m->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(m->stream);
   if (err != cudaSuccess) return cuda_error(err, "conservation sums");
+  st = take_status(m);
+  if (st != LBM_OK) return st;
   const int d = m->lat->d;
   bool finite = true;
   for (int q = 0; q <= d; ++q) {
@@ -651,7 +738,8 @@ lbm_status lbm_model_synchronize(lbm_model* m) {
   if (!m) return set_error(LBM_ERR_ARG, "NULL model");
   DeviceGuard guard(m->device);
   cudaError_t err = cudaStreamSynchronize(m->stream);
-  return err == cudaSuccess ? LBM_OK : cuda_error(err, "synchronize");
+  if (err != cudaSuccess) return cuda_error(err, "synchronize");
+  return take_status(m);
 }
 
 lbm_status lbm_model_destroy(lbm_model* m) {

@@ -57,6 +57,11 @@ struct lbm_model {
   double force_A, force_phase;
   double u_const[3];
   double nonlin;
+  int ncde_variant;  // lbm_ncde_variant
+  double a1;         // mixed-derivative coefficient A1 = a1 I (Eq. (GNCDE))
+  bool tensor_cores; // 16-bit storage: contractions on tcgen05 (k_step_tc)
+  bool tc_no_issue;  // test hook: k_step_tc issues no matrix product, so its waits run out
+  int* status;       // device status word: non-zero after a device-side wait ran out
   int64_t steps, launches;
   int device;
   lbm_batch* batch;         // batch the model belongs to (its kernels then run on the batch's stream)
@@ -88,13 +93,21 @@ struct StepParams {
   CT wmom_ref[kMaxR];  // rho_ref sum_i w_i mono_k(e_i): moments of the reference state w_i rho_ref
   CT sh_rho_ref;       // s_high * rho_ref
   CT s_high, one_minus_sh, cs2_eq, nonlin_third;
-  CT u_const[3];
+  CT u_const[3];         // NCDE: convection velocity of M1 = u phi (zero for the CDE variant)
+  // NCDE variants: per-cell first-order rates (RATE: s_a(phi) = 1 / (kfac_a g(phi) + 1/2),
+  // g = 1 + nonlin_rate phi^2) and the CDE source (S_G = sum_a cde_coef_a M1_a, M0G = half0 S_G)
+  int ncde_variant;
+  CT kfac[3];
+  CT nonlin_rate, a1;
+  CT cde_coef[3];
+  CT half0;
   int n[3];
   int ncells;
   unsigned div_m[2];     // cell index -> (x, y, z): q = umulhi(v, div_m) >> div_s exactly divides
   int div_s[2];          // by n[0] (slot 0) and n[1] (slot 1) for every v < 2^31
   int force_a, force_b;  // force_b < 0: no body force
   const CT* force_tab;
+  static constexpr bool kNcdeVariants = true;
 };
 
 // Rows of order >= 4 that relax with their own rates (the full Q x Q collision). The kernel
@@ -107,6 +120,16 @@ struct HighParams {
   CT ho[kMaxHighOdd][kMaxPairs];
   CT ae[kMaxHighEven];
   CT ao[kMaxHighOdd];
+};
+
+// Tensor-core kernel parameters: the monomial table mono_k(e_i) (paper's row order) and the
+// tile count; status receives 1 if an mbarrier wait ran out.
+struct TcParams {
+  int8_t mono[kMaxQ][kMaxR];
+  int ntiles;
+  int* status;
+  unsigned wait_limit;  // mbarrier polls before a wait is declared lost
+  int no_issue;         // test hook: issue no matrix product (every wait then runs out)
 };
 
 // Multiply-high division by a runtime divisor 2 <= d < 2^31, exact for numerators below 2^31:
@@ -124,6 +147,7 @@ struct GenParams {
   int8_t e[kMaxQ][3];
   double c[3];
   double wref[kMaxQ];
+  double cde_half[3];  // NCDE CDE variant: phi = sum f + sum_a cde_half_a sum_i c_ia f_i
   int force_a, force_b;
   const void* force_tab;
 };
@@ -277,5 +301,7 @@ template <class CT>
 void make_high_params(const lbm_model* m, HighParams<CT>* hp);
 // true when some row of order >= 4 relaxes with a rate other than s_high
 bool has_high_rates(const lbm_model* m);
+void make_tc_params(const lbm_model* m, TcParams* tp);
+int tc_grid(const lbm_model* m, int ntiles, const void* kernel);
 
 }  // namespace lbm

@@ -20,14 +20,15 @@
 
 #include "lbm_internal.cuh"
 
-// Tuning knobs of the collide-stream kernel (defaults measured best on GB300 for rD3Q53 FP32:
-// 5 blocks of 128 threads per SM cap the kernel at 96 registers, 20 warps/SM instead of 16,
-// 0.838 ms instead of 0.852 ms per 256x256x192 step; evict-first loads or stores were slower):
+// Tuning knobs of the collide-stream kernel (defaults measured best on GB300 for rD3Q53 on
+// 256x256x192: 4 blocks of 128 threads per SM leave the kernel 128 registers without spills,
+// 0.833 ms per FP32 step and 0.686 ms per FP16-deviation step, against 0.883 / 0.732 ms with
+// 5 blocks (96 registers) and 0.989 / 0.756 ms with 6; evict-first loads or stores were slower):
 //   LBM_K1_MIN_BLOCKS  minimum resident blocks per SM requested through __launch_bounds__
 //   LBM_K1_LOAD        0: ld.global.nc (__ldg), 1: evict-first (__ldcs), 2: plain load
 //   LBM_K1_STORE       0: plain store, 1: evict-first streaming store (__stcs)
 #ifndef LBM_K1_MIN_BLOCKS
-#define LBM_K1_MIN_BLOCKS 5
+#define LBM_K1_MIN_BLOCKS 4
 #endif
 #ifndef LBM_K1_LOAD
 #define LBM_K1_LOAD 0
@@ -246,13 +247,23 @@ __device__ __forceinline__ void row_moments(const P& p, const CT (&mu)[L::R], co
   }
 }
 
+// Per-cell first-order factors of the NCDE (from the parameters, or per cell for the rate
+// variant) and the CDE source S_G (zero otherwise).
+template <class CT>
+struct NcdeCell {
+  CT sd1[3];    // s_a - s_high on the first-order rows
+  CT half1[3];  // factor of u d_t phi in M1G
+  CT sg;        // S_G of the CDE variant
+};
+
 // g_r / N_r with g = s_h m^eq - (S - s_h I)(m - m^eq) + sigma. S is diagonal except on the normal
 // second-order rows, where the d x d block S_n carries the bulk coupling of Eq. (4-27).
 // sigma: NSE (I - S/2) M1F = (1 - s/2) F on order 1 and M2G = (I - S2/2)(uF + Fu) on order 2;
-// NCDE M1G = (I - S1/2) u d_t phi on order 1.
+// NCDE M1G = (I - S1/2) u d_t phi - S1 A1 d_t(u phi) on order 1 (factor half1) and, for the
+// CDE variant, M0G = (1 - s0/2) S_G on order 0.
 template <class L, class CT, int EQ, int r, class P>
 __device__ __forceinline__ CT row_update(const P& p, const CT (&meq)[L::R], const CT (&neq)[L::R],
-                                         const CT (&u)[3], const CT (&F)[3], CT dphi) {
+                                         const CT (&u)[3], const CT (&F)[3], CT dphi, const NcdeCell<CT>& nc) {
   constexpr int deg = degree(mono<L::D>(r));
   constexpr int na = normal_index<L::D>(r);
   CT relax, sig = CT(0);
@@ -267,8 +278,14 @@ __device__ __forceinline__ CT row_update(const P& p, const CT (&meq)[L::R], cons
     relax = p.sd[r] * neq[r];
     if constexpr (deg == 1) {
       constexpr int a = axis_n(mono<L::D>(r), 0);
-      if constexpr (EQ == LBM_NSE) sig = p.half[r] * F[a];
-      else sig = p.half[r] * p.u_const[a] * dphi;
+      if constexpr (EQ == LBM_NSE) {
+        sig = p.half[r] * F[a];
+      } else {
+        relax = nc.sd1[a] * neq[r];
+        sig = nc.half1[a] * p.u_const[a] * dphi;
+      }
+    } else if constexpr (deg == 0 && EQ == LBM_NCDE && P::kNcdeVariants) {
+      sig = p.half0 * nc.sg;
     } else if constexpr (deg == 2 && EQ == LBM_NSE) {
       constexpr int a = axis_n(mono<L::D>(r), 0), b = axis_n(mono<L::D>(r), 1);
       sig = p.half[r] * fma(u[a], F[b], u[b] * F[a]);
@@ -333,16 +350,16 @@ __device__ __forceinline__ void high_back(CT (&f)[L::Q], const P& p, const HighP
 // DEV: f holds deviations f - w rho_ref (16-bit storage). The moments of the reference state are
 // added back (only 1 and the squares c_a^2 have non-zero lattice moments), and the update
 // f* - w rho_ref = (1 - s_h)(f - w rho_ref) + w H(h) - s_h w rho_ref folds the last term into h_0.
-// HI: rows of order >= 4 relax with the rates of hp (the full Q x Q collision); hp may be null
-// otherwise.
-template <class L, class CT, int EQ, bool DEV = false, bool HI = false, class P>
-__device__ __forceinline__ void collide(CT (&f)[L::Q], const P& p, const CT (&F)[3],
-                                        CT phi_prev, CT& phi_now, const HighParams<CT>* hp = nullptr) {
+// HP = HighParams<CT>: the rows of order >= 4 relax with the rates of hp (the full Q x Q
+// collision); HP = NoHigh: they share s_high (the reduced form alone).
+struct NoHigh {};
+
+// The collision in moment space: from the raw moments mu_k = sum_i mono_k(e_i) f_i (k < R) to
+// the monomial-basis coefficients h of the update f*_i = (1 - s_h) f_i + w_i sum_k mono_k(e_i) h_k.
+template <class L, class CT, int EQ, bool DEV, class P>
+__device__ __forceinline__ void collide_moments(CT (&mu)[L::R], const P& p, const CT (&F)[3], CT phi_prev,
+                                                CT& phi_now, CT (&h)[L::R]) {
   constexpr int R = L::R, D = L::D;
-  CT ze[high_even<L>()], zo[high_odd<L>() > 0 ? high_odd<L>() : 1];
-  if constexpr (HI) high_moments<L>(f, *hp, ze, zo);
-  CT mu[R];
-  raw_moments<L>(f, mu);
   if constexpr (DEV) {
     static_for<R>([&](auto k) {
       constexpr Mono mk = mono<L::D>(decltype(k)::value);
@@ -358,6 +375,7 @@ __device__ __forceinline__ void collide(CT (&f)[L::Q], const P& p, const CT (&F)
   CT me[R];
   CT u[3] = {CT(0), CT(0), CT(0)};
   CT dphi = CT(0);
+  NcdeCell<CT> nc;
   if constexpr (EQ == LBM_NSE) {
     // Eq. (2-4-2) with S = 0, F_F = F: rho = sum f, rho u = sum c f + F / 2
     const CT rho = mu[0];
@@ -370,8 +388,31 @@ __device__ __forceinline__ void collide(CT (&f)[L::Q], const P& p, const CT (&F)
     });
     eq_raw_nse<L>(rho, j, u, rho * p.cs2_eq, me);
   } else {
-    // Eq. (2-4-1) with S = 0: phi = sum f
-    const CT phi = mu[0];
+    // Eq. (2-4-1) with S = 0: phi = sum f (+ S_G / 2, lambda = 1, for the CDE variant)
+    CT phi = mu[0];
+    static_for<3>([&](auto a) {
+      nc.sd1[decltype(a)::value] = p.sd[decltype(a)::value + 1];
+      nc.half1[decltype(a)::value] = p.half[decltype(a)::value + 1];
+    });
+    nc.sg = CT(0);
+    if constexpr (P::kNcdeVariants) {
+      if (p.ncde_variant == LBM_NCDE_CDE) {
+        // S_G = -u . grad phi with grad_a phi = -s_a M1_a^ne / cs2 (M1 = 0)
+        CT sg = CT(0);
+        static_for<D>([&](auto a) { sg = fma(p.cde_coef[decltype(a)::value], mu[1 + decltype(a)::value], sg); });
+        nc.sg = sg;
+        phi = fma(CT(0.5), sg, phi);
+      } else if (p.ncde_variant == LBM_NCDE_RATE) {
+        // s_a(phi) = 1 / ((1/s_a - 1/2)(1 + nonlin phi^2) + 1/2)
+        const CT g = fma(p.nonlin_rate, phi * phi, CT(1));
+        static_for<D>([&](auto a) {
+          constexpr int A = decltype(a)::value;
+          const CT s1 = CT(1) / fma(p.kfac[A], g, CT(0.5));
+          nc.sd1[A] = s1 - p.s_high;
+          nc.half1[A] = fma(-s1, CT(0.5) + p.a1, CT(1));
+        });
+      }
+    }
     phi_now = phi;
     dphi = phi - phi_prev;
     eq_raw_ncde<L>(phi, fma(p.nonlin_third, phi * phi * phi, phi), p, me);
@@ -384,13 +425,24 @@ __device__ __forceinline__ void collide(CT (&f)[L::Q], const P& p, const CT (&F)
   CT gN[R];
   static_for<R>([&](auto r) {
     constexpr int Rr = decltype(r)::value;
-    gN[Rr] = row_update<L, CT, EQ, Rr>(p, meq, neq, u, F, dphi);
+    gN[Rr] = row_update<L, CT, EQ, Rr>(p, meq, neq, u, F, dphi, nc);
   });
-  CT h[R];
   hermite_to_monomial<L>(p, gN, h);
   if constexpr (DEV) h[0] -= p.sh_rho_ref;
+}
+
+template <class L, class CT, int EQ, bool DEV = false, class P, class HP = NoHigh>
+__device__ __forceinline__ void collide(CT (&f)[L::Q], const P& p, const CT (&F)[3],
+                                        CT phi_prev, CT& phi_now, const HP& hp = HP{}) {
+  constexpr bool HI = !std::is_same<HP, NoHigh>::value;
+  CT ze[high_even<L>()], zo[high_odd<L>() > 0 ? high_odd<L>() : 1];
+  if constexpr (HI) high_moments<L>(f, hp, ze, zo);
+  CT mu[L::R];
+  raw_moments<L>(f, mu);
+  CT h[L::R];
+  collide_moments<L, CT, EQ, DEV>(mu, p, F, phi_prev, phi_now, h);
   back_project<L>(f, p, h, p.one_minus_sh);
-  if constexpr (HI) high_back<L>(f, p, *hp, ze, zo);
+  if constexpr (HI) high_back<L>(f, p, hp, ze, zo);
 }
 
 // Equilibrium populations of given fields, Eq. (feq-1): f^eq_i = w_i sum_r H_ri m^eq_r / N_r.
@@ -518,7 +570,7 @@ __global__ void __launch_bounds__(kBlock, LBM_K1_MIN_BLOCKS) k_step(const StepPa
 // kernel is bound by the FMA pipe rather than HBM; fewer resident blocks leave it the registers).
 template <class L, class CT, class ST, int EQ>
 __global__ void __launch_bounds__(kBlock, 2) k_step_high(const StepParams<CT> p,
-                                                          const __grid_constant__ HighParams<CT> hp,
+                                                          const HighParams<CT> hp,
                                                           const ST* __restrict__ fin,
                                                           ST* __restrict__ fout, CT* __restrict__ phi) {
   const int cell = blockIdx.x * kBlock + threadIdx.x;
@@ -536,7 +588,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_step_high(const StepParams<CT> p,
   body_force(p.force_a, p.force_b, p.force_tab, nb.x, nb.y, nb.z, F);
   CT phi_prev = CT(0), phi_now = CT(0);
   if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
-  collide<L, CT, EQ, DEV, true>(f, p, F, phi_prev, phi_now, &hp);
+  collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, hp);
   if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
   static_for<L::Q>([&](auto i) {
     constexpr int I = decltype(i)::value;
@@ -586,6 +638,7 @@ struct BatchView {
   const CT (&halfn)[3][3];
   const CT (&u_const)[3];
   CT s_high, one_minus_sh, sh_rho_ref, cs2_eq, nonlin_third;
+  static constexpr bool kNcdeVariants = false;  // batched NCDE solves use the moment variant
   __device__ __forceinline__ BatchView(const BatchTables<CT>& t, const SolveDesc<CT>& d)
       : T(t.T), D(t.D), invN(t.invN), w(t.w), wref(t.wref), wmom_ref(t.wmom_ref), sd(d.sd), half(d.half),
         sdn(d.sdn), halfn(d.halfn), u_const(d.u_const), s_high(d.s_high), one_minus_sh(d.one_minus_sh), sh_rho_ref(d.sh_rho_ref),
@@ -647,6 +700,12 @@ __global__ void __launch_bounds__(BLOCK, batch_min_blocks<BLOCK>())
   }
 }
 
+}  // namespace lbm
+
+#include "tc_kernels.cuh"
+
+namespace lbm {
+
 template <class L, class CT, class ST, int EQ, class F>
 lbm_status batch_by_block(int block, F&& fn) {
   switch (block) {
@@ -707,10 +766,31 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
   const bool high = collide_on && has_high_rates(m);
   HighParams<CT> hp;
   if (high) make_high_params<CT>(m, &hp);
+  [[maybe_unused]] const bool tensor = collide_on && !high && m->tensor_cores;
+  TcParams tp;
+  int tgrid = 0;
+  if constexpr (is_deviation_storage<ST>()) {
+    if (tensor) {
+      make_tc_params(m, &tp);
+      tgrid = m->eq == LBM_NSE ? tc_grid(m, tp.ntiles, reinterpret_cast<const void*>(k_step_tc<L, ST, LBM_NSE>))
+                               : tc_grid(m, tp.ntiles, reinterpret_cast<const void*>(k_step_tc<L, ST, LBM_NCDE>));
+    }
+  }
   for (int64_t s = 0; s < nsteps; ++s) {
     const ST* fin = static_cast<const ST*>(m->f[m->cur]);
     ST* fout = static_cast<ST*>(m->f[m->cur ^ 1]);
-    if (high) {
+    bool done = false;
+    if constexpr (is_deviation_storage<ST>()) {
+      if (tensor) {
+        if (m->eq == LBM_NSE)
+          k_step_tc<L, ST, LBM_NSE><<<tgrid, 128, 0, m->stream>>>(p, tp, fin, fout, phi);
+        else
+          k_step_tc<L, ST, LBM_NCDE><<<tgrid, 128, 0, m->stream>>>(p, tp, fin, fout, phi);
+        done = true;
+      }
+    }
+    if (done) {
+    } else if (high) {
       if (m->eq == LBM_NSE)
         k_step_high<L, CT, ST, LBM_NSE><<<grid, kBlock, 0, m->stream>>>(p, hp, fin, fout, phi);
       else

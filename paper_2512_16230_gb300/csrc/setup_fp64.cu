@@ -354,12 +354,16 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup_high(const SetupIn in, 
         __syncthreads();
         if (tid < Q) hw->Hh[n][tid] = v[tid] / scale;
         __syncthreads();
+        // a row whose W-norm vanishes on the scale of the largest weight lives on zero-weight
+        // velocities only (the Euclidean norm of a unit-max row is at least 1)
         const double nn = block_sum64(tid < Q ? low->w[tid] * hw->Hh[n][tid] * hw->Hh[n][tid] : 0.0, red);
-        const double na = block_sum64(tid < Q ? fabs(low->w[tid]) * hw->Hh[n][tid] * hw->Hh[n][tid] : 0.0, red);
+        const double ne = block_sum64(tid < Q ? hw->Hh[n][tid] * hw->Hh[n][tid] : 0.0, red);
         if (tid == 0) {
+          double wmax = 0.0;
+          for (int i = 0; i < Q; ++i) wmax = fabs(low->w[i]) > wmax ? fabs(low->w[i]) : wmax;
           hw->N[n] = nn;
           hw->order[n] = deg;
-          if (!(fabs(nn) > 1e-10 * na)) hw->status = 2;
+          if (!(fabs(nn) > 1e-10 * wmax * ne)) hw->status = 2;
         }
         __syncthreads();
         ++n;

@@ -1,0 +1,244 @@
+// Tensor-core collide-stream kernel for 16-bit deviation storage (FP16 or BF16 deviations
+// f_i - w_i rho_ref, collision arithmetic in FP32).
+//
+// The two contractions of the collision with the lattice are dense products over one tile of
+// 128 cells, with integer coefficients mono_k(e_i) that are exact in FP16/BF16:
+//   forward   mu (128 x R)  = D (128 x Q) . M^T (Q x R),   D the stored deviations (exact operands)
+//   backward  Delta (128 x Q) = h (128 x R) . M (R x Q),    f*_i = (1 - s_h) d_i + w_i Delta_i
+// with M_ki = mono_k(e_i). Both run on tcgen05 (kind::f16, M = 128, FP32 accumulation in TMEM);
+// one thread of the CTA issues them, and every thread reads its own cell's row back with a
+// 32x32b tensor-memory load. h, computed per cell in FP32 by the same moment-space collision as
+// the CUDA-core kernel (collide_moments), is scaled per cell by a power of two and split into a
+// 16-bit high and low part (K = 2R), so the back projection keeps about 22 bits of h.
+// Operands sit in shared memory in the K-major, non-swizzled canonical layout (core matrices of
+// 8 rows x 16 bytes). Every mbarrier wait is bounded: on timeout the CTA records an error in the
+// model's status word, frees its tensor memory and returns.
+#pragma once
+
+#include "tcgen05.cuh"
+
+namespace lbm {
+
+template <class L>
+struct TcShape {
+  static constexpr int QP = (L::Q + 15) / 16 * 16;  // K of the forward product, N of the backward
+  static constexpr int RP = (L::R + 15) / 16 * 16;  // N of the forward product
+  static constexpr int K2 = 2 * RP;                 // K of the backward product (high | low)
+};
+
+// Byte offset of element (r, k) of a K-major tile of 16-bit values with KP values per row.
+__host__ __device__ constexpr uint32_t kmajor_off(int r, int k, int KP) {
+  return uint32_t((r >> 3) * (KP * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+template <class L>
+struct __align__(1024) TcSmem {
+  using S = TcShape<L>;
+  uint8_t a[128 * S::QP * 2];   // deviations: row = cell, k = population
+  uint8_t b1[S::RP * S::QP * 2];  // row = monomial k, column = population i: mono_k(e_i)
+  uint8_t a2[128 * S::K2 * 2];  // per-cell h: high parts, then low parts
+  uint8_t b2[S::QP * S::K2 * 2];  // row = population i, column = monomial (twice): mono_k(e_i)
+  uint64_t mbar;
+  uint32_t tmem;
+};
+
+template <class ST>
+__device__ __forceinline__ uint16_t bits16(ST v);
+template <>
+__device__ __forceinline__ uint16_t bits16(__half v) { return __half_as_ushort(v); }
+template <>
+__device__ __forceinline__ uint16_t bits16(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+
+template <class ST>
+__device__ __forceinline__ ST from_bits16(uint16_t b);
+template <>
+__device__ __forceinline__ __half from_bits16(uint16_t b) { return __ushort_as_half(b); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_bits16(uint16_t b) { return __ushort_as_bfloat16(b); }
+
+template <class ST>
+__device__ __forceinline__ uint16_t round16(float v) {
+  if constexpr (std::is_same<ST, __half>::value) return __half_as_ushort(__float2half_rn(v));
+  else return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+constexpr int kTcCols = 128;                  // TMEM columns per CTA: D1 at 0, D2 at 64
+
+template <class L, class ST, int EQ>
+__global__ void __launch_bounds__(128, 4) k_step_tc(const StepParams<float> p, const TcParams tp,
+                                                    const ST* __restrict__ fin, ST* __restrict__ fout,
+                                                    float* __restrict__ phi) {
+  using S = TcShape<L>;
+  constexpr int Q = L::Q, R = L::R, QP = S::QP, RP = S::RP, K2 = S::K2;
+  constexpr bool BF = std::is_same<ST, __nv_bfloat16>::value;
+  static_assert(QP <= 64 && RP <= 32, "TMEM column plan: D1 in columns [0, 32), D2 in [64, 128)");
+  __shared__ TcSmem<L> sm;
+  const int tid = threadIdx.x;
+
+  // operand tables, once per CTA
+  for (int idx = tid; idx < RP * QP; idx += 128) {
+    const int n = idx / QP, k = idx % QP;
+    const float v = (n < R && k < Q) ? float(tp.mono[k][n]) : 0.f;
+    *reinterpret_cast<uint16_t*>(sm.b1 + kmajor_off(n, k, QP)) = round16<ST>(v);
+  }
+  for (int idx = tid; idx < QP * K2; idx += 128) {
+    const int i = idx / K2, k = idx % K2, kk = k % RP;
+    const float v = (i < Q && kk < R) ? float(tp.mono[i][kk]) : 0.f;
+    *reinterpret_cast<uint16_t*>(sm.b2 + kmajor_off(i, k, K2)) = round16<ST>(v);
+  }
+  if (tid == 0) {
+    tc::mbar_init(&sm.mbar, 1);
+    tc::mbar_fence_init();
+  }
+  if (tid < 32) {
+    tc::alloc(&sm.tmem, kTcCols);
+    tc::relinquish();
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = sm.tmem;
+  const uint32_t row_lane = uint32_t(tid & ~31) << 16;  // this warp's 32 TMEM lanes
+  const uint32_t d1 = tmem, d2 = tmem + 64;
+  const uint32_t a_s = tc::smem_addr(sm.a), b1_s = tc::smem_addr(sm.b1);
+  const uint32_t a2_s = tc::smem_addr(sm.a2), b2_s = tc::smem_addr(sm.b2);
+  constexpr uint32_t idesc1 = tc::idesc_f16<BF>(128, RP);
+  constexpr uint32_t idesc2 = tc::idesc_f16<BF>(128, QP);
+  const size_t N = size_t(p.ncells);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  for (int tile = blockIdx.x; tile < tp.ntiles; tile += gridDim.x) {
+    const int cell = tile * 128 + tid;
+    const bool live = cell < p.ncells;
+    uint32_t dp[QP / 2];  // raw 16-bit deviations, two per register
+    static_for<QP / 2>([&](auto j) { dp[decltype(j)::value] = 0u; });
+    int x = 0, y = 0, z = 0;
+    if (live) {
+      const Neigh<L> nb(cell, p);
+      x = nb.x;
+      y = nb.y;
+      z = nb.z;
+      static_for<Q>([&](auto i) {
+        constexpr int I = decltype(i)::value;
+        const uint32_t b = bits16(k1_load(fin + size_t(I) * N + nb.template src<I>()));
+        dp[I / 2] |= (I & 1) ? (b << 16) : b;
+      });
+    }
+    static_for<QP / 8>([&](auto c) {
+      constexpr int C = decltype(c)::value;
+      *reinterpret_cast<uint4*>(sm.a + kmajor_off(tid, 8 * C, QP)) =
+          make_uint4(dp[4 * C], dp[4 * C + 1], dp[4 * C + 2], dp[4 * C + 3]);
+    });
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0 && !tp.no_issue) {
+      tc::fence_after_sync();
+      static_for<QP / 16>([&](auto kk) {
+        constexpr int KK = decltype(kk)::value;
+        tc::mma_f16(d1, tc::smem_desc(a_s + KK * 256, 128, QP * 16), tc::smem_desc(b1_s + KK * 256, 128, QP * 16),
+                    idesc1, KK > 0 ? 1u : 0u);
+      });
+      tc::commit(&sm.mbar);
+    }
+    bool ok = tc::mbar_wait_bounded(&sm.mbar, phase, tp.wait_limit);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+
+    // moments of this cell's row, then the moment-space collision in FP32
+    float mu[R];
+    static_for<RP / 16>([&](auto c) {
+      constexpr int C = decltype(c)::value;
+      float v[16];
+      tc::ld16(d1 + row_lane + 16 * C, v);
+      tc::wait_ld();
+      static_for<16>([&](auto j) {
+        constexpr int K = 16 * C + decltype(j)::value;
+        if constexpr (K < R) mu[K] = v[decltype(j)::value];
+      });
+    });
+    float F[3] = {0.f, 0.f, 0.f};
+    body_force(p.force_a, p.force_b, p.force_tab, x, y, z, F);
+    float phi_prev = 0.f, phi_now = 0.f;
+    if constexpr (EQ == LBM_NCDE) phi_prev = live ? phi[cell] : 0.f;
+    float h[R];
+    collide_moments<L, float, EQ, true>(mu, p, F, phi_prev, phi_now, h);
+    if constexpr (EQ == LBM_NCDE) {
+      if (live) phi[cell] = phi_now;
+    }
+    // per-cell power-of-two scale, then h = high + low in 16 bits each
+    float hmax = 0.f;
+    static_for<R>([&](auto k) { hmax = fmaxf(hmax, fabsf(h[decltype(k)::value])); });
+    const uint32_t ex = (__float_as_uint(hmax) >> 23) & 0xFFu;
+    const float sc = (live && hmax > 0.f && ex >= 1u && ex <= 252u) ? __uint_as_float((254u - ex) << 23) : 1.f;
+    uint32_t hp[K2 / 2];
+    static_for<K2 / 2>([&](auto j) { hp[decltype(j)::value] = 0u; });
+    static_for<R>([&](auto k) {
+      constexpr int K = decltype(k)::value;
+      const float v = live ? h[K] * sc : 0.f;
+      const uint16_t hi = round16<ST>(v);
+      const float hif = float(RawCodec<ST>::dec(from_bits16<ST>(hi)));
+      const uint16_t lo = round16<ST>(v - hif);
+      hp[K / 2] |= (K & 1) ? (uint32_t(hi) << 16) : uint32_t(hi);
+      hp[(RP + K) / 2] |= (K & 1) ? (uint32_t(lo) << 16) : uint32_t(lo);
+    });
+    static_for<K2 / 8>([&](auto c) {
+      constexpr int C = decltype(c)::value;
+      *reinterpret_cast<uint4*>(sm.a2 + kmajor_off(tid, 8 * C, K2)) =
+          make_uint4(hp[4 * C], hp[4 * C + 1], hp[4 * C + 2], hp[4 * C + 3]);
+    });
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0 && !tp.no_issue) {
+      tc::fence_after_sync();
+      static_for<K2 / 16>([&](auto kk) {
+        constexpr int KK = decltype(kk)::value;
+        tc::mma_f16(d2, tc::smem_desc(a2_s + KK * 256, 128, K2 * 16), tc::smem_desc(b2_s + KK * 256, 128, K2 * 16),
+                    idesc2, KK > 0 ? 1u : 0u);
+      });
+      tc::commit(&sm.mbar);
+    }
+    ok = tc::mbar_wait_bounded(&sm.mbar, phase, tp.wait_limit);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+
+    // f*_i = (1 - s_h) d_i + w_i Delta_i / sc, stored at the cell itself
+    const float inv = 1.f / sc;
+    static_for<QP / 16>([&](auto c) {
+      constexpr int C = decltype(c)::value;
+      float v[16];
+      tc::ld16(d2 + row_lane + 16 * C, v);
+      tc::wait_ld();
+      static_for<16>([&](auto j) {
+        constexpr int I = 16 * C + decltype(j)::value;
+        if constexpr (I < Q) {
+          if (live) {
+            const uint16_t b = uint16_t((I & 1) ? (dp[I / 2] >> 16) : (dp[I / 2] & 0xFFFFu));
+            const float d = RawCodec<ST>::dec(from_bits16<ST>(b));
+            const float fs = fmaf(p.one_minus_sh, d, p.w[I] * (v[decltype(j)::value] * inv));
+            k1_store(fout + size_t(I) * N + cell, RawCodec<ST>::enc(fs));
+          }
+        }
+      });
+    });
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  if (failed && tid == 0) atomicExch(tp.status, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid < 32) tc::dealloc(tmem, kTcCols);
+}
+
+}  // namespace lbm

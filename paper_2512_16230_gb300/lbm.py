@@ -31,6 +31,7 @@ HEADER = os.path.join(_build.ROOT, "include", "lbm_mrt.h")
 _P = c_void_p
 _PD = POINTER(c_double)
 _PI64 = POINTER(c_int64)
+NCDE_VARIANTS = {"moment": 0, "rate": 1, "cde": 2}
 SIGNATURES = {
     "lbm_abi_version": (c_int, []),
     "lbm_last_error": (c_char_p, []),
@@ -47,6 +48,7 @@ SIGNATURES = {
     "lbm_model_set_high_rates": (c_int, [_P, _PD, c_int]),
     "lbm_model_set_force": (c_int, [_P, c_int, c_int, c_double, c_int, c_double]),
     "lbm_model_set_ncde": (c_int, [_P, _PD, c_double]),
+    "lbm_model_set_ncde_variant": (c_int, [_P, c_int, c_double]),
     "lbm_model_init_fields": (c_int, [_P, _P, _P, c_int]),
     "lbm_model_set_populations": (c_int, [_P, _P, c_int]),
     "lbm_model_get_populations": (c_int, [_P, _P, c_int]),
@@ -261,7 +263,14 @@ class Model:
     def set_ncde(self, u_const, nonlin=0.0):
         _check(load().lbm_model_set_ncde(self.handle, _dbuf(u_const, 3), float(nonlin)), "lbm_model_set_ncde")
 
+    def set_ncde_variant(self, variant="moment", a1=0.0):
+        """App. A variants: "moment" (default), "rate" (per-cell S1(phi)) or "cde" (diffusion-based
+        CDE); a1 is the mixed-derivative coefficient of Eq. (GNCDE)."""
+        _check(load().lbm_model_set_ncde_variant(self.handle, NCDE_VARIANTS[variant], float(a1)),
+               "lbm_model_set_ncde_variant")
+
     # -- state ---------------------------------------------------------------------------------
+
     def init_fields(self, rho_or_phi, u=None):
         p0, dev0, k0 = _ptr(rho_or_phi)
         p1, dev1, k1 = _ptr(u)

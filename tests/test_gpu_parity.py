@@ -264,13 +264,12 @@ def test_bulk_viscosity_step(name, store):
     assert rel_l2(gm.get_populations(), om.f) <= TOL[store]
 
 
-def _order_projectors(H, N, orders, w):
-    """W H_k^T N_k^-1 H_k for every order k of the given rows."""
+def _order_projectors(H, orders, w):
+    """W H_k^T (H_k W H_k^T)^-1 H_k for every order k of the given rows (any basis of a block)."""
     out = {}
     for k in sorted(set(orders)):
-        sel = [r for r, o in enumerate(orders) if o == k]
-        Hk = H[sel]
-        out[k] = (w[:, None] * Hk.T) @ np.diag(1.0 / N[sel]) @ Hk
+        Hk = H[[r for r, o in enumerate(orders) if o == k]]
+        out[k] = (w[:, None] * Hk.T) @ np.linalg.solve((Hk * w) @ Hk.T, Hk)
     return out
 
 
@@ -286,14 +285,18 @@ def test_high_rows_match_oracle_blocks(name):
     R = olat.R
     assert len(hi["orders"]) == olat.Q - R
     assert sorted(hi["orders"]) == sorted(olat.full_orders[R:])
-    N_o = np.einsum("ri,i,ri->r", olat.Hfull[R:], olat.w, olat.Hfull[R:])
-    Pg = _order_projectors(hi["H"], hi["N"], list(hi["orders"]), glat.tables["w"])
-    Po = _order_projectors(olat.Hfull[R:], N_o, olat.full_orders[R:], olat.w)
+    assert np.allclose(hi["N"], np.einsum("ri,i,ri->r", hi["H"], glat.tables["w"], hi["H"]), rtol=1e-12, atol=0)
+    Pg = _order_projectors(hi["H"], list(hi["orders"]), glat.tables["w"])
+    Po = _order_projectors(olat.Hfull[R:], olat.full_orders[R:], olat.w)
     for k in Po:
         assert np.abs(Pg[k] - Po[k]).max() < 1e-10, k
-    # W-orthogonal to the rows of order <= 3
-    G = (hi["H"] * glat.tables["w"]) @ glat.tables["H"].T
+    # W-orthogonal to the rows of order <= 3 and to each other (the kernel divides by N_r row by row)
+    w = glat.tables["w"]
+    G = (hi["H"] * w) @ glat.tables["H"].T
     assert np.abs(G).max() < 1e-12 * np.sqrt(np.abs(hi["N"])).max() * np.sqrt(glat.tables["N"]).max()
+    Gh = (hi["H"] * w) @ hi["H"].T
+    sc = np.sqrt(np.abs(np.diag(Gh)))
+    assert np.abs(Gh / np.outer(sc, sc) - np.eye(len(sc))).max() < 1e-12
 
 
 def test_high_rows_need_nonzero_weights():
@@ -348,3 +351,70 @@ def test_high_order_rates_flow(store):
     gm.step(wl.steps)
     eu = rel_l2(gm.read_fields()[1], om.fields()[1])
     assert eu <= (1e-5 if store == "f32" else 1e-3)
+
+
+NCDE_VARIANTS = [("moment", 0.7), ("rate", 0.0), ("rate", -0.5), ("cde", 0.0)]
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("variant,a1", NCDE_VARIANTS)
+@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q25", "rD3Q33", "rD3Q53"])
+def test_ncde_variant_steps(name, variant, a1, store):
+    """App. A variants against the oracle from far-from-equilibrium populations over three steps
+    (so that phi^{n-1} enters): the mixed-derivative term a1 of Eq. (GNCDE), the per-cell rates
+    s1(phi) and the diffusion-based CDE with its local-gradient source S_G."""
+    spec = ALL_SPECS[name]
+    d = spec.d
+    n = RAGGED[d]
+    s = _random_rates(spec.R, 13)
+    kw = dict(s_high=1.2, u_const=tuple(np.linspace(0.04, 0.08, d)), nonlin=0.0 if variant == "cde" else 1.0,
+              ncde_mode=variant, a1=a1)
+    om = oracle_model(spec, "ncde", n, s, **kw)
+    gm = gpu_model(spec, "ncde", n, s, store=store, **kw)
+    f0 = round_to_store(I.random_populations(n, om.lat.Q, seed=17), store)
+    om.set_populations(f0)
+    gm.set_populations(f0)
+    for _ in range(3):
+        om.step(1)
+        gm.step(1)
+        assert rel_l2(gm.get_populations(), om.f) <= TOL[store]
+    phi_g, _ = gm.read_fields()
+    phi_o, _ = om.fields()
+    assert rel_l2(phi_g, phi_o) <= TOL[store]
+
+
+@pytest.mark.parametrize("variant", ["rate", "cde"])
+def test_ncde_variant_hill_flow(variant):
+    """A Gaussian hill (config 2 in miniature, 96 x 80 rD2Q13, FP32) over 300 steps in the rate and
+    CDE variants: phi against the FP64 oracle."""
+    spec = W.LATTICES["rD2Q13"]
+    n = (96, 80)
+    s = np.ones(spec.R)
+    s[1:3] = 1.6
+    kw = dict(u_const=(0.02, 0.01), nonlin=0.0 if variant == "cde" else 1.0, ncde_mode=variant)
+    om = oracle_model(spec, "ncde", n, s, **kw)
+    gm = gpu_model(spec, "ncde", n, s, store="f32", **kw)
+    phi0 = I.gaussian_hill(n, spec.c, 20.0, 1.0, noise=1e-3, seed=0)
+    om.init_fields(phi0)
+    gm.init_fields(phi0)
+    om.step(300)
+    gm.step(300)
+    assert rel_l2(gm.read_fields()[0], om.fields()[0]) <= 1e-5
+
+
+def test_ncde_variant_errors():
+    from paper_2512_16230_gb300 import lbm
+    spec = W.LATTICES["rD2Q13"]
+    nse = gpu_model(spec, "nse", (8, 8), np.ones(spec.R), store="f32")
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        nse.set_ncde_variant("rate")
+    m = gpu_model(spec, "ncde", (8, 8), np.ones(spec.R), store="f32", u_const=(0.01, 0.0))
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        m.set_ncde_variant("cde", 0.5)
+    b = lbm.Batch(4)
+    b.add(m)
+    with pytest.raises(lbm.LBMError, match="NOT_IMPLEMENTED"):
+        m.set_ncde_variant("rate")
+    m.set_ncde_variant("moment", 0.3)     # the moment variant (with a1) stays batchable
+    b.remove(m)
+    b.close()

@@ -328,7 +328,7 @@ def test_m1g_pin_catches_dropped_term():
     assert abs(got - (0.02 - (1 / s1 - 0.5) * 0.1 ** 2)) < 2e-6
 
 
-def _hill_error(r):
+def _hill_error(r, mode="moment"):
     c, cs2, _ = LATS["rD2Q13"]
     lat = L.build("rD2Q13", c, cs2)
     K = 0.05
@@ -337,7 +337,7 @@ def _hill_error(r):
     n = (64 * r, 52 * r)
     u = np.array([0.15, 0.1]) / r
     sig, steps = 6.0 * r, 150 * r * r
-    m = M.Model(lat, "ncde", n, s, 1.0, u_const=u, nonlin=0.0)
+    m = M.Model(lat, "ncde", n, s, 1.0, u_const=u, nonlin=0.0, ncde_mode=mode)
     m.init_fields(I.gaussian_hill(n, c, sig, 1.0))
     m.step(steps)
     phi, _ = m.fields()
@@ -357,6 +357,31 @@ def test_gaussian_hill_linear_ncde_second_order():
     e1, e2 = _hill_error(1), _hill_error(2)
     assert e1 < 1e-2
     assert 3.5 < e1 / e2 < 4.5
+
+
+def test_gaussian_hill_diffusion_based_cde_second_order():
+    """App. A special case (3): the diffusion-based CDE (M1 = 0, M2 = cs2 phi I, lambda = 1,
+    S_G = -u . grad phi from the local gradient of Eq. (M-NCDE-3-00a)) recovers
+    d_t phi + u . grad phi = K lap phi: the same advected Gaussian as the NCDE, second order."""
+    e1, e2 = _hill_error(1, "cde"), _hill_error(2, "cde")
+    assert e1 < 1e-2
+    assert 3.5 < e1 / e2 < 4.5
+
+
+def test_cde_pin_catches_wrong_source_moment(monkeypatch):
+    """Planted mistake on the oracle: M0G = S_G instead of (1 - s0/2) S_G (Eq. (M-NCDE-4) with
+    lambda = 1) spoils the advection of the hill far beyond the scheme's own error."""
+    good = _hill_error(1, "cde")
+    base = M.Model.source_moments
+
+    def wrong(self, fields):
+        mF, mG = base(self, fields)
+        if self.ncde_mode == "cde":
+            mG[0] = mG[0] / (1.0 - 0.5 * self.s[0])
+        return mF, mG
+
+    monkeypatch.setattr(M.Model, "source_moments", wrong)
+    assert _hill_error(1, "cde") > 5 * good
 
 
 def test_ncde_nonlinear_conserves_phi():
@@ -403,14 +428,14 @@ def test_taylor_green_3d_decay_rd3q53():
     assert e16 / e32 > 3.5
 
 
-def _sine_decay_rate(nonlin, background):
+def _sine_decay_rate(nonlin, background, mode="moment"):
     c, cs2, _ = LATS["rD2Q13"]
     lat = L.build("rD2Q13", c, cs2)
     K = 0.05
     s = np.ones(lat.R)
     s[1:3] = 1.0 / (K / cs2[0] + 0.5)
     n = (32, 3)
-    m = M.Model(lat, "ncde", n, s, 1.0, u_const=np.zeros(2), nonlin=nonlin)
+    m = M.Model(lat, "ncde", n, s, 1.0, u_const=np.zeros(2), nonlin=nonlin, ncde_mode=mode)
     x = I.coords(n, c)[0]
     k = 2 * math.pi / (n[0] * c[0])
     m.init_fields(background + 1e-4 * np.sin(k * x))
@@ -431,6 +456,57 @@ def test_ncde_nonlinear_diffusivity(background):
     (1 + phi0^2) times its rate in the linear model."""
     ratio = _sine_decay_rate(1.0, background) / _sine_decay_rate(0.0, background)
     assert abs(ratio / (1 + background ** 2) - 1) < 2e-3
+
+
+@pytest.mark.parametrize("background", [0.5, 1.0])
+def test_ncde_rate_reading_diffusivity(background):
+    """The other reading of the nonlinear diffusion: D(phi) = phi in M2 and a per-cell rate
+    s1(phi) with K(phi) = K0 (1 + phi^2) = cs2 (1/s1(phi) - 1/2). A small perturbation of phi0
+    again diffuses with K0 (1 + phi0^2)."""
+    ratio = _sine_decay_rate(1.0, background, "rate") / _sine_decay_rate(0.0, background, "rate")
+    assert abs(ratio / (1 + background ** 2) - 1) < 2e-3
+
+
+def _mixed_mode_omega(a1, nx=64):
+    """Complex frequency of a sine mode phi = 1 + eps exp(i k x) advected along x."""
+    c, cs2, _ = LATS["rD2Q13"]
+    lat = L.build("rD2Q13", c, cs2)
+    K = 0.05
+    s = np.ones(lat.R)
+    s[1:3] = 1.0 / (K / cs2[0] + 0.5)
+    n = (nx, 3)
+    u = np.array([0.2, 0.0])
+    m = M.Model(lat, "ncde", n, s, 1.0, u_const=u, a1=a1)
+    x = I.coords(n, c)[0]
+    k = 2 * math.pi / (n[0] * c[0])
+    m.init_fields(1.0 + 1e-4 * np.cos(k * x))
+
+    def amp():
+        return np.sum((m.fields()[0] - 1.0) * np.exp(-1j * k * x))
+
+    m.step(40)
+    a0 = amp()
+    logr = 0.0
+    for _ in range(20):          # phase advances < pi per chunk: unwrapped sum of the angles
+        m.step(10)
+        a1_ = amp()
+        logr += np.log(a1_ / a0)
+        a0 = a1_
+    got = 1j * logr / 200.0
+    A, B, C = K * k * k, k * u[0], a1 * k * u[0]
+    want = ((A * C + B) + 1j * (B * C - A)) / (1 + C * C)
+    return got, want
+
+
+@pytest.mark.parametrize("a1", [0.0, -1.0])
+def test_mixed_derivative_term(a1):
+    """Eq. (GNCDE) with A1 = a1 I and B-bar = u phi, so that M1G gains -S1 A1 d_t(u phi): the PDE
+    d_t phi + u . grad phi = K lap phi + a1 u . grad d_t phi (K1 = dt A1, the derivation's
+    coefficient) has omega = (K k^2 + i k u) / (i + a1 k u) for exp(i(k x - omega t)); the LB
+    decay rate and phase speed match it (a1 = -1 nearly doubles the damping)."""
+    got, want = _mixed_mode_omega(a1)
+    assert abs(got.imag / want.imag - 1) < 5e-3
+    assert abs(got.real / want.real - 1) < 2e-3
 
 
 def _sound_damping(s_bulk, axis, nu=0.05):
@@ -520,3 +596,33 @@ def test_distinct_high_order_rates(kind):
     assert np.abs(diff - want).max() < 1e-12 * np.abs(f).max()
     assert np.abs(diff.sum(0)).max() < 1e-15
     assert np.abs(lat.cvel.T @ diff).max() < 1e-15
+
+
+def _sound_period(cs2_eq, axis):
+    """Half periods of a standing sound wave on rD2Q25 (dy/dx = 4/3), from the zero crossings of
+    its density mode."""
+    c, cs2, fw = LATS["rD2Q25"]
+    lat = L.build("rD2Q25", c, cs2, fw)
+    s = np.full(lat.R, 1.0 / (0.02 / cs2_eq + 0.5))
+    n = (48, 4) if axis == 0 else (4, 36)
+    m = M.Model(lat, "nse", n, s, 1.0, cs2_eq=cs2_eq)
+    xs = I.coords(n, c)
+    k = 2 * math.pi / (n[axis] * c[axis])
+    mode = np.cos(k * xs[axis])
+    m.init_fields(1.0 + 1e-4 * mode, np.zeros((2,) + xs[0].shape))
+    a = []
+    for _ in range(260):
+        a.append(float(np.sum((m.fields()[0] - 1.0) * mode)))
+        m.step(1)
+    a = np.array(a)
+    t = [i + a[i] / (a[i] - a[i + 1]) for i in range(len(a) - 1) if a[i] * a[i + 1] < 0]
+    return np.diff(t).mean(), math.pi / (k * math.sqrt(cs2_eq))
+
+
+@pytest.mark.parametrize("cs2_eq", [0.8, 0.6])
+def test_equation_of_state_sets_sound_speed(cs2_eq):
+    """p = rho cs2_eq (Eq. (M-NSEs-6-1) with a pressure other than the lattice's c_s^2, p = rho R T):
+    a standing sound wave oscillates at k sqrt(cs2_eq) along both axes of the rectangular lattice."""
+    for axis in (0, 1):
+        half, want = _sound_period(cs2_eq, axis)
+        assert abs(half / want - 1) < 1e-2
