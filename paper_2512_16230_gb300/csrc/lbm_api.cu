@@ -186,14 +186,17 @@ void make_tc_params(const lbm_model* m, TcParams* tp) {
   tp->wait_limit = m->tc_no_issue ? (1u << 10) : (1u << 22);
 }
 
-// Persistent grid of the tensor-core kernel: resident CTAs per SM (at most 4, so that their
-// 128 TMEM columns each fit the SM's 512) times the SM count, capped by the tile count.
+// Persistent grid of the tensor-core kernel: four CTAs per SM (their 128 TMEM columns each fill
+// the SM's 512; __launch_bounds__ caps the registers at 128 and the operand tiles take 46 KB of
+// shared memory, so four are resident) times the SM count, capped by the tile count.
 int tc_grid(const lbm_model* m, int ntiles, const void* kernel) {
-  int sms = 0, per_sm = 0;
+  int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
-  per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
-  const int g = (sms > 0 ? sms : 1) * per_sm;
+  // the largest shared-memory carveout, so that four CTAs' operand tiles fit one SM
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           int(cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+    cudaGetLastError();
+  const int g = (sms > 0 ? sms : 1) * 4;
   return ntiles < g ? ntiles : g;
 }
 

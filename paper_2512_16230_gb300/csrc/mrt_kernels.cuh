@@ -295,53 +295,132 @@ __device__ __forceinline__ CT row_update(const P& p, const CT (&meq)[L::R], cons
   return g * p.invN[r];
 }
 
-// Rows of order >= 4 with their own rates: z_r = a_r sum_j h_r(c_j) f_j, a_r = -(s_r - s_h) / N_r.
-// Pairs outermost, so each +-e pair is summed once and feeds every row: even rows take
-// f_+ + f_-, odd rows f_+ - f_- (h_r(-c) = +-h_r(c)). For deviation storage the reference state
-// drops out (every such row is W-orthogonal to H_0).
+// Coefficients of the rows of order >= 4 staged in shared memory, row-major (the values of one
+// row at the rest velocity, c = 0, and at the + member of each +-e pair, c = P + 1, adjacent, so
+// that one vector load serves four pairs), with a per-thread slot for each row's z_r. The row
+// loops run at run time (rows outermost, pairs unrolled), which keeps the register footprint at
+// the populations plus one accumulator per pair.
 template <class L, class CT>
-__device__ __forceinline__ void high_moments(const CT (&f)[L::Q], const HighParams<CT>& hp,
-                                             CT (&ze)[high_even<L>()], CT (&zo)[high_odd<L>() > 0 ? high_odd<L>() : 1]) {
-  constexpr int HE = high_even<L>(), HO = high_odd<L>();
-  static_for<HE>([&](auto r) { ze[decltype(r)::value] = hp.he[decltype(r)::value][0] * f[0]; });
-  static_for<HO>([&](auto r) { zo[decltype(r)::value] = CT(0); });
-  static_for<num_pairs<L>()>([&](auto q) {
+struct HighTable {
+  static constexpr int HE = high_even<L>(), HO = high_odd<L>();
+  static constexpr int NP = num_pairs<L>();
+  static constexpr int CE = (NP + 1 + 3) / 4 * 4, CO = (NP + 3) / 4 * 4;  // padded row lengths
+  alignas(16) CT he[HE * CE];
+  alignas(16) CT ho[(HO > 0 ? HO : 1) * CO];
+  CT ae[HE];
+  CT ao[HO > 0 ? HO : 1];
+  CT z[(HE + HO) * kBlock];  // z_r of thread t at z[r * kBlock + t]
+  // block-wide copy from the kernel parameters (call before any thread returns)
+  __device__ __forceinline__ void fill(const HighParams<CT>& hp) {
+    for (int idx = threadIdx.x; idx < HE * (NP + 1); idx += blockDim.x)
+      he[(idx / (NP + 1)) * CE + idx % (NP + 1)] = hp.he[idx / (NP + 1)][idx % (NP + 1)];
+    for (int idx = threadIdx.x; idx < HO * NP; idx += blockDim.x) ho[(idx / NP) * CO + idx % NP] = hp.ho[idx / NP][idx % NP];
+    for (int idx = threadIdx.x; idx < HE; idx += blockDim.x) ae[idx] = hp.ae[idx];
+    for (int idx = threadIdx.x; idx < HO; idx += blockDim.x) ao[idx] = hp.ao[idx];
+  }
+};
+
+// Four consecutive coefficients of a 16-byte-aligned shared-memory row.
+template <class CT>
+__device__ __forceinline__ void load4(const CT* p, CT (&v)[4]) {
+  if constexpr (std::is_same<CT, float>::value) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+}
+
+// Rows of order >= 4 with their own rates: z_r = a_r sum_j h_r(c_j) f_j, a_r = -(s_r - s_h) / N_r,
+// kept in the table's per-thread slots. Even rows take f_+ + f_- of each +-e pair, odd rows
+// f_+ - f_- (h_r(-c) = +-h_r(c)). For deviation storage the reference state drops out (every
+// such row is W-orthogonal to H_0).
+template <class L, class CT>
+__device__ __forceinline__ void high_moments(const CT (&f)[L::Q], HighTable<L, CT>& tb) {
+  using T = HighTable<L, CT>;
+  constexpr int NP = T::NP;
+  CT sp[NP], sm[NP];
+  static_for<NP>([&](auto q) {
     constexpr int P = decltype(q)::value;
     constexpr int ip = pair_plus<L>(P);
     constexpr int im = opposite<L>(ip);
-    const CT sp = f[ip] + f[im];
-    const CT sm = f[ip] - f[im];
-    static_for<HE>([&](auto r) {
-      constexpr int Rr = decltype(r)::value;
-      ze[Rr] = fma(hp.he[Rr][P + 1], sp, ze[Rr]);
-    });
-    static_for<HO>([&](auto r) {
-      constexpr int Rr = decltype(r)::value;
-      zo[Rr] = fma(hp.ho[Rr][P], sm, zo[Rr]);
-    });
+    sp[P] = f[ip] + f[im];
+    sm[P] = f[ip] - f[im];
   });
-  static_for<HE>([&](auto r) { ze[decltype(r)::value] *= hp.ae[decltype(r)::value]; });
-  static_for<HO>([&](auto r) { zo[decltype(r)::value] *= hp.ao[decltype(r)::value]; });
+#pragma unroll 1
+  for (int r = 0; r < T::HE; ++r) {
+    const CT* h = tb.he + r * T::CE;
+    CT acc = CT(0);
+    static_for<T::CE / 4>([&](auto g) {
+      CT v[4];
+      load4(h + 4 * decltype(g)::value, v);
+      static_for<4>([&](auto j) {
+        constexpr int C = 4 * decltype(g)::value + decltype(j)::value;  // c = 0: rest, c = P + 1: pair P
+        if constexpr (C == 0) acc = fma(v[decltype(j)::value], f[0], acc);
+        else if constexpr (C <= NP) acc = fma(v[decltype(j)::value], sp[C - 1], acc);
+      });
+    });
+    tb.z[r * kBlock + threadIdx.x] = acc * tb.ae[r];
+  }
+#pragma unroll 1
+  for (int r = 0; r < T::HO; ++r) {
+    const CT* h = tb.ho + r * T::CO;
+    CT acc = CT(0);
+    static_for<T::CO / 4>([&](auto g) {
+      CT v[4];
+      load4(h + 4 * decltype(g)::value, v);
+      static_for<4>([&](auto j) {
+        constexpr int C = 4 * decltype(g)::value + decltype(j)::value;
+        if constexpr (C < NP) acc = fma(v[decltype(j)::value], sm[C], acc);
+      });
+    });
+    tb.z[(T::HE + r) * kBlock + threadIdx.x] = acc * tb.ao[r];
+  }
 }
 
 // f_i += w_i sum_r h_r(c_i) z_r over the rows of order >= 4 (the weights of a +-e pair are equal).
 template <class L, class CT, class P>
-__device__ __forceinline__ void high_back(CT (&f)[L::Q], const P& p, const HighParams<CT>& hp,
-                                          const CT (&ze)[high_even<L>()],
-                                          const CT (&zo)[high_odd<L>() > 0 ? high_odd<L>() : 1]) {
-  constexpr int HE = high_even<L>(), HO = high_odd<L>();
-  CT e0 = CT(0);
-  static_for<HE>([&](auto r) { e0 = fma(hp.he[decltype(r)::value][0], ze[decltype(r)::value], e0); });
-  f[0] = fma(p.w[0], e0, f[0]);
-  static_for<num_pairs<L>()>([&](auto q) {
+__device__ __forceinline__ void high_back(CT (&f)[L::Q], const P& p, const HighTable<L, CT>& tb) {
+  using T = HighTable<L, CT>;
+  constexpr int NP = T::NP;
+  CT ev[NP + 1], od[NP];
+  static_for<NP + 1>([&](auto q) { ev[decltype(q)::value] = CT(0); });
+  static_for<NP>([&](auto q) { od[decltype(q)::value] = CT(0); });
+#pragma unroll 1
+  for (int r = 0; r < T::HE; ++r) {
+    const CT* h = tb.he + r * T::CE;
+    const CT zr = tb.z[r * kBlock + threadIdx.x];
+    static_for<T::CE / 4>([&](auto g) {
+      CT v[4];
+      load4(h + 4 * decltype(g)::value, v);
+      static_for<4>([&](auto j) {
+        constexpr int C = 4 * decltype(g)::value + decltype(j)::value;
+        if constexpr (C <= NP) ev[C] = fma(v[decltype(j)::value], zr, ev[C]);
+      });
+    });
+  }
+#pragma unroll 1
+  for (int r = 0; r < T::HO; ++r) {
+    const CT* h = tb.ho + r * T::CO;
+    const CT zr = tb.z[(T::HE + r) * kBlock + threadIdx.x];
+    static_for<T::CO / 4>([&](auto g) {
+      CT v[4];
+      load4(h + 4 * decltype(g)::value, v);
+      static_for<4>([&](auto j) {
+        constexpr int C = 4 * decltype(g)::value + decltype(j)::value;
+        if constexpr (C < NP) od[C] = fma(v[decltype(j)::value], zr, od[C]);
+      });
+    });
+  }
+  f[0] = fma(p.w[0], ev[0], f[0]);
+  static_for<NP>([&](auto q) {
     constexpr int Pq = decltype(q)::value;
     constexpr int ip = pair_plus<L>(Pq);
     constexpr int im = opposite<L>(ip);
-    CT ev = CT(0), od = CT(0);
-    static_for<HE>([&](auto r) { ev = fma(hp.he[decltype(r)::value][Pq + 1], ze[decltype(r)::value], ev); });
-    static_for<HO>([&](auto r) { od = fma(hp.ho[decltype(r)::value][Pq], zo[decltype(r)::value], od); });
-    f[ip] = fma(p.w[ip], ev + od, f[ip]);
-    f[im] = fma(p.w[im], ev - od, f[im]);
+    f[ip] = fma(p.w[ip], ev[Pq + 1] + od[Pq], f[ip]);
+    f[im] = fma(p.w[im], ev[Pq + 1] - od[Pq], f[im]);
   });
 }
 
@@ -350,7 +429,7 @@ __device__ __forceinline__ void high_back(CT (&f)[L::Q], const P& p, const HighP
 // DEV: f holds deviations f - w rho_ref (16-bit storage). The moments of the reference state are
 // added back (only 1 and the squares c_a^2 have non-zero lattice moments), and the update
 // f* - w rho_ref = (1 - s_h)(f - w rho_ref) + w H(h) - s_h w rho_ref folds the last term into h_0.
-// HP = HighParams<CT>: the rows of order >= 4 relax with the rates of hp (the full Q x Q
+// HP = HighTable<L, CT>: the rows of order >= 4 relax with the rates in hp (the full Q x Q
 // collision); HP = NoHigh: they share s_high (the reduced form alone).
 struct NoHigh {};
 
@@ -433,16 +512,15 @@ __device__ __forceinline__ void collide_moments(CT (&mu)[L::R], const P& p, cons
 
 template <class L, class CT, int EQ, bool DEV = false, class P, class HP = NoHigh>
 __device__ __forceinline__ void collide(CT (&f)[L::Q], const P& p, const CT (&F)[3],
-                                        CT phi_prev, CT& phi_now, const HP& hp = HP{}) {
+                                        CT phi_prev, CT& phi_now, HP* hp = nullptr) {
   constexpr bool HI = !std::is_same<HP, NoHigh>::value;
-  CT ze[high_even<L>()], zo[high_odd<L>() > 0 ? high_odd<L>() : 1];
-  if constexpr (HI) high_moments<L>(f, hp, ze, zo);
+  if constexpr (HI) high_moments<L>(f, *hp);
   CT mu[L::R];
   raw_moments<L>(f, mu);
   CT h[L::R];
   collide_moments<L, CT, EQ, DEV>(mu, p, F, phi_prev, phi_now, h);
   back_project<L>(f, p, h, p.one_minus_sh);
-  if constexpr (HI) high_back<L>(f, p, hp, ze, zo);
+  if constexpr (HI) high_back<L>(f, p, *hp);
 }
 
 // Equilibrium populations of given fields, Eq. (feq-1): f^eq_i = w_i sum_r H_ri m^eq_r / N_r.
@@ -567,12 +645,15 @@ __global__ void __launch_bounds__(kBlock, LBM_K1_MIN_BLOCKS) k_step(const StepPa
 
 // K1 with distinct rates for the orders >= 4: the same gather / collide / store plus the two
 // contractions with the higher rows (about 2 (Q - 1) (Q - R) / 2 more FMAs per cell, so the
-// kernel is bound by the FMA pipe rather than HBM; fewer resident blocks leave it the registers).
+// kernel is bound by instruction issue rather than HBM; 3 resident blocks leave it 168 registers).
 template <class L, class CT, class ST, int EQ>
-__global__ void __launch_bounds__(kBlock, 2) k_step_high(const StepParams<CT> p,
+__global__ void __launch_bounds__(kBlock, 3) k_step_high(const StepParams<CT> p,
                                                           const HighParams<CT> hp,
                                                           const ST* __restrict__ fin,
                                                           ST* __restrict__ fout, CT* __restrict__ phi) {
+  __shared__ HighTable<L, CT> tab;
+  tab.fill(hp);
+  __syncthreads();
   const int cell = blockIdx.x * kBlock + threadIdx.x;
   if (cell >= p.ncells) return;
   const Neigh<L> nb(cell, p);
@@ -588,7 +669,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_step_high(const StepParams<CT> p,
   body_force(p.force_a, p.force_b, p.force_tab, nb.x, nb.y, nb.z, F);
   CT phi_prev = CT(0), phi_now = CT(0);
   if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
-  collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, hp);
+  collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, &tab);
   if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
   static_for<L::Q>([&](auto i) {
     constexpr int I = decltype(i)::value;

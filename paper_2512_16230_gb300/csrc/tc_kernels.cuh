@@ -109,27 +109,32 @@ __global__ void __launch_bounds__(128, 4) k_step_tc(const StepParams<float> p, c
   uint32_t phase = 0;
   bool failed = false;
 
-  for (int tile = blockIdx.x; tile < tp.ntiles; tile += gridDim.x) {
+  // Software pipeline: the gather loads of the next tile are issued before this tile's collision
+  // and consumed only when that tile is written to shared memory, so their latency overlaps the
+  // matrix products and the moment-space arithmetic.
+  auto gather = [&](int tile, uint16_t (&raw)[Q]) {
     const int cell = tile * 128 + tid;
-    const bool live = cell < p.ncells;
-    uint32_t dp[QP / 2];  // raw 16-bit deviations, two per register
-    static_for<QP / 2>([&](auto j) { dp[decltype(j)::value] = 0u; });
-    int x = 0, y = 0, z = 0;
-    if (live) {
+    if (tile < tp.ntiles && cell < p.ncells) {
       const Neigh<L> nb(cell, p);
-      x = nb.x;
-      y = nb.y;
-      z = nb.z;
       static_for<Q>([&](auto i) {
         constexpr int I = decltype(i)::value;
-        const uint32_t b = bits16(k1_load(fin + size_t(I) * N + nb.template src<I>()));
-        dp[I / 2] |= (I & 1) ? (b << 16) : b;
+        raw[I] = bits16(k1_load(fin + size_t(I) * N + nb.template src<I>()));
       });
+    } else {
+      static_for<Q>([&](auto i) { raw[decltype(i)::value] = 0; });
     }
+  };
+  auto stage = [&](const uint16_t (&raw)[Q]) {  // row tid of A, then the forward product
     static_for<QP / 8>([&](auto c) {
       constexpr int C = decltype(c)::value;
-      *reinterpret_cast<uint4*>(sm.a + kmajor_off(tid, 8 * C, QP)) =
-          make_uint4(dp[4 * C], dp[4 * C + 1], dp[4 * C + 2], dp[4 * C + 3]);
+      uint32_t w4[4];
+      static_for<4>([&](auto j) {
+        constexpr int I0 = 8 * C + 2 * decltype(j)::value;
+        const uint32_t lo = I0 < Q ? uint32_t(raw[I0 < Q ? I0 : 0]) : 0u;
+        const uint32_t hi = I0 + 1 < Q ? uint32_t(raw[I0 + 1 < Q ? I0 + 1 : 0]) : 0u;
+        w4[decltype(j)::value] = lo | (hi << 16);
+      });
+      *reinterpret_cast<uint4*>(sm.a + kmajor_off(tid, 8 * C, QP)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
     });
     tc::fence_async_smem();
     __syncthreads();
@@ -142,6 +147,18 @@ __global__ void __launch_bounds__(128, 4) k_step_tc(const StepParams<float> p, c
       });
       tc::commit(&sm.mbar);
     }
+  };
+  if (int(blockIdx.x) < tp.ntiles) {
+    uint16_t raw[Q];
+    gather(blockIdx.x, raw);
+    stage(raw);
+  }
+  for (int tile = blockIdx.x; tile < tp.ntiles; tile += gridDim.x) {
+    const int cell = tile * 128 + tid;
+    const bool live = cell < p.ncells;
+    const int next = tile + int(gridDim.x);
+    uint16_t nraw[Q];
+    gather(next, nraw);
     bool ok = tc::mbar_wait_bounded(&sm.mbar, phase, tp.wait_limit);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
@@ -162,6 +179,13 @@ __global__ void __launch_bounds__(128, 4) k_step_tc(const StepParams<float> p, c
         if constexpr (K < R) mu[K] = v[decltype(j)::value];
       });
     });
+    int x = 0, y = 0, z = 0;
+    if (live) {
+      const Neigh<L> nb(cell, p);
+      x = nb.x;
+      y = nb.y;
+      z = nb.z;
+    }
     float F[3] = {0.f, 0.f, 0.f};
     body_force(p.force_a, p.force_b, p.force_tab, x, y, z, F);
     float phi_prev = 0.f, phi_now = 0.f;
@@ -212,20 +236,24 @@ __global__ void __launch_bounds__(128, 4) k_step_tc(const StepParams<float> p, c
     }
     tc::fence_after_sync();
 
-    // f*_i = (1 - s_h) d_i + w_i Delta_i / sc, stored at the cell itself
+    // f*_i = (1 - s_h) d_i + w_i Delta_i / sc, stored at the cell itself; d_i from row tid of A
     const float inv = 1.f / sc;
     static_for<QP / 16>([&](auto c) {
       constexpr int C = decltype(c)::value;
       float v[16];
       tc::ld16(d2 + row_lane + 16 * C, v);
+      const uint4 q0 = *reinterpret_cast<const uint4*>(sm.a + kmajor_off(tid, 16 * C, QP));
+      const uint4 q1 = *reinterpret_cast<const uint4*>(sm.a + kmajor_off(tid, 16 * C + 8, QP));
+      const uint32_t dw[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
       tc::wait_ld();
       static_for<16>([&](auto j) {
-        constexpr int I = 16 * C + decltype(j)::value;
+        constexpr int J = decltype(j)::value;
+        constexpr int I = 16 * C + J;
         if constexpr (I < Q) {
           if (live) {
-            const uint16_t b = uint16_t((I & 1) ? (dp[I / 2] >> 16) : (dp[I / 2] & 0xFFFFu));
+            const uint16_t b = uint16_t((J & 1) ? (dw[J / 2] >> 16) : (dw[J / 2] & 0xFFFFu));
             const float d = RawCodec<ST>::dec(from_bits16<ST>(b));
-            const float fs = fmaf(p.one_minus_sh, d, p.w[I] * (v[decltype(j)::value] * inv));
+            const float fs = fmaf(p.one_minus_sh, d, p.w[I] * (v[J] * inv));
             k1_store(fout + size_t(I) * N + cell, RawCodec<ST>::enc(fs));
           }
         }
@@ -233,6 +261,7 @@ __global__ void __launch_bounds__(128, 4) k_step_tc(const StepParams<float> p, c
     });
     tc::fence_before_sync();
     __syncthreads();
+    if (next < tp.ntiles) stage(nraw);
   }
   if (failed && tid == 0) atomicExch(tp.status, 1);
   tc::fence_before_sync();

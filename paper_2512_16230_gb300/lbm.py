@@ -25,7 +25,7 @@ DTYPES = {"f64": 0, "f32": 1, "bf16_dev": 2, "f16_dev": 3}
 COMPUTE_OF = {"f64": "f64", "f32": "f32", "bf16_dev": "f32", "f16_dev": "f32"}
 EQS = {"nse": 0, "ncde": 1}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_LATTICE_INFEASIBLE", 3: "LBM_ERR_OOM",
-          4: "LBM_ERR_CUDA", 5: "LBM_ERR_NONFINITE", 6: "LBM_ERR_NOT_IMPLEMENTED"}
+          4: "LBM_ERR_CUDA", 5: "LBM_ERR_NONFINITE", 6: "LBM_ERR_NOT_IMPLEMENTED", 7: "LBM_ERR_TIMEOUT"}
 HEADER = os.path.join(_build.ROOT, "include", "lbm_mrt.h")
 
 _P = c_void_p
@@ -49,6 +49,7 @@ SIGNATURES = {
     "lbm_model_set_force": (c_int, [_P, c_int, c_int, c_double, c_int, c_double]),
     "lbm_model_set_ncde": (c_int, [_P, _PD, c_double]),
     "lbm_model_set_ncde_variant": (c_int, [_P, c_int, c_double]),
+    "lbm_model_set_tensor_cores": (c_int, [_P, c_int]),
     "lbm_model_init_fields": (c_int, [_P, _P, _P, c_int]),
     "lbm_model_set_populations": (c_int, [_P, _P, c_int]),
     "lbm_model_get_populations": (c_int, [_P, _P, c_int]),
@@ -262,6 +263,11 @@ class Model:
 
     def set_ncde(self, u_const, nonlin=0.0):
         _check(load().lbm_model_set_ncde(self.handle, _dbuf(u_const, 3), float(nonlin)), "lbm_model_set_ncde")
+
+    def set_tensor_cores(self, enable=1):
+        """16-bit storage: run the collision's contractions on tcgen05 (0 = CUDA cores; 2 = the
+        test hook whose waits run out)."""
+        _check(load().lbm_model_set_tensor_cores(self.handle, int(enable)), "lbm_model_set_tensor_cores")
 
     def set_ncde_variant(self, variant="moment", a1=0.0):
         """App. A variants: "moment" (default), "rate" (per-cell S1(phi)) or "cde" (diffusion-based
