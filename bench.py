@@ -36,7 +36,6 @@ METRIC = "rD3Q53 MLUPS"
 UNIT = "MLUPS"
 GRID = (256, 256, 192)
 Q = 53
-STORE_BYTES = 4
 PROFILE = os.path.join(ROOT, "profiles", "k_step_rd3q53_f32_tgv3d_256x256x192.md")
 CPU_SAMPLE_GRID = (256, 256, 16)    # cpu_baseline: ~10-30 s of oracle work on the GPU machine
 CPU_SAMPLE_STEPS = 8
@@ -45,16 +44,21 @@ HIGH_RATES = {4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25}   # variant: one rate pe
 VARIANT_STEPS = 100
 
 
-def _workload(grid=GRID):
+STORE_DTYPE = {"f32": ("f32", 4, "FP32"), "f16_dev": ("f16", 2, "FP16 deviation storage"),
+               "bf16_dev": ("bf16", 2, "BF16 deviation storage")}
+
+
+def _workload(grid=GRID, store="f32"):
     from paper_2512_16230_gb300 import workloads as W
-    return W.taylor_green_3d(n=tuple(grid), steps=1000, store="f32")
+    return W.taylor_green_3d(n=tuple(grid), steps=1000, store=store)
 
 
-def _config(extra=None, grid=GRID):
+def _config(extra=None, grid=GRID, store="f32"):
     cfg = {
-        "workload": f"rD3Q53 Taylor-Green 3D, {grid[0]}x{grid[1]}x{grid[2]} cells (dz/dx=4/3), Ma 0.3, Re 1600, FP32",
+        "workload": f"rD3Q53 Taylor-Green 3D, {grid[0]}x{grid[1]}x{grid[2]} cells (dz/dx=4/3), Ma 0.3, Re 1600, "
+                    f"{STORE_DTYPE[store][2]}",
         "lattice": "rD3Q53", "cells": int(math.prod(grid)), "grid": list(grid), "Q": Q,
-        "store": "f32", "compute": "f32",
+        "store": store, "compute": "f32",
         "l2": "inputs larger than L2 (2 x 2.67 GB population arrays vs 129 MB L2), no flush",
         "parallelism": "replicas",
     }
@@ -301,13 +305,15 @@ def bench_ours(args):
     B.build()
     lbm.load()
     grid = tuple(args.grid)
-    wl = _workload(grid)
+    wl = _workload(grid, args.store)
     spec = wl.lattice
     cells = wl.ncells
     lat = lbm.Lattice(spec.kind, spec.c, spec.cs2, spec.free_w)
     stream = torch.cuda.current_stream(dev)
-    model = lbm.Model(lat, "nse", wl.n, store="f32", stream=stream.cuda_stream)
+    model = lbm.Model(lat, "nse", wl.n, store=args.store, stream=stream.cuda_stream)
     model.set_relaxation(wl.s, wl.s_high)
+    if args.tensor_cores:
+        model.set_tensor_cores(1)
     rho, u = wl.fields()
     rho_d = torch.from_numpy(rho).to(dev)
     u_d = torch.from_numpy(np.ascontiguousarray(u)).to(dev)
@@ -372,9 +378,11 @@ def bench_ours(args):
 
     if rank == 0:
         peak, peak_src = _peaks()
-        algo_bytes = 2 * Q * STORE_BYTES * cells
+        algo_bytes = 2 * Q * STORE_DTYPE[args.store][1] * cells
         achieved = algo_bytes / (launch_ms / 1e3) / 1e9
         traffic, sha = _profile_traffic(cells)
+        if args.store != "f32" or args.tensor_cores:
+            traffic = None
         cpu = run_cpu_baseline() if (ws == 1 and not args.no_cpu_baseline) else None
         if grid != GRID:
             traffic = None
@@ -382,10 +390,12 @@ def bench_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic (analytic Taylor-Green initial field)", "config": _config(grid=grid),
+            "dtype": STORE_DTYPE[args.store][0], "data": "synthetic (analytic Taylor-Green initial field)",
+            "config": _config(grid=grid, store=args.store),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                         "kernel": "k_step<rD3Q53, f32, NSE> (fused pull-gather, collide, store)",
+                         "kernel": ("k_step_tc<rD3Q53, " if args.tensor_cores else "k_step<rD3Q53, ")
+                                   + args.store + ", NSE> (fused pull-gather, collide, store)",
                          "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": launch_ms},
             "clocks": {k: csum[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes / args.steps,
@@ -452,6 +462,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=160,
                     help="requests of the seeded serving mix (config 5) served after the step benchmark; 0 skips")
+    ap.add_argument("--store", choices=sorted(STORE_DTYPE), default="f32",
+                    help="population storage (the benchmark is FP32; 16-bit deviations for the reduced-precision path)")
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="16-bit storage only: the collision's contractions on tcgen05 (k_step_tc)")
     ap.add_argument("--grid", type=int, nargs=3, default=list(GRID),
                     help="grid for a smaller profiling case (the benchmark workload is 256 256 192)")
     args = ap.parse_args(argv)
