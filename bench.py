@@ -416,6 +416,27 @@ def bench_ours(args):
     model.close()
     del model
     torch.cuda.empty_cache()
+    # the same variant with FP16-deviation storage, where its dense higher rows run on tcgen05
+    m16 = lbm.Model(lat, "nse", wl.n, store="f16_dev", stream=stream.cuda_stream)
+    m16.set_relaxation(wl.s, wl.s_high)
+    m16.set_high_rates([HIGH_RATES[k] for k in sorted(HIGH_RATES)])
+    m16.init_fields(rho_d, u_d)
+    m16.step(3)
+    barrier()
+    v0.record(stream)
+    m16.step(vsteps)
+    v1.record(stream)
+    barrier()
+    high16_ms = v0.elapsed_time(v1) / vsteps
+    m16.close()
+    del m16
+    torch.cuda.empty_cache()
+    if rank == 0:
+        line["variants"]["high_order_rates_f16_tensor_cores"] = {
+            "kernel": "k_step_tc<rD3Q53, f16_dev, NSE, higher rows> (tcgen05 products with the dense higher rows)",
+            "rates": {str(k): v for k, v in HIGH_RATES.items()}, "steps": vsteps,
+            "ms_per_step": high16_ms, "mlups": cells / high16_ms / 1e3,
+            "hbm_frac": 2 * Q * 2 * cells / (high16_ms / 1e3) / 1e9 / peak}
     if args.serving_requests > 0:
         serving = run_serving(args.serving_requests)
         if rank == 0:

@@ -186,6 +186,10 @@ lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_o
  * of the Hermite-moment collision (Eq. (H-MRT-LB-1)) run as tcgen05 matrix products over tiles
  * of 128 cells with the integer monomial table mono_k(e_i) as the other operand (exact in 16 bits);
  * the per-cell moment-space arithmetic stays in FP32. enable = 0 selects the CUDA-core kernel.
+ * With distinct rates for the orders >= 4 (lbm_model_set_high_rates) the higher rows join both
+ * products as dense 16-bit operands (the full Q x Q collision). Default, until this is called:
+ * the tensor cores for 16-bit storage with distinct higher-order rates (there they are the faster
+ * kernel), the CUDA cores otherwise.
  * Device-side waits are bounded; a timeout is latched in the model's status word and returned as
  * LBM_ERR_TIMEOUT by the next lbm_model_synchronize / read / get / sums call.
  * enable = 2 is a test hook for that path: the kernel issues no matrix product, every wait runs

@@ -180,23 +180,28 @@ void make_tc_params(const lbm_model* m, TcParams* tp) {
       for (int q = 0; q < mk.c; ++q) v *= L->e[i * 3 + 2];
       tp->mono[i][r] = int8_t(v);
     }
+  if (has_high_rates(m))
+    for (int r = 0; r < L->nhigh; ++r) {
+      for (int i = 0; i < L->Q; ++i) tp->hrow[r][i] = float(L->Hh[size_t(r) * L->Q + i]);
+      tp->ah[r] = float(-(high_rate(m, L->h_order[r]) - m->s_high) / L->Nh[r]);
+    }
   tp->ntiles = (m->ncells + 127) / 128;
   tp->status = m->status;
   tp->no_issue = m->tc_no_issue ? 1 : 0;
   tp->wait_limit = m->tc_no_issue ? (1u << 10) : (1u << 22);
 }
 
-// Persistent grid of the tensor-core kernel: four CTAs per SM (their 128 TMEM columns each fill
-// the SM's 512; __launch_bounds__ caps the registers at 128 and the operand tiles take 46 KB of
-// shared memory, so four are resident) times the SM count, capped by the tile count.
-int tc_grid(const lbm_model* m, int ntiles, const void* kernel) {
+// Persistent grid of the tensor-core kernel: ctas_per_sm CTAs per SM (their 128 TMEM columns
+// each fit the SM's 512; __launch_bounds__ caps the registers so that they are resident) times
+// the SM count, capped by the tile count. The operand tiles are dynamic shared memory.
+int tc_grid(const lbm_model* m, int ntiles, const void* kernel, int ctas_per_sm, size_t smem_bytes) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
-  // the largest shared-memory carveout, so that four CTAs' operand tiles fit one SM
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_bytes)) != cudaSuccess ||
+      cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                            int(cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
     cudaGetLastError();
-  const int g = (sms > 0 ? sms : 1) * 4;
+  const int g = (sms > 0 ? sms : 1) * ctas_per_sm;
   return ntiles < g ? ntiles : g;
 }
 
@@ -480,6 +485,7 @@ lbm_status lbm_model_create(const lbm_lattice* L, lbm_eq eq, const int64_t* n, l
     m->cs2_eq = L->cs2[0];
     m->rho_ref = eq == LBM_NSE ? 1.0 : 0.0;
     m->force_b = -1;
+    m->tc_auto = store == LBM_BF16_DEV || store == LBM_F16_DEV;
     *out = m;
     return LBM_OK;
   } catch (...) {
@@ -537,6 +543,7 @@ lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable) {
     return set_error(LBM_ERR_ARG, "the tensor-core collision needs 16-bit deviation storage");
   m->tensor_cores = enable != 0;
   m->tc_no_issue = enable == 2;
+  m->tc_auto = false;
   return LBM_OK;
 }
 

@@ -60,6 +60,7 @@ struct lbm_model {
   int ncde_variant;  // lbm_ncde_variant
   double a1;         // mixed-derivative coefficient A1 = a1 I (Eq. (GNCDE))
   bool tensor_cores; // 16-bit storage: contractions on tcgen05 (k_step_tc)
+  bool tc_auto;      // no explicit choice yet: tcgen05 for 16-bit storage with per-order rates
   bool tc_no_issue;  // test hook: k_step_tc issues no matrix product, so its waits run out
   int* status;       // device status word: non-zero after a device-side wait ran out
   int64_t steps, launches;
@@ -124,8 +125,11 @@ struct HighParams {
 
 // Tensor-core kernel parameters: the monomial table mono_k(e_i) (paper's row order) and the
 // tile count; status receives 1 if an mbarrier wait ran out.
+constexpr int kMaxHigh = kMaxQ - kMaxR;  // rows of order >= 4 (rD3Q53: 33)
 struct TcParams {
   int8_t mono[kMaxQ][kMaxR];
+  float hrow[kMaxHigh][kMaxQ];  // higher rows on the lattice (one rate per order >= 4)
+  float ah[kMaxHigh];           // -(s_r - s_high) / N_r
   int ntiles;
   int* status;
   unsigned wait_limit;  // mbarrier polls before a wait is declared lost
@@ -302,6 +306,6 @@ void make_high_params(const lbm_model* m, HighParams<CT>* hp);
 // true when some row of order >= 4 relaxes with a rate other than s_high
 bool has_high_rates(const lbm_model* m);
 void make_tc_params(const lbm_model* m, TcParams* tp);
-int tc_grid(const lbm_model* m, int ntiles, const void* kernel);
+int tc_grid(const lbm_model* m, int ntiles, const void* kernel, int ctas_per_sm, size_t smem_bytes);
 
 }  // namespace lbm

@@ -847,14 +847,32 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
   const bool high = collide_on && has_high_rates(m);
   HighParams<CT> hp;
   if (high) make_high_params<CT>(m, &hp);
-  [[maybe_unused]] const bool tensor = collide_on && !high && m->tensor_cores;
+  // tcgen05 when asked for, and by default for 16-bit storage with per-order rates (where the
+  // dense higher rows make it the faster kernel)
+  [[maybe_unused]] const bool tensor = collide_on && (m->tensor_cores || (m->tc_auto && high));
   TcParams tp;
   int tgrid = 0;
+  size_t tsmem = 0;
+  [[maybe_unused]] auto tc_kernel = [&](auto hi_tag, auto eq_tag) {
+    return k_step_tc<L, ST, decltype(eq_tag)::value, decltype(hi_tag)::value>;
+  };
   if constexpr (is_deviation_storage<ST>()) {
     if (tensor) {
       make_tc_params(m, &tp);
-      tgrid = m->eq == LBM_NSE ? tc_grid(m, tp.ntiles, reinterpret_cast<const void*>(k_step_tc<L, ST, LBM_NSE>))
-                               : tc_grid(m, tp.ntiles, reinterpret_cast<const void*>(k_step_tc<L, ST, LBM_NCDE>));
+      using NSE_ = std::integral_constant<int, LBM_NSE>;
+      using NCDE_ = std::integral_constant<int, LBM_NCDE>;
+      const void* k = nullptr;
+      if (high) {
+        tsmem = sizeof(TcSmem<L, true>);
+        k = m->eq == LBM_NSE ? reinterpret_cast<const void*>(tc_kernel(std::true_type{}, NSE_{}))
+                             : reinterpret_cast<const void*>(tc_kernel(std::true_type{}, NCDE_{}));
+        tgrid = tc_grid(m, tp.ntiles, k, TcShape<L, true>::CTAS, tsmem);
+      } else {
+        tsmem = sizeof(TcSmem<L, false>);
+        k = m->eq == LBM_NSE ? reinterpret_cast<const void*>(tc_kernel(std::false_type{}, NSE_{}))
+                             : reinterpret_cast<const void*>(tc_kernel(std::false_type{}, NCDE_{}));
+        tgrid = tc_grid(m, tp.ntiles, k, TcShape<L, false>::CTAS, tsmem);
+      }
     }
   }
   for (int64_t s = 0; s < nsteps; ++s) {
@@ -863,10 +881,17 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
     bool done = false;
     if constexpr (is_deviation_storage<ST>()) {
       if (tensor) {
-        if (m->eq == LBM_NSE)
-          k_step_tc<L, ST, LBM_NSE><<<tgrid, 128, 0, m->stream>>>(p, tp, fin, fout, phi);
-        else
-          k_step_tc<L, ST, LBM_NCDE><<<tgrid, 128, 0, m->stream>>>(p, tp, fin, fout, phi);
+        if (high) {
+          if (m->eq == LBM_NSE)
+            k_step_tc<L, ST, LBM_NSE, true><<<tgrid, 128, tsmem, m->stream>>>(p, tp, fin, fout, phi);
+          else
+            k_step_tc<L, ST, LBM_NCDE, true><<<tgrid, 128, tsmem, m->stream>>>(p, tp, fin, fout, phi);
+        } else {
+          if (m->eq == LBM_NSE)
+            k_step_tc<L, ST, LBM_NSE, false><<<tgrid, 128, tsmem, m->stream>>>(p, tp, fin, fout, phi);
+          else
+            k_step_tc<L, ST, LBM_NCDE, false><<<tgrid, 128, tsmem, m->stream>>>(p, tp, fin, fout, phi);
+        }
         done = true;
       }
     }

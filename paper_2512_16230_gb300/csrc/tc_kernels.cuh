@@ -10,6 +10,9 @@
 // 32x32b tensor-memory load. h, computed per cell in FP32 by the same moment-space collision as
 // the CUDA-core kernel (collide_moments), is scaled per cell by a power of two and split into a
 // 16-bit high and low part (K = 2R), so the back projection keeps about 22 bits of h.
+// HI (one rate per order >= 4): the Q - R higher rows join both products as dense 16-bit
+// operands, y_r = sum_i H_r(c_i) d_i in the forward product and sum_r H_r(c_i) z_r (z_r = a_r y_r,
+// a_r = -(s_r - s_h) / N_r) in the back projection, which is the full Q x Q collision.
 // Operands sit in shared memory in the K-major, non-swizzled canonical layout (core matrices of
 // 8 rows x 16 bytes). Every mbarrier wait is bounded: on timeout the CTA records an error in the
 // model's status word, frees its tensor memory and returns.
@@ -19,11 +22,15 @@
 
 namespace lbm {
 
-template <class L>
+template <class L, bool HI>
 struct TcShape {
-  static constexpr int QP = (L::Q + 15) / 16 * 16;  // K of the forward product, N of the backward
-  static constexpr int RP = (L::R + 15) / 16 * 16;  // N of the forward product
-  static constexpr int K2 = 2 * RP;                 // K of the backward product (high | low)
+  static constexpr int QP = (L::Q + 15) / 16 * 16;    // K of the forward product, N of the backward
+  static constexpr int RP = (L::R + 15) / 16 * 16;    // moment columns of the forward product
+  static constexpr int NH = HI ? L::Q - L::R : 0;     // higher rows (HI)
+  static constexpr int NHP = (NH + 15) / 16 * 16;
+  static constexpr int N1 = RP + NHP;                 // N of the forward product
+  static constexpr int K2 = 2 * RP + NHP;             // K of the backward: h high | h low | z
+  static constexpr int CTAS = HI ? 3 : 4;             // resident CTAs per SM (shared memory)
 };
 
 // Byte offset of element (r, k) of a K-major tile of 16-bit values with KP values per row.
@@ -31,13 +38,13 @@ __host__ __device__ constexpr uint32_t kmajor_off(int r, int k, int KP) {
   return uint32_t((r >> 3) * (KP * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-template <class L>
+template <class L, bool HI>
 struct __align__(1024) TcSmem {
-  using S = TcShape<L>;
-  uint8_t a[128 * S::QP * 2];   // deviations: row = cell, k = population
-  uint8_t b1[S::RP * S::QP * 2];  // row = monomial k, column = population i: mono_k(e_i)
-  uint8_t a2[128 * S::K2 * 2];  // per-cell h: high parts, then low parts
-  uint8_t b2[S::QP * S::K2 * 2];  // row = population i, column = monomial (twice): mono_k(e_i)
+  using S = TcShape<L, HI>;
+  uint8_t a[128 * S::QP * 2];     // deviations: row = cell, k = population
+  uint8_t b1[S::N1 * S::QP * 2];  // row n < R: mono_n(e_i); row RP + r: H_r(c_i) of the higher rows
+  uint8_t a2[128 * S::K2 * 2];    // per cell: h high parts, h low parts, z
+  uint8_t b2[S::QP * S::K2 * 2];  // row = population i: mono_k(e_i) twice, then H_r(c_i)
   uint64_t mbar;
   uint32_t tmem;
 };
@@ -62,28 +69,38 @@ __device__ __forceinline__ uint16_t round16(float v) {
   else return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
-constexpr int kTcCols = 128;                  // TMEM columns per CTA: D1 at 0, D2 at 64
+constexpr int kTcCols = 128;  // TMEM columns per CTA: D1 in [0, N1), then D2 in [0, QP)
 
-template <class L, class ST, int EQ>
-__global__ void __launch_bounds__(128, 4) k_step_tc(const StepParams<float> p, const TcParams tp,
-                                                    const ST* __restrict__ fin, ST* __restrict__ fout,
-                                                    float* __restrict__ phi) {
-  using S = TcShape<L>;
-  constexpr int Q = L::Q, R = L::R, QP = S::QP, RP = S::RP, K2 = S::K2;
+template <class L, class ST, int EQ, bool HI>
+__global__ void __launch_bounds__(128, TcShape<L, HI>::CTAS)
+    k_step_tc(const StepParams<float> p, const TcParams tp, const ST* __restrict__ fin, ST* __restrict__ fout,
+              float* __restrict__ phi) {
+  using S = TcShape<L, HI>;
+  constexpr int Q = L::Q, R = L::R, QP = S::QP, RP = S::RP, NH = S::NH, NHP = S::NHP, N1 = S::N1, K2 = S::K2;
   constexpr bool BF = std::is_same<ST, __nv_bfloat16>::value;
-  static_assert(QP <= 64 && RP <= 32, "TMEM column plan: D1 in columns [0, 32), D2 in [64, 128)");
-  __shared__ TcSmem<L> sm;
+  static_assert(QP <= kTcCols && N1 <= kTcCols, "TMEM column plan");
+  static_assert(NH <= kMaxHigh, "higher-row table");
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  TcSmem<L, HI>& sm = *reinterpret_cast<TcSmem<L, HI>*>(tc_smem_raw);
   const int tid = threadIdx.x;
 
   // operand tables, once per CTA
-  for (int idx = tid; idx < RP * QP; idx += 128) {
+  for (int idx = tid; idx < N1 * QP; idx += 128) {
     const int n = idx / QP, k = idx % QP;
-    const float v = (n < R && k < Q) ? float(tp.mono[k][n]) : 0.f;
+    float v = 0.f;
+    if (k < Q) {
+      if (n < R) v = float(tp.mono[k][n]);
+      else if (n >= RP && n - RP < NH) v = tp.hrow[n - RP][k];
+    }
     *reinterpret_cast<uint16_t*>(sm.b1 + kmajor_off(n, k, QP)) = round16<ST>(v);
   }
   for (int idx = tid; idx < QP * K2; idx += 128) {
-    const int i = idx / K2, k = idx % K2, kk = k % RP;
-    const float v = (i < Q && kk < R) ? float(tp.mono[i][kk]) : 0.f;
+    const int i = idx / K2, k = idx % K2;
+    float v = 0.f;
+    if (i < Q) {
+      if (k < 2 * RP && k % RP < R) v = float(tp.mono[i][k % RP]);
+      else if (k >= 2 * RP && k - 2 * RP < NH) v = tp.hrow[k - 2 * RP][i];
+    }
     *reinterpret_cast<uint16_t*>(sm.b2 + kmajor_off(i, k, K2)) = round16<ST>(v);
   }
   if (tid == 0) {
@@ -100,10 +117,10 @@ __global__ void __launch_bounds__(128, 4) k_step_tc(const StepParams<float> p, c
   tc::fence_after_sync();
   const uint32_t tmem = sm.tmem;
   const uint32_t row_lane = uint32_t(tid & ~31) << 16;  // this warp's 32 TMEM lanes
-  const uint32_t d1 = tmem, d2 = tmem + 64;
+  const uint32_t d1 = tmem, d2 = tmem;  // D2 reuses D1's columns once every row has been read
   const uint32_t a_s = tc::smem_addr(sm.a), b1_s = tc::smem_addr(sm.b1);
   const uint32_t a2_s = tc::smem_addr(sm.a2), b2_s = tc::smem_addr(sm.b2);
-  constexpr uint32_t idesc1 = tc::idesc_f16<BF>(128, RP);
+  constexpr uint32_t idesc1 = tc::idesc_f16<BF>(128, N1);
   constexpr uint32_t idesc2 = tc::idesc_f16<BF>(128, QP);
   const size_t N = size_t(p.ncells);
   uint32_t phase = 0;
@@ -190,14 +207,29 @@ __global__ void __launch_bounds__(128, 4) k_step_tc(const StepParams<float> p, c
     body_force(p.force_a, p.force_b, p.force_tab, x, y, z, F);
     float phi_prev = 0.f, phi_now = 0.f;
     if constexpr (EQ == LBM_NCDE) phi_prev = live ? phi[cell] : 0.f;
+    // HI: z_r = a_r y_r from the higher-row columns of the forward product
+    float zr[NH > 0 ? NH : 1];
+    if constexpr (HI) {
+      static_for<NHP / 16>([&](auto c) {
+        constexpr int C = decltype(c)::value;
+        float v[16];
+        tc::ld16(d1 + row_lane + RP + 16 * C, v);
+        tc::wait_ld();
+        static_for<16>([&](auto j) {
+          constexpr int K = 16 * C + decltype(j)::value;
+          if constexpr (K < NH) zr[K] = tp.ah[K] * v[decltype(j)::value];
+        });
+      });
+    }
     float h[R];
     collide_moments<L, float, EQ, true>(mu, p, F, phi_prev, phi_now, h);
     if constexpr (EQ == LBM_NCDE) {
       if (live) phi[cell] = phi_now;
     }
-    // per-cell power-of-two scale, then h = high + low in 16 bits each
+    // per-cell power-of-two scale, then h = high + low in 16 bits each (z rides with h's scale)
     float hmax = 0.f;
     static_for<R>([&](auto k) { hmax = fmaxf(hmax, fabsf(h[decltype(k)::value])); });
+    if constexpr (HI) static_for<NH>([&](auto k) { hmax = fmaxf(hmax, fabsf(zr[decltype(k)::value])); });
     const uint32_t ex = (__float_as_uint(hmax) >> 23) & 0xFFu;
     const float sc = (live && hmax > 0.f && ex >= 1u && ex <= 252u) ? __uint_as_float((254u - ex) << 23) : 1.f;
     uint32_t hp[K2 / 2];
@@ -211,6 +243,13 @@ __global__ void __launch_bounds__(128, 4) k_step_tc(const StepParams<float> p, c
       hp[K / 2] |= (K & 1) ? (uint32_t(hi) << 16) : uint32_t(hi);
       hp[(RP + K) / 2] |= (K & 1) ? (uint32_t(lo) << 16) : uint32_t(lo);
     });
+    if constexpr (HI) {
+      static_for<NH>([&](auto k) {
+        constexpr int K = decltype(k)::value;
+        const uint16_t b = round16<ST>(live ? zr[K] * sc : 0.f);
+        hp[(2 * RP + K) / 2] |= (K & 1) ? (uint32_t(b) << 16) : uint32_t(b);
+      });
+    }
     static_for<K2 / 8>([&](auto c) {
       constexpr int C = decltype(c)::value;
       *reinterpret_cast<uint4*>(sm.a2 + kmajor_off(tid, 8 * C, K2)) =

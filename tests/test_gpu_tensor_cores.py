@@ -125,3 +125,48 @@ def test_tensor_cores_need_16bit_storage():
     gm = gpu_model(spec, "nse", (8, 8), np.ones(spec.R), store="f32")
     with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
         gm.set_tensor_cores(1)
+
+
+HIGH_RATES = {4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25}
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q25", "rD3Q33", "rD3Q45", "rD3Q53"])
+def test_tensor_core_high_order_rates_step(name, store):
+    """The full Q x Q collision with one rate per order >= 4 on tcgen05 (the higher rows join both
+    products): one step against the FP64 oracle with the same per-order rates, within the
+    rounding of input and output."""
+    spec = ALL_SPECS[name]
+    d = spec.d
+    n = RAGGED[d]
+    s = np.random.default_rng(31).uniform(0.6, 1.9, spec.R)
+    kw = dict(s_high=1.2, force=(0, d - 1, 1e-3, 1, 0.2), s_orders=HIGH_RATES)
+    gm = gpu_model(spec, "nse", n, s, store=store, **kw)
+    om = oracle_model(spec, "nse", n, s, **kw)
+    gm.set_tensor_cores(1)
+    w = om.lat.w.reshape((-1,) + (1,) * d)
+    r = np.random.default_rng(6).uniform(-0.1, 0.1, size=(gm.Q,) + n[::-1])
+    f_in = w * (1.0 + r)
+    gm.set_populations(f_in)
+    om.set_populations(w + _stored_deviation(f_in, w, store))
+    gm.step(1)
+    om.step(1)
+    err = rel_l2(gm.get_populations() - w, om.f - w)
+    print(f"{name} {store}: deviation rel L2 after one tensor-core step with per-order rates {err:.2e}")
+    assert err <= 4 * UNIT[store]
+
+
+def test_tensor_core_high_order_rates_flow():
+    """A Taylor-Green flow (24 x 24 x 18 rD3Q53, Re 100) with per-order rates over 40 steps with
+    FP16 deviations, where tcgen05 is the default kernel: velocity against the FP64 oracle within
+    the FP16 bound."""
+    wl = W.taylor_green_3d(n=(24, 24, 18), steps=40, re=100.0)
+    spec = wl.lattice
+    om = oracle_model(spec, wl.eq, wl.n, wl.s, wl.s_high, s_orders=HIGH_RATES)
+    gm = gpu_model(spec, wl.eq, wl.n, wl.s, wl.s_high, store="f16_dev", s_orders=HIGH_RATES)
+    rho, u = wl.fields()
+    om.init_fields(rho, u)
+    gm.init_fields(rho, u)
+    om.step(wl.steps)
+    gm.step(wl.steps)
+    assert rel_l2(gm.read_fields()[1], om.fields()[1]) <= 1e-3
