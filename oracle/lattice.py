@@ -31,7 +31,11 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-KINDS = ("rD2Q13", "rD2Q17", "rD2Q21", "rD2Q25", "rD3Q33", "rD3Q45", "rD3Q53")
+KINDS = ("rD2Q13", "rD2Q17", "rD2Q21", "rD2Q25", "rD3Q33", "rD3Q45", "rD3Q53", "rD2Q9", "rD3Q27")
+
+# Single-speed (standard) lattices on rectangular cells: the special case of Sec. 3.4 with k = 1,
+# whose velocity components are 0 and +-1 only.
+SINGLE_SPEED = ("rD2Q9", "rD3Q27")
 
 # ---------------------------------------------------------------------------------------------
 # Velocity sets (integer multiples e_j of the axis speeds c_a), columns in the paper's order.
@@ -61,6 +65,8 @@ VELOCITIES = {
     "rD3Q53": E_RD3Q53,
     "rD3Q45": E_RD3Q53[:45],
     "rD3Q33": E_RD3Q53[:33],
+    "rD2Q9": E_RD2Q25[:9],       # rest, the four axis and the four diagonal vectors
+    "rD3Q27": E_RD3Q53[:27],     # every vector with components in {-1, 0, 1}
 }
 
 # App. C: the special D2Q21 lattice with knight-move velocities (a CHECK case, not a runtime lattice).
@@ -78,7 +84,7 @@ E_SPECIAL_D2Q21 = np.array([
 #   rD3Q45: ()                     rD3Q53 with w45 = 0
 #   rD3Q33: ()                     App. D (w33 = w37 = w41 = w45 = 0)
 N_FREE = {"rD2Q25": 4, "rD2Q21": 3, "rD2Q17": 1, "rD2Q13": 0,
-          "rD3Q53": 1, "rD3Q45": 0, "rD3Q33": 0}
+          "rD3Q53": 1, "rD3Q45": 0, "rD3Q33": 0, "rD2Q9": 0, "rD3Q27": 0}
 
 
 def dim_of(kind: str) -> int:
@@ -207,7 +213,22 @@ def weights(kind: str, c, cs2, free_w=()) -> np.ndarray:
         return expand_rd3(cls, int(kind[4:]))
     if kind == "rD3Q33":
         return expand_rd3(weights_rd3q33_classes(dd[0], dd[1], dd[2]), 33)
+    if kind in SINGLE_SPEED:
+        return weights_single_speed(VELOCITIES[kind], dd)
     raise ValueError(kind)
+
+
+def weights_single_speed(e, dd) -> np.ndarray:
+    """Single-speed lattices: the weight conditions of Eq. (new11) that a velocity set with
+    components in {0, +-1} can meet are sum w = 1, Delta2_aa = c_sa^2 and the mixed fourth (and,
+    in 3D, sixth) moments Delta4_aabb = Delta2_aa Delta2_bb, Delta6_xxyyzz = Delta2_xx Delta2_yy
+    Delta2_zz (the axis condition Delta4_aaaa = 3 Delta2_aa^2 fails unless d_0a = 1/3: that defect
+    is the delta^(4) of k = 1). With one weight per reflection class these conditions are solved
+    by the product of the one-dimensional weights w(0) = 1 - d_0a, w(+-1) = d_0a / 2."""
+    w = np.ones(e.shape[0])
+    for a in range(e.shape[1]):
+        w = w * np.where(e[:, a] == 0, 1.0 - dd[a], 0.5 * dd[a])
+    return w
 
 
 def lattice_moment(w, cvel, idx) -> float:
@@ -264,13 +285,15 @@ CORRECTIONS_2D = {8: (6,), 9: (7,)}
 CORRECTIONS_3D = {17: (10, 11), 18: (12, 13), 19: (14, 15)}
 
 
-def hermite_polys(d, w, cvel, correct=True):
+def hermite_polys(d, w, cvel, correct=True, single=False):
     """Sec. 5: H0 = e, H1 = E, H2 = <EE> - Delta2, H3 = ccc - <c Delta2>, then the
     rectangular-cell correction of the third-order rows by W-projection (Eq. (CorrectQ25), App. D).
 
     Delta2 is the lattice tensor of Eq. (new0) computed from the weights. Returns the list of
-    polynomials and the projection coefficients used by the correction."""
-    rows = ROWS_2D if d == 2 else ROWS_3D
+    polynomials and the projection coefficients used by the correction. ``single``: a
+    single-speed lattice, where c_a^3 is c_a^2 times c_a, so the pure cubes (the last d rows, the
+    only corrected ones) are dependent on the first-order rows and are left out."""
+    rows = row_list(d, single)
     delta2 = np.array([[lattice_moment(w, cvel, (a, b)) for b in range(d)] for a in range(d)])
     polys = []
     for axes in rows:
@@ -285,7 +308,7 @@ def hermite_polys(d, w, cvel, correct=True):
             p = poly_add(p, {_unit(d, (g,)): -delta2[a, b]})
         polys.append(p)
     coefs = {}
-    if correct:
+    if correct and not single:
         corr = CORRECTIONS_2D if d == 2 else CORRECTIONS_3D
         for r, against in corr.items():
             hbar = poly_eval(polys[r], cvel)
@@ -299,9 +322,15 @@ def hermite_polys(d, w, cvel, correct=True):
     return polys, coefs
 
 
+def row_list(d, single=False):
+    """Rows of order <= 3 in the paper's order; single-speed lattices drop the pure cubes."""
+    rows = ROWS_2D if d == 2 else ROWS_3D
+    return rows[:len(rows) - d] if single else rows
+
+
 # Orders of the rows above (0..3), used for the blocks H_k of Eq. (feq-1).
-def row_orders(d):
-    return [len(a) for a in (ROWS_2D if d == 2 else ROWS_3D)]
+def row_orders(d, single=False):
+    return [len(a) for a in row_list(d, single)]
 
 
 # Higher rows printed by the paper: rD2Q13 rows 11-13 of Eq. (TransM) and rD3Q33 rows M21..M33 (App. D).
@@ -364,9 +393,10 @@ def build(kind: str, c, cs2, free_w=(), correct=True, high_rows=None) -> Lattice
 
 def build_from(kind, d, c, cs2, e, w, correct=True, high_rows=None) -> Lattice:
     cvel = e * np.asarray(c)[None, :]
-    polys, coefs = hermite_polys(d, w, cvel, correct=correct)
+    single = kind in SINGLE_SPEED
+    polys, coefs = hermite_polys(d, w, cvel, correct=correct, single=single)
     H = np.stack([poly_eval(p, cvel) for p in polys])
-    orders = row_orders(d)
+    orders = row_orders(d, single)
     Q = e.shape[0]
     # Higher rows, graded by degree: the order-k block is the W-orthogonal complement of all rows of
     # lower degree inside the span of the monomials of degree <= k on the lattice (a subspace fixed

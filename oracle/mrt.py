@@ -62,10 +62,12 @@ def axis_of(alpha: int, d: int, lead: int = 1) -> int:
 # Continuous moments and Hermite moments of the equilibrium
 # ---------------------------------------------------------------------------------------------
 
-def continuous_moment_nse(ex, rho, j, p):
+def continuous_moment_nse(ex, rho, j, p, m30=True):
     """Raw continuous moment of the monomial with exponents ``ex`` for the NSE equilibrium:
-    M0 = rho, M1 = rho u, M2 = rho u u + p I, M3 = p (u_a d_bg + u_b d_ag + u_g d_ab) + rho u u u
-    (Eq. (M-NSEs-6a), Eq. (M-NSEs-6-1) with k = 0 and M30 = rho u u u)."""
+    M0 = rho, M1 = rho u, M2 = rho u u + p I, M3 = p (u_a d_bg + u_b d_ag + u_g d_ab) + M30
+    (Eq. (M-NSEs-6a), Eq. (M-NSEs-6-1)): multispeed lattices take k = 0 and M30 = rho u u u;
+    single-speed lattices (k = 1) take M30 = 0 as the standard-lattice case of Sec. 3.4 does, and
+    have no pure-cube rows, so the k delta^(4) part of M3 never enters a row."""
     axes = [a for a, k in enumerate(ex) for _ in range(k)]
     u = [j[a] / rho for a in range(len(j))]
     if len(axes) == 0:
@@ -77,7 +79,7 @@ def continuous_moment_nse(ex, rho, j, p):
         return rho * u[a] * u[b] + (p if a == b else 0.0)
     if len(axes) == 3:
         a, b, g = axes
-        out = rho * u[a] * u[b] * u[g]
+        out = rho * u[a] * u[b] * u[g] if m30 else 0.0 * rho
         if b == g:
             out = out + p * u[a]
         if a == g:
@@ -91,11 +93,12 @@ def continuous_moment_nse(ex, rho, j, p):
 def hermite_moments_eq_nse(lat: L.Lattice, rho, j, cs2_eq):
     """m^eq_r = P_r(M): each Hermite polynomial with its monomials replaced by the moments."""
     p = rho * cs2_eq
+    m30 = lat.kind not in L.SINGLE_SPEED
     out = []
     for poly in lat.polys:
         m = np.zeros_like(rho)
         for ex, coef in poly.items():
-            m = m + coef * continuous_moment_nse(ex, rho, j, p)
+            m = m + coef * continuous_moment_nse(ex, rho, j, p, m30)
         out.append(m)
     return np.stack(out)
 
@@ -175,6 +178,8 @@ class Model:
         self.normal = [r for r, p in enumerate(self.lat.polys)
                        if self.lat.orders[r] == 2 and max(max(p, key=sum)) == 2]
         if self.s_bulk is not None:
+            if self.lat.kind in L.SINGLE_SPEED:
+                raise ValueError("the bulk block of Eq. (4-27) is read for the multispeed lattices (k = 0) only")
             S[np.ix_(self.normal, self.normal)] = self.normal_block()
         self.S = S
         self.Hinv = L.hermite_inverse(self.lat)

@@ -36,9 +36,16 @@ class LatticeSpec:
         return len(self.c)
 
     @property
-    def R(self):
-        return 10 if self.d == 2 else 20
+    def single(self):
+        """Single-speed lattice (components in {0, +-1}; k = 1 of Sec. 3.4)."""
+        return self.kind in SINGLE_SPEED
 
+    @property
+    def R(self):
+        return len(row_orders(self.d, self.single))
+
+
+SINGLE_SPEED = ("rD2Q9", "rD3Q27")
 
 # Shared-c_s setting of rD3Q53 on dz/dx = 4/3 (negative weights and a negative H_zzz norm).
 RD3Q53_SHARED_CS = LatticeSpec("rD3Q53", (1.0, 1.0, 4.0 / 3.0), (0.624,) * 3, (2.9625e-4,))
@@ -52,27 +59,40 @@ LATTICES = {
     "rD3Q53-cubic": LatticeSpec("rD3Q53", (1.0, 1.0, 1.0), (0.6,) * 3, (2.4e-4,)),
     "rD3Q45": LatticeSpec("rD3Q45", (1.0, 1.0, 1.0), (0.6,) * 3, ()),
     "rD3Q33": LatticeSpec("rD3Q33", (1.0, 1.0, 1.0), (0.5,) * 3, ()),
+    # single-speed lattices on rectangular cells (d_0 = c_s^2 / c_a^2 < 1 keeps every weight positive)
+    "rD2Q9": LatticeSpec("rD2Q9", (1.0, 4.0 / 3.0), (1.0 / 3.0, 1.0 / 3.0), ()),
+    "rD3Q27": LatticeSpec("rD3Q27", (1.0, 1.0, 4.0 / 3.0), (1.0 / 3.0,) * 3, ()),
 }
 
 
-def row_orders(d):
-    """Order (0..3) of each Hermite row in the paper's order (2D: App. C, 3D: App. D)."""
-    return [0, 1, 1, 2, 2, 2, 3, 3, 3, 3] if d == 2 else [0, 1, 1, 1] + [2] * 6 + [3] * 10
+def row_orders(d, single=False):
+    """Order (0..3) of each Hermite row in the paper's order (2D: App. C, 3D: App. D); the
+    single-speed lattices have no pure-cube rows (the last d)."""
+    o = [0, 1, 1, 2, 2, 2, 3, 3, 3, 3] if d == 2 else [0, 1, 1, 1] + [2] * 6 + [3] * 10
+    return o[:len(o) - d] if single else o
 
 
-def rates_nse(d, nu, cs2, s3=1.0):
-    """s_nu = 1 / (nu / cs2 + 1/2) on every second-order row, s3 on the third-order rows."""
-    s = np.ones(10 if d == 2 else 20)
-    o = np.array(row_orders(d))
+def rates_nse(d, nu, cs2, s3=1.0, spec=None):
+    """s_nu = 1 / (nu / cs2 + 1/2) on every second-order row, s3 on the third-order rows. On a
+    single-speed lattice (k = 1) the normal rows c_a^2 - c_sa^2 take s_a = 1 / (2 nu / (c_a^2 - cs2)
+    + 1/2) per axis, which makes the normal viscosity of Eq. (4-29) equal to the shear one."""
+    single = spec is not None and spec.single
+    o = np.array(row_orders(d, single))
+    s = np.ones(len(o))
     s[o == 2] = 1.0 / (nu / cs2 + 0.5)
     s[o == 3] = s3
+    if single:
+        normal = (3, 5) if d == 2 else (4, 5, 6)
+        for a, r in enumerate(normal):
+            s[r] = 1.0 / (2.0 * nu / (spec.c[a] ** 2 - cs2) + 0.5)
     return s
 
 
-def rates_ncde(d, K, cs2):
+def rates_ncde(d, K, cs2, spec=None):
     """s_1 = 1 / (K / cs2 + 1/2) on the first-order rows."""
-    s = np.ones(10 if d == 2 else 20)
-    s[np.array(row_orders(d)) == 1] = 1.0 / (K / cs2 + 0.5)
+    o = np.array(row_orders(d, spec is not None and spec.single))
+    s = np.ones(len(o))
+    s[o == 1] = 1.0 / (K / cs2 + 0.5)
     return s
 
 
@@ -111,13 +131,13 @@ class Workload:
         raise ValueError(kind)
 
 
-def taylor_green_2d(n=(64, 48), steps=200, store="f64", re=100.0, ma=0.05):
+def taylor_green_2d(n=(64, 48), steps=200, store="f64", re=100.0, ma=0.05, lattice="rD2Q25"):
     """Config: rD2Q25 Taylor-Green vortex, L = 2 pi on rectangular cells (dy/dx = 4/3),
     u0 = 0.05 c_s, Re = u0 L / nu with L = L_x / (2 pi)."""
-    lat = LATTICES["rD2Q25"]
+    lat = LATTICES[lattice]
     u0 = ma * math.sqrt(lat.cs2[0])
     nu = u0 * (n[0] * lat.c[0] / (2 * math.pi)) / re
-    return Workload("rD2Q25 Taylor-Green 2D", lat, "nse", tuple(n), steps, rates_nse(2, nu, lat.cs2[0]),
+    return Workload(f"{lat.kind} Taylor-Green 2D", lat, "nse", tuple(n), steps, rates_nse(2, nu, lat.cs2[0], spec=lat),
                     store=store, init=dict(kind="tgv2d", u0=u0, nu=nu))
 
 
@@ -126,7 +146,7 @@ def ncde_hill(n=(1024, 768), steps=5000, store="f32", D0=0.1, nonlin=1.0, sigma=
     """Config: rD2Q13 nonlinear convection-diffusion d_t phi + div(u phi) = div(D0 (1 + phi^2) grad phi),
     u = (0.02, 0.01), dy/dx = 1.25, Gaussian hill A = 1, sigma = 20 dx plus U[-1e-3, 1e-3] noise."""
     lat = LATTICES["rD2Q13"]
-    return Workload("rD2Q13 nonlinear CDE", lat, "ncde", tuple(n), steps, rates_ncde(2, D0, lat.cs2[0]),
+    return Workload("rD2Q13 nonlinear CDE", lat, "ncde", tuple(n), steps, rates_ncde(2, D0, lat.cs2[0], spec=lat),
                     store=store, u_const=tuple(u), nonlin=nonlin,
                     init=dict(kind="hill", sigma=sigma, noise=noise, seed=seed, D0=D0))
 
@@ -137,7 +157,7 @@ def taylor_green_3d(n=(256, 256, 192), steps=1000, store="f32", re=1600.0, ma=0.
     lat = LATTICES[lattice]
     u0 = ma * math.sqrt(lat.cs2[0])
     nu = u0 * (n[0] * lat.c[0] / (2 * math.pi)) / re
-    return Workload(f"{lat.kind} Taylor-Green 3D", lat, "nse", tuple(n), steps, rates_nse(3, nu, lat.cs2[0]),
+    return Workload(f"{lat.kind} Taylor-Green 3D", lat, "nse", tuple(n), steps, rates_nse(3, nu, lat.cs2[0], spec=lat),
                     store=store, init=dict(kind="tgv3d", u0=u0, nu=nu))
 
 
@@ -147,7 +167,7 @@ def kolmogorov_3d(lattice="rD3Q53-cubic", n=(32, 32, 32), steps=200, store="f32"
     ly = n[1] * lat.c[1]
     umax = umax_ma * math.sqrt(lat.cs2[0])
     A = umax * nu * (2 * math.pi / ly) ** 2
-    return Workload(f"{lat.kind} Kolmogorov 3D", lat, "nse", tuple(n), steps, rates_nse(3, nu, lat.cs2[0]),
+    return Workload(f"{lat.kind} Kolmogorov 3D", lat, "nse", tuple(n), steps, rates_nse(3, nu, lat.cs2[0], spec=lat),
                     store=store, force=(0, 1, A, 1, 0.0), init=dict(kind="rest"))
 
 
@@ -162,11 +182,11 @@ def serving_workload(req, store):
         lat = LATTICES[req["lattice"]]
         u0 = 0.05 * math.sqrt(lat.cs2[0])
         nu = u0 * (n[0] * lat.c[0] / (2 * math.pi)) / 100.0
-        wl = Workload(f"{lat.kind} Taylor-Green 2D", lat, "nse", n, req["steps"], rates_nse(2, nu, lat.cs2[0]),
+        wl = Workload(f"{lat.kind} Taylor-Green 2D", lat, "nse", n, req["steps"], rates_nse(2, nu, lat.cs2[0], spec=lat),
                       store=store, init=dict(kind="tgv2d", u0=u0, nu=nu))
     else:
         lat = LATTICES[req["lattice"]]
-        wl = Workload(f"{lat.kind} nonlinear CDE", lat, "ncde", n, req["steps"], rates_ncde(2, 0.1, lat.cs2[0]),
+        wl = Workload(f"{lat.kind} nonlinear CDE", lat, "ncde", n, req["steps"], rates_ncde(2, 0.1, lat.cs2[0], spec=lat),
                       store=store, u_const=(0.02, 0.01), nonlin=1.0,
                       init=dict(kind="hill", sigma=max(2.0, n[0] / 8.0), noise=1e-3, seed=req["seed"]))
     return wl

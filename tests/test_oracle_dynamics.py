@@ -626,3 +626,101 @@ def test_equation_of_state_sets_sound_speed(cs2_eq):
     for axis in (0, 1):
         half, want = _sound_period(cs2_eq, axis)
         assert abs(half / want - 1) < 1e-2
+
+
+@pytest.mark.parametrize("kind,c", [("rD2Q9", (1.0, 4.0 / 3.0)), ("rD3Q27", (1.0, 1.0, 4.0 / 3.0))])
+def test_single_speed_equilibrium_moments(kind, c):
+    """Single-speed EDF: every monomial of degree <= 2 and every mixed third-order one takes its
+    continuous moment with M30 = 0 (p u for c_a c_b^2, zero for c_x c_y c_z); the pure cubes are
+    fixed by the lattice, sum f^eq c_a^3 = c_a^2 rho u_a, the k = 1 form of M3 (rho (c_s^2 Delta
+    + delta^(4)) . u with delta^(4)_aaaa = c_a^2 - 3 c_s^2)."""
+    d = len(c)
+    cs2 = (0.3,) * d
+    lat = L.build(kind, c, cs2)
+    n = (3,) * d
+    rho, u = I.random_fields(n, d, seed=2)
+    m = M.Model(lat, "nse", n, np.ones(lat.R), cs2_eq=0.3)
+    feq = m.equilibrium(rho, u)
+    p = 0.3 * rho
+    for deg in range(4):
+        for ex in itertools.product(range(deg + 1), repeat=d):
+            if sum(ex) != deg:
+                continue
+            axes = [a for a in range(d) for _ in range(ex[a])]
+            got = np.tensordot(_mono(lat.cvel, axes), feq, axes=(0, 0))
+            if deg == 0:
+                want = rho
+            elif deg == 1:
+                want = rho * u[axes[0]]
+            elif deg == 2:
+                a, b = axes
+                want = rho * u[a] * u[b] + (p if a == b else 0.0)
+            elif max(ex) == 3:
+                a = axes[0]
+                want = c[a] ** 2 * rho * u[a]
+            else:
+                want = sum(p * u[x] for x, y, z in itertools.permutations(axes) if y == z) / 2 if len(set(axes)) == 2 else 0 * rho
+            assert np.abs(got - want).max() < 1e-14, ex
+
+
+def _single_speed_sound(axis, s_n=1.5, nsteps=400):
+    c, cs2 = (1.0, 4.0 / 3.0), (1.0 / 3.0, 1.0 / 3.0)
+    lat = L.build("rD2Q9", c, cs2)
+    s = np.ones(lat.R)
+    s[[3, 5]] = s_n
+    n = (48, 4) if axis == 0 else (4, 36)
+    m = M.Model(lat, "nse", n, s, 1.0)
+    xs = I.coords(n, c)
+    k = 2 * math.pi / (n[axis] * c[axis])
+    m.init_fields(1.0 + 1e-4 * np.cos(k * xs[axis]), np.zeros((2,) + xs[0].shape))
+
+    def energy():
+        r, u = m.fields()
+        return np.sum((r - 1.0) ** 2 * cs2[0] + r * (u ** 2).sum(0))
+
+    m.step(40)
+    e0 = energy()
+    m.step(nsteps)
+    gamma = math.log(e0 / energy()) / nsteps / 2
+    nu_long = (1.0 / s_n - 0.5) * (c[axis] ** 2 - cs2[0])
+    return gamma / (k * k * nu_long / 2)
+
+
+def test_single_speed_normal_viscosity_k1():
+    """Eq. (4-29) with k = 1: on a single-speed lattice the lattice itself sets the pure-cube third
+    moment, sum f c_a^3 = c_a^2 rho u_a, so a longitudinal wave along axis a sees the normal
+    viscosity (1/s_n - 1/2)(c_a^2 - c_s^2) (= 2 mu_a / p with mu_a of Eq. (4-29)); on rectangular
+    rD2Q9 (dy/dx = 4/3, c_s^2 = 1/3) a sound wave is damped 13/6 times faster along y than along x
+    at equal rates, each at k^2 nu_long / 2."""
+    rx, ry = _single_speed_sound(0), _single_speed_sound(1)
+    assert abs(rx - 1) < 2e-2 and abs(ry - 1) < 2e-2
+
+
+def _single_speed_tgv_rate(per_axis):
+    c, cs2 = (1.0, 4.0 / 3.0), (1.0 / 3.0, 1.0 / 3.0)
+    n = (64, 48)
+    lat = L.build("rD2Q9", c, cs2)
+    u0 = 0.05 * math.sqrt(cs2[0])
+    nu = 0.05
+    s = np.ones(lat.R)
+    s[4] = 1.0 / (nu / cs2[0] + 0.5)                     # shear row xy
+    for a, r in ((0, 3), (1, 5)):                          # normal rows xx, yy
+        s[r] = 1.0 / (2 * nu / (c[a] ** 2 - cs2[0]) + 0.5) if per_axis else s[4]
+    m = M.Model(lat, "nse", n, s, 1.0)
+    rho, u = I.taylor_green_2d(n, c, u0, 1.0, cs2[0])
+    m.init_fields(rho, u)
+    k2 = 2 * (2 * math.pi / (n[0] * c[0])) ** 2
+    m.step(60)
+    e60 = _kinetic_energy(m)
+    m.step(140)
+    return math.log(e60 / _kinetic_energy(m)) / 140.0 / (2 * nu * k2)
+
+
+def test_single_speed_taylor_green_needs_axis_rates():
+    """k = 1 on rectangular rD2Q9: with the normal-row rates chosen per axis so that
+    (1/s_a - 1/2)(c_a^2 - c_s^2) = 2 nu (Eq. (4-29), k = 1) the Taylor-Green vortex decays at
+    2 nu |k|^2 within 1%; with one rate for every second-order row the normal stresses carry
+    the lattice anisotropy and the decay rate is off by more than 5%."""
+    good, bad = _single_speed_tgv_rate(True), _single_speed_tgv_rate(False)
+    assert abs(good - 1) < 1e-2
+    assert abs(bad - 1) > 5e-2

@@ -316,3 +316,41 @@ def test_shared_sound_speed_rd3q53_is_indefinite():
     assert -2.1e-3 < lat.w.min() < -1.9e-3
     N = np.sum(lat.w * lat.H ** 2, axis=1)
     assert N[19] < 0 and np.all(N[:19] > 0)
+
+
+@pytest.mark.parametrize("kind,c,cs2", [("rD2Q9", (1.0, 1.0), (1 / 3, 1 / 3)), ("rD2Q9", (1.0, 4 / 3), (0.3, 0.3)),
+                                        ("rD3Q27", (1.0, 1.0, 1.0), (1 / 3,) * 3),
+                                        ("rD3Q27", (1.0, 1.2, 4 / 3), (0.3, 0.32, 0.34))])
+def test_single_speed_weights(kind, c, cs2):
+    """Single-speed lattices: sum w = 1, Delta2_aa = c_sa^2 and the mixed fourth/sixth moments are
+    products (Eq. (new11a), (Cont1-5a), (Cont1-5b), (Cont1-5e)), while the axis fourth moment is
+    c_a^2 c_sa^2 instead of 3 c_sa^4 (the anisotropy delta^(4) of k = 1); odd moments vanish; on
+    the square D2Q9 / D3Q27 at c_s^2 = 1/3 the weights are the textbook 4/9, 1/9, 1/36 and
+    8/27, 2/27, 1/54, 1/216."""
+    lat = L.build(kind, c, cs2)
+    d = lat.d
+    m = lambda *idx: L.lattice_moment(lat.w, lat.cvel, idx)
+    assert abs(lat.w.sum() - 1) < 1e-15
+    for a in range(d):
+        assert abs(m(a, a) - cs2[a]) < 1e-15
+        assert abs(m(a) ) < 1e-15 and abs(m(a, a, a)) < 1e-15
+        assert abs(m(a, a, a, a) - c[a] ** 2 * cs2[a]) < 1e-14
+        for b in range(a + 1, d):
+            assert abs(m(a, a, b, b) - cs2[a] * cs2[b]) < 1e-15
+            assert abs(m(a, b)) < 1e-15
+    if d == 3:
+        assert abs(m(0, 0, 1, 1, 2, 2) - cs2[0] * cs2[1] * cs2[2]) < 1e-15
+    if c == (1.0,) * d:
+        want = [4 / 9, 1 / 9, 1 / 36] if d == 2 else [8 / 27, 2 / 27, 1 / 54, 1 / 216]
+        near = np.abs(lat.w[:, None] - np.array(want)[None, :])
+        assert near.min(axis=1).max() < 1e-15
+        assert set(near.argmin(axis=1)) == set(range(len(want)))
+    # the rows of order <= 3 are the paper's list without the pure cubes, mutually W-orthogonal
+    # and W-orthogonal to the higher rows
+    R = lat.R
+    assert R == (8 if d == 2 else 17)
+    G = (lat.Hfull * lat.w) @ lat.Hfull.T
+    sc = np.sqrt(np.diag(G))
+    rel = G / np.outer(sc, sc)
+    assert np.abs(rel[:R, :R] - np.eye(R)).max() < 1e-13
+    assert np.abs(rel[:R, R:]).max() < 1e-12
