@@ -65,7 +65,9 @@ typedef enum {
   LBM_RD2Q25 = 3, /* Eq. (3-1)                                           */
   LBM_RD3Q33 = 4, /* App. D, rD3Q33                                      */
   LBM_RD3Q45 = 5, /* App. D, rD3Q53 with w45 = 0 (the eight (+-2)^3 vectors dropped) */
-  LBM_RD3Q53 = 6  /* App. D, rD3Q53                                      */
+  LBM_RD3Q53 = 6, /* App. D, rD3Q53                                      */
+  LBM_RD2Q9 = 7,  /* single-speed rectangular D2Q9 (Sec. 3.4, k = 1): rD2Q25's first 9 columns */
+  LBM_RD3Q27 = 8  /* single-speed rectangular D3Q27 (k = 1): rD3Q53's first 27 columns       */
 } lbm_kind;
 
 typedef enum {
@@ -98,16 +100,21 @@ const char* lbm_last_error(void);
 /* Build lattice `kind` on the current CUDA device, in FP64, on the GPU:
  *   - weights from the printed closed forms: Eq. (WeightQ25) (rD2Q25 and its sub-lattices),
  *     Eq. (Q13lattice), the rD3Q53 and rD3Q33 weight lists of App. D, with
- *     d_0a = cs2[a] / c[a]^2 (the definition stated with Eq. (new11));
+ *     d_0a = cs2[a] / c[a]^2 (the definition stated with Eq. (new11)); the single-speed rD2Q9 and
+ *     rD3Q27 meet only sum w = 1, Delta2_aa = cs2[a] and the mixed fourth/sixth moments (their
+ *     axis fourth moment is c_a^2 cs2[a], the delta^(4) anisotropy of k = 1), which gives the
+ *     product of the 1D weights 1 - d_0a and d_0a / 2;
  *   - Hermite rows H0..H3 (Sec. 5) by weighted Gram-Schmidt of the monomials in the paper's row
  *     order, which yields the rectangular-cell correction of the third-order rows of
- *     Eq. (CorrectQ25) and App. D;
+ *     Eq. (CorrectQ25) and App. D; on the single-speed lattices the pure cubes c_a^3 equal
+ *     c_a^2 c_a and are left out (R = 8 in 2D, 17 in 3D; 10 and 20 otherwise), and their
+ *     equilibrium takes M30 = 0, the standard-lattice case of Sec. 3.4;
  *   - norms N_r = sum_i w_i H_ri^2 and a check that H W H^T is diagonal.
  * c[d]      axis speeds c_a = dx_a / dx_1 (c[0] = 1 in lattice units), host memory.
  * cs2[d]    squared sound speed per axis c_sa^2 (Remark 2; equal values = isotropic), host.
  * free_w    the free weights, host memory (may be NULL when n_free == 0), in this order:
  *             rD2Q25: w13, w17, w18, w21     rD2Q21: w13, w17, w18     rD2Q17: w13
- *             rD3Q53: w45                    rD2Q13, rD3Q45, rD3Q33: none
+ *             rD3Q53: w45                    rD2Q13, rD3Q45, rD3Q33, rD2Q9, rD3Q27: none
  * Negative weights are allowed (reported by lbm_lattice_query). Synchronous.
  * Errors: LBM_ERR_ARG (bad kind, n_free, c <= 0, cs2 <= 0), LBM_ERR_LATTICE_INFEASIBLE,
  *         LBM_ERR_CUDA. On success *out receives a new handle. */
@@ -161,15 +168,19 @@ lbm_status lbm_model_create(const lbm_lattice* lat, lbm_eq eq, const int64_t* n,
 /* Diagonal relaxation matrix S in the Hermite basis (Sec. 4, Eq. (H-MRT-LB-1)):
  * s[R] the rate of each Hermite row in the paper's order, s_high the one rate shared by every
  * row of order >= 4. Rates must lie in (0, 2]. The kinematic viscosity of the NSE is
- * nu = cs2_eq (1/s_2 - 1/2) (Eq. (4-29), compressible, k = 0); the NCDE diffusivity is
- * K = cs2_eq (1/s_1 - 1/2) (Eq. (ME-NCDE-3)). */
+ * nu = cs2_eq (1/s_2 - 1/2) (Eq. (4-29), compressible, k = 0); on the single-speed lattices
+ * (k = 1) the normal row c_a^2 - c_sa^2 gives the normal viscosity (1/s_a - 1/2)(c_a^2 - cs2_eq),
+ * so s_a = 1 / (2 nu / (c_a^2 - cs2_eq) + 1/2) per axis makes it isotropic. The NCDE
+ * diffusivity is K = cs2_eq (1/s_1 - 1/2) (Eq. (ME-NCDE-3)). */
 lbm_status lbm_model_set_relaxation(lbm_model* m, const double* s, double s_high);
 
 /* Independent bulk viscosity (NSE): the normal second-order moments relax with the inverse of
  * S2^(1) = diag(1/s_sa) + a 1^T / d, a_a = 1/s_bulk - 1/s_sa (Eq. (4-27) read for the multispeed
  * lattices, k = 0), where s_sa are the rates set for the normal rows c_a^2 - c_sa^2; then
  * mu = (1/s_s - 1/2) p dt and mu_b = (2/d)(1/s_bulk - 1/2) p dt (Eq. (4-29)). The same block
- * enters (I - S2/2) M2G. s_bulk <= 0 restores the diagonal relaxation (mu_b = 2 mu / d). */
+ * enters (I - S2/2) M2G. s_bulk <= 0 restores the diagonal relaxation (mu_b = 2 mu / d).
+ * Errors: LBM_ERR_ARG, LBM_ERR_NOT_IMPLEMENTED (a single-speed lattice: the block is read for the
+ * multispeed lattices, k = 0). */
 lbm_status lbm_model_set_bulk(lbm_model* m, double s_bulk);
 
 /* Rates of the rows of order >= 4, one per order (Eq. (H-MRT-LB) with the full Q x Q Hermite

@@ -69,6 +69,8 @@ lbm_status dispatch_batch_kind(int kind, F&& f) {
     case LBM_RD3Q33: return f(std::integral_constant<int, LBM_RD3Q33>{});
     case LBM_RD3Q45: return f(std::integral_constant<int, LBM_RD3Q45>{});
     case LBM_RD3Q53: return f(std::integral_constant<int, LBM_RD3Q53>{});
+    case LBM_RD2Q9: return f(std::integral_constant<int, LBM_RD2Q9>{});
+    case LBM_RD3Q27: return f(std::integral_constant<int, LBM_RD3Q27>{});
   }
   return set_error(LBM_ERR_ARG, "unknown lattice kind");
 }

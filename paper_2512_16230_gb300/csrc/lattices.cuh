@@ -70,15 +70,20 @@ constexpr int parity_class(Mono m) {
 template <int KIND>
 struct Lat;
 
+// SINGLE: the single-speed lattices (components in {0, +-1}), where c_a^3 = c_a^2 c_a makes the
+// pure-cube rows (the last D of the paper's list) dependent: they keep the first R - D rows, and
+// their equilibrium takes M30 = 0 (the standard-lattice case, k = 1).
 template <int Q_>
 struct Lat2D {
-  static constexpr int D = 2, Q = Q_, R = 10;
-  static constexpr int RMAX = Q_ >= 17 ? 3 : 2;
+  static constexpr bool SINGLE = Q_ == 9;
+  static constexpr int D = 2, Q = Q_, R = SINGLE ? 8 : 10;
+  static constexpr int RMAX = SINGLE ? 1 : (Q_ >= 17 ? 3 : 2);
   static constexpr Vel e(int j) { return kQ25[j]; }
 };
 template <int Q_>
 struct Lat3D {
-  static constexpr int D = 3, Q = Q_, R = 20, RMAX = 2;
+  static constexpr bool SINGLE = Q_ == 27;
+  static constexpr int D = 3, Q = Q_, R = SINGLE ? 17 : 20, RMAX = SINGLE ? 1 : 2;
   static constexpr Vel e(int j) { return q53(j); }
 };
 
@@ -89,6 +94,8 @@ template <> struct Lat<LBM_RD2Q25> : Lat2D<25> { static constexpr int KIND = LBM
 template <> struct Lat<LBM_RD3Q33> : Lat3D<33> { static constexpr int KIND = LBM_RD3Q33; };
 template <> struct Lat<LBM_RD3Q45> : Lat3D<45> { static constexpr int KIND = LBM_RD3Q45; };
 template <> struct Lat<LBM_RD3Q53> : Lat3D<53> { static constexpr int KIND = LBM_RD3Q53; };
+template <> struct Lat<LBM_RD2Q9> : Lat2D<9> { static constexpr int KIND = LBM_RD2Q9; };
+template <> struct Lat<LBM_RD3Q27> : Lat3D<27> { static constexpr int KIND = LBM_RD3Q27; };
 
 // Index of the velocity opposite to j (every lattice here is symmetric under e -> -e).
 template <class L>
@@ -222,7 +229,13 @@ __host__ __device__ __forceinline__ void static_for(F&& f) {
 }
 
 // Host-side view of a lattice's velocity table (for generic, non-hot kernels and set-up).
-inline int lattice_dims(int kind) { return kind <= LBM_RD2Q25 ? 2 : 3; }
+inline int lattice_dims(int kind) { return (kind <= LBM_RD2Q25 || kind == LBM_RD2Q9) ? 2 : 3; }
+inline bool lattice_single(int kind) { return kind == LBM_RD2Q9 || kind == LBM_RD3Q27; }
+// rows of order <= 3: the paper's 10 (2D) or 20 (3D), without the d pure cubes on single-speed sets
+inline int lattice_r(int kind) {
+  const int d = lattice_dims(kind);
+  return (d == 2 ? 10 : 20) - (lattice_single(kind) ? d : 0);
+}
 inline int lattice_q(int kind) {
   switch (kind) {
     case LBM_RD2Q13: return 13;
@@ -232,6 +245,8 @@ inline int lattice_q(int kind) {
     case LBM_RD3Q33: return 33;
     case LBM_RD3Q45: return 45;
     case LBM_RD3Q53: return 53;
+    case LBM_RD2Q9: return 9;
+    case LBM_RD3Q27: return 27;
   }
   return 0;
 }
@@ -250,7 +265,10 @@ inline void lattice_pairs(int kind, int* plus) {
     if (opp > i) plus[n++] = i;
   }
 }
-inline int lattice_rmax(int kind) { return (kind == LBM_RD2Q17 || kind == LBM_RD2Q21 || kind == LBM_RD2Q25) ? 3 : 2; }
+inline int lattice_rmax(int kind) {
+  if (lattice_single(kind)) return 1;
+  return (kind == LBM_RD2Q17 || kind == LBM_RD2Q21 || kind == LBM_RD2Q25) ? 3 : 2;
+}
 
 constexpr int kMaxQ = 53;
 constexpr int kMaxR = 20;

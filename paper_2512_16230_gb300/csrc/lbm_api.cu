@@ -306,6 +306,8 @@ lbm_status dispatch_kind(int kind, F&& f) {
     case LBM_RD3Q33: return f(std::integral_constant<int, LBM_RD3Q33>{});
     case LBM_RD3Q45: return f(std::integral_constant<int, LBM_RD3Q45>{});
     case LBM_RD3Q53: return f(std::integral_constant<int, LBM_RD3Q53>{});
+    case LBM_RD2Q9: return f(std::integral_constant<int, LBM_RD2Q9>{});
+    case LBM_RD3Q27: return f(std::integral_constant<int, LBM_RD3Q27>{});
   }
   return set_error(LBM_ERR_ARG, "unknown lattice kind");
 }
@@ -339,8 +341,8 @@ lbm_status lbm_lattice_create(lbm_kind kind, const double* c, const double* cs2,
   try {
     if (!out || !c || !cs2) return set_error(LBM_ERR_ARG, "NULL argument");
     *out = nullptr;
-    if (int(kind) < LBM_RD2Q13 || int(kind) > LBM_RD3Q53) return set_error(LBM_ERR_ARG, "unknown lattice kind");
-    static const int kFree[7] = {0, 1, 3, 4, 0, 0, 1};
+    if (int(kind) < LBM_RD2Q13 || int(kind) > LBM_RD3Q27) return set_error(LBM_ERR_ARG, "unknown lattice kind");
+    static const int kFree[9] = {0, 1, 3, 4, 0, 0, 1, 0, 0};
     if (n_free != kFree[kind])
       return set_error(LBM_ERR_ARG, "lattice kind " + std::to_string(int(kind)) + " takes " +
                                         std::to_string(kFree[kind]) + " free weights");
@@ -351,7 +353,7 @@ lbm_status lbm_lattice_create(lbm_kind kind, const double* c, const double* cs2,
     L->kind = kind;
     L->d = lattice_dims(kind);
     L->Q = lattice_q(kind);
-    L->R = L->d == 2 ? 10 : 20;
+    L->R = lattice_r(kind);
     L->rmax = lattice_rmax(kind);
     for (int a = 0; a < L->d; ++a) {
       if (!(c[a] > 0.0) || !(cs2[a] > 0.0) || !std::isfinite(c[a]) || !std::isfinite(cs2[a])) {
@@ -507,6 +509,8 @@ lbm_status lbm_model_set_relaxation(lbm_model* m, const double* s, double s_high
 lbm_status lbm_model_set_bulk(lbm_model* m, double s_bulk) {
   if (!m) return set_error(LBM_ERR_ARG, "NULL model");
   if (m->eq != LBM_NSE) return set_error(LBM_ERR_ARG, "the bulk rate applies to the NSE model");
+  if (lattice_single(m->lat->kind) && s_bulk > 0.0)
+    return set_error(LBM_ERR_NOT_IMPLEMENTED, "the bulk block is read for the multispeed lattices (k = 0) only");
   if (!(s_bulk <= 2.0) || !std::isfinite(s_bulk)) return set_error(LBM_ERR_ARG, "bulk rate must be <= 2");
   m->s_bulk = s_bulk;
   batch_mark_dirty(m->batch);

@@ -118,7 +118,8 @@ __device__ __forceinline__ void raw_moments(const CT (&f)[L::Q], CT (&mu)[L::R])
 
 // Continuous raw moments of the NSE equilibrium (Eq. (M-NSEs-6a), Eq. (M-NSEs-6-1) with k = 0,
 // M30 = rho u u u, p = rho cs2_eq): M0 = rho, M1 = j, M2 = j u + p I,
-// M3 = j u u + p (u delta)_sym, for every monomial of the paper's row order.
+// M3 = j u u + p (u delta)_sym, for every monomial of the paper's row order. Single-speed
+// lattices (k = 1) take M30 = 0 and have no pure-cube rows.
 template <class L, class CT>
 __device__ __forceinline__ void eq_raw_nse(CT rho, const CT (&j)[3], const CT (&u)[3], CT P,
                                            CT (&me)[L::R]) {
@@ -135,7 +136,7 @@ __device__ __forceinline__ void eq_raw_nse(CT rho, const CT (&j)[3], const CT (&
       if constexpr (a0 == a1) me[K] = fma(j[a0], u[a1], P);
       else me[K] = j[a0] * u[a1];
     } else {
-      CT v = j[a0] * u[a1] * u[a2];
+      CT v = L::SINGLE ? CT(0) : j[a0] * u[a1] * u[a2];  // M30 = rho u u u (multispeed) or 0 (single speed)
       if constexpr (a1 == a2) v = fma(P, u[a0], v);
       if constexpr (a0 == a2) v = fma(P, u[a1], v);
       if constexpr (a0 == a1) v = fma(P, u[a2], v);

@@ -20,7 +20,8 @@ import numpy as np
 
 from . import build as _build
 
-KINDS = {"rD2Q13": 0, "rD2Q17": 1, "rD2Q21": 2, "rD2Q25": 3, "rD3Q33": 4, "rD3Q45": 5, "rD3Q53": 6}
+KINDS = {"rD2Q13": 0, "rD2Q17": 1, "rD2Q21": 2, "rD2Q25": 3, "rD3Q33": 4, "rD3Q45": 5, "rD3Q53": 6,
+         "rD2Q9": 7, "rD3Q27": 8}
 DTYPES = {"f64": 0, "f32": 1, "bf16_dev": 2, "f16_dev": 3}
 COMPUTE_OF = {"f64": "f64", "f32": "f32", "bf16_dev": "f32", "f16_dev": "f32"}
 EQS = {"nse": 0, "ncde": 1}

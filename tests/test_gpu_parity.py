@@ -418,3 +418,29 @@ def test_ncde_variant_errors():
     m.set_ncde_variant("moment", 0.3)     # the moment variant (with a1) stays batchable
     b.remove(m)
     b.close()
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("lattice,n", [("rD2Q9", (64, 48)), ("rD3Q27", (24, 24, 18))])
+def test_single_speed_taylor_green(lattice, n, store):
+    """Single-speed rectangular lattices (k = 1) with the per-axis normal rates of Eq. (4-29):
+    a Taylor-Green vortex over 100 steps against the FP64 oracle."""
+    if len(n) == 2:
+        wl = W.taylor_green_2d(n=n, steps=100, store=store, lattice=lattice)
+    else:
+        wl = W.taylor_green_3d(n=n, steps=100, store=store, re=100.0, ma=0.1, lattice=lattice)
+    om, gm = workload_pair(wl)
+    om.step(wl.steps)
+    gm.step(wl.steps)
+    r_g, u_g = gm.read_fields()
+    r_o, u_o = om.fields()
+    assert rel_l2(u_g, u_o) <= TOL[store]
+    assert rel_l2(r_g, r_o) <= TOL[store]
+
+
+def test_single_speed_rejects_bulk_block():
+    from paper_2512_16230_gb300 import lbm
+    spec = W.LATTICES["rD2Q9"]
+    gm = gpu_model(spec, "nse", (8, 8), np.ones(spec.R), store="f32")
+    with pytest.raises(lbm.LBMError, match="NOT_IMPLEMENTED"):
+        gm.set_bulk(1.2)

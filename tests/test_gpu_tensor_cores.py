@@ -43,7 +43,7 @@ def _pair(name, eq, store, seed):
 
 @pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
 @pytest.mark.parametrize("eq", ["nse", "ncde"])
-@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q17", "rD2Q25", "rD3Q33", "rD3Q45", "rD3Q53"])
+@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q17", "rD2Q25", "rD3Q33", "rD3Q45", "rD3Q53", "rD2Q9", "rD3Q27"])
 def test_tensor_core_step_against_oracle(name, eq, store):
     """One step on tcgen05 from stored deviations: the new deviations f - w agree with the FP64
     oracle (fed the same stored values) within the rounding of input and output."""
@@ -131,7 +131,7 @@ HIGH_RATES = {4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25}
 
 
 @pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
-@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q25", "rD3Q33", "rD3Q45", "rD3Q53"])
+@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q25", "rD3Q33", "rD3Q45", "rD3Q53", "rD2Q9", "rD3Q27"])
 def test_tensor_core_high_order_rates_step(name, store):
     """The full Q x Q collision with one rate per order >= 4 on tcgen05 (the higher rows join both
     products): one step against the FP64 oracle with the same per-order rates, within the
