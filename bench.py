@@ -200,23 +200,35 @@ def cpu_baseline_worker(nx, ny, nz, steps):
     print(json.dumps({"mlups": nx * ny * nz * steps / dt / 1e6, "seconds": dt}))
 
 
-def run_cpu_baseline(threads=None):
-    threads = threads or os.cpu_count() or 1
+def _oracle_timing(threads, grid, steps):
     env = dict(os.environ)
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[var] = str(threads)
     env.pop("CUDA_VISIBLE_DEVICES", None)
     code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
-            f"bench.cpu_baseline_worker({CPU_SAMPLE_GRID[0]}, {CPU_SAMPLE_GRID[1]}, {CPU_SAMPLE_GRID[2]}, "
-            f"{CPU_SAMPLE_STEPS})")
+            f"bench.cpu_baseline_worker({grid[0]}, {grid[1]}, {grid[2]}, {steps})")
     res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
     if res.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": threads, "kind": "oracle", "error": res.stderr[-500:]}
-    out = json.loads(res.stdout.strip().splitlines()[-1])
+        return None, res.stderr[-500:]
+    return json.loads(res.stdout.strip().splitlines()[-1]), None
+
+
+def run_cpu_baseline(threads=None):
+    """The oracle on all host cores (the reported baseline) and, on a sixteenth of the slab, on one
+    core (BLAS threads = 1)."""
+    threads = threads or os.cpu_count() or 1
+    out, err = _oracle_timing(threads, CPU_SAMPLE_GRID, CPU_SAMPLE_STEPS)
+    if out is None:
+        return {"value": None, "unit": UNIT, "cores": threads, "kind": "oracle", "error": err}
+    one_grid = (CPU_SAMPLE_GRID[0] // 4, CPU_SAMPLE_GRID[1] // 4, CPU_SAMPLE_GRID[2])
+    one, _ = _oracle_timing(1, one_grid, CPU_SAMPLE_STEPS)
     return {"value": out["mlups"], "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": (f"FP64 numpy oracle, {CPU_SAMPLE_STEPS} steps of the same rD3Q53 Taylor-Green workload on a "
                        f"{CPU_SAMPLE_GRID[0]}x{CPU_SAMPLE_GRID[1]}x{CPU_SAMPLE_GRID[2]} periodic slab of the benchmark "
-                       f"grid ({out['seconds']:.1f} s; BLAS threads = cores)")}
+                       f"grid ({out['seconds']:.1f} s; BLAS threads = cores)"),
+            "single_core": None if one is None else {
+                "value": one["mlups"], "unit": UNIT, "cores": 1,
+                "sample": f"{CPU_SAMPLE_STEPS} steps on {one_grid[0]}x{one_grid[1]}x{one_grid[2]} ({one['seconds']:.1f} s)"}}
 
 
 def reference_worker(steps, warmup, budget_s):
