@@ -175,12 +175,13 @@ lbm_status lbm_model_create(const lbm_lattice* lat, lbm_eq eq, const int64_t* n,
 lbm_status lbm_model_set_relaxation(lbm_model* m, const double* s, double s_high);
 
 /* Independent bulk viscosity (NSE): the normal second-order moments relax with the inverse of
- * S2^(1) = diag(1/s_sa) + a 1^T / d, a_a = 1/s_bulk - 1/s_sa (Eq. (4-27) read for the multispeed
- * lattices, k = 0), where s_sa are the rates set for the normal rows c_a^2 - c_sa^2; then
- * mu = (1/s_s - 1/2) p dt and mu_b = (2/d)(1/s_bulk - 1/2) p dt (Eq. (4-29)). The same block
- * enters (I - S2/2) M2G. s_bulk <= 0 restores the diagonal relaxation (mu_b = 2 mu / d).
- * Errors: LBM_ERR_ARG, LBM_ERR_NOT_IMPLEMENTED (a single-speed lattice: the block is read for the
- * multispeed lattices, k = 0). */
+ * S2^(1) = diag(1/s_sa) + a b^T / d (Eq. (4-27)), where s_sa are the rates set for the normal rows
+ * c_a^2 - c_sa^2. Multispeed lattices (k = 0): a_a = 1/s_bulk - 1/s_sa, b = 1, so that
+ * mu = (1/s_s - 1/2) p dt and mu_b = (2/d)(1/s_bulk - 1/2) p dt (Eq. (4-29)). Single-speed
+ * lattices (k = 1): a_a = (1/s_bulk - 1/s_sa)(c_a^2 - cs2_eq), b_b = 1/(c_b^2 - cs2_eq) as printed,
+ * so that a longitudinal wave along a sees (c_a^2 - cs2_eq)((1/s_sa - 1/2) + (1/s_bulk - 1/s_sa)/d).
+ * The same block enters (I - S2/2) M2G. s_bulk <= 0 restores the diagonal relaxation.
+ * Errors: LBM_ERR_ARG. */
 lbm_status lbm_model_set_bulk(lbm_model* m, double s_bulk);
 
 /* Rates of the rows of order >= 4, one per order (Eq. (H-MRT-LB) with the full Q x Q Hermite

@@ -33,8 +33,9 @@ Readings of points the paper leaves open (each is listed in the design notes):
 * rows of order >= 4 (left to the designer by the paper) relax with one shared rate s_high, or
   with ``s_orders`` one rate per order k on the graded block: the W-orthogonal complement of the
   lower orders inside the lattice functions spanned by the monomials of degree <= k.
-* bulk viscosity (Eq. (4-27), k = 0): with ``s_bulk`` the normal second-order rows relax through
-  the inverse of S2^(1) = diag(1/s_s) + (1/s_b - 1/s_s) 1 1^T / d.
+* bulk viscosity (Eq. (4-27)): with ``s_bulk`` the normal second-order rows relax through
+  the inverse of S2^(1) = diag(1/s_s) + a b^T / d, with a = 1/s_b - 1/s_s, b = 1 on the
+  multispeed lattices (k = 0) and the printed (c_a^2 - c_s^2) factors on the single-speed ones.
 
 Arrays use the grid in C order with x fastest: a field has shape (n_z, n_y, n_x) in 3D and
 (n_y, n_x) in 2D; populations have a leading Q axis; velocity fields a leading d axis (u[0]=u_x).
@@ -178,8 +179,6 @@ class Model:
         self.normal = [r for r, p in enumerate(self.lat.polys)
                        if self.lat.orders[r] == 2 and max(max(p, key=sum)) == 2]
         if self.s_bulk is not None:
-            if self.lat.kind in L.SINGLE_SPEED:
-                raise ValueError("the bulk block of Eq. (4-27) is read for the multispeed lattices (k = 0) only")
             S[np.ix_(self.normal, self.normal)] = self.normal_block()
         self.S = S
         self.Hinv = L.hermite_inverse(self.lat)
@@ -189,14 +188,20 @@ class Model:
             self.u_const = np.asarray(self.u_const, dtype=np.float64)
 
     def normal_block(self):
-        """Eq. (4-27) with k = 0: the relaxation of the normal second moments is the inverse of
-        S2^(1) = diag(1/s_sa) + a b^T / d with a_a = 1/s_b - 1/s_sa and b = 1, so that the trace
-        relaxes with s_b and the deviatoric part with s_s (Eq. (4-29): mu = (1/s_s - 1/2) p dt,
-        mu_b = (2/d)(1/s_b - 1/2) p dt)."""
+        """Eq. (4-27): the relaxation of the normal second moments is the inverse of
+        S2^(1) = diag(1/s_sa) + a b^T / d. Multispeed lattices (k = 0): a_a = 1/s_b - 1/s_sa and
+        b = 1, so that the trace relaxes with s_b and the deviatoric part with s_s (Eq. (4-29):
+        mu = (1/s_s - 1/2) p dt, mu_b = (2/d)(1/s_b - 1/2) p dt). Single-speed lattices (k = 1):
+        a_a = (1/s_b - 1/s_sa)(c_a^2 - c_s^2) and b_b = 1/(c_b^2 - c_s^2) as printed, c_s^2 = cs2_eq,
+        because there the normal moments are driven by (c_a^2 - c_s^2) rho d_a u_a."""
         d = self.lat.d
         ss = self.s[self.normal]
-        a = 1.0 / self.s_bulk - 1.0 / ss
-        return np.linalg.inv(np.diag(1.0 / ss) + np.outer(a, np.ones(d)) / d)
+        if self.lat.kind in L.SINGLE_SPEED:
+            D = self.lat.c ** 2 - self.cs2_eq
+        else:
+            D = np.ones(d)
+        a = (1.0 / self.s_bulk - 1.0 / ss) * D
+        return np.linalg.inv(np.diag(1.0 / ss) + np.outer(a, 1.0 / D) / d)
 
     # -- body force ---------------------------------------------------------------------------
     def force_field(self):

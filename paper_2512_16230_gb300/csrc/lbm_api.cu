@@ -52,10 +52,15 @@ void make_step_params(const lbm_model* m, StepParams<CT>* p) {
     }
     double Sn[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     if (m->s_bulk > 0.0 && m->eq == LBM_NSE) {
+      // k = 1 (single-speed lattices): a_a = (1/s_b - 1/s_sa)(c_a^2 - c_s^2), b_b = 1/(c_b^2 - c_s^2)
+      double Dk[3] = {1.0, 1.0, 1.0};
+      if (lattice_single(L->kind))
+        for (int a = 0; a < d; ++a) Dk[a] = L->c[a] * L->c[a] - m->cs2_eq;
       double A[3][6];  // [M | I] Gauss-Jordan
       for (int i = 0; i < d; ++i)
         for (int j = 0; j < d; ++j) {
-          A[i][j] = (i == j ? 1.0 / m->s[rows[i]] : 0.0) + (1.0 / m->s_bulk - 1.0 / m->s[rows[i]]) / d;
+          A[i][j] = (i == j ? 1.0 / m->s[rows[i]] : 0.0) +
+                    (1.0 / m->s_bulk - 1.0 / m->s[rows[i]]) * Dk[i] / Dk[j] / d;
           A[i][d + j] = i == j ? 1.0 : 0.0;
         }
       for (int c = 0; c < d; ++c) {
@@ -509,8 +514,6 @@ lbm_status lbm_model_set_relaxation(lbm_model* m, const double* s, double s_high
 lbm_status lbm_model_set_bulk(lbm_model* m, double s_bulk) {
   if (!m) return set_error(LBM_ERR_ARG, "NULL model");
   if (m->eq != LBM_NSE) return set_error(LBM_ERR_ARG, "the bulk rate applies to the NSE model");
-  if (lattice_single(m->lat->kind) && s_bulk > 0.0)
-    return set_error(LBM_ERR_NOT_IMPLEMENTED, "the bulk block is read for the multispeed lattices (k = 0) only");
   if (!(s_bulk <= 2.0) || !std::isfinite(s_bulk)) return set_error(LBM_ERR_ARG, "bulk rate must be <= 2");
   m->s_bulk = s_bulk;
   batch_mark_dirty(m->batch);

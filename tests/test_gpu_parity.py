@@ -245,7 +245,7 @@ def test_steps_are_deterministic():
 
 
 @pytest.mark.parametrize("store", ["f64", "f32"])
-@pytest.mark.parametrize("name", ["rD2Q25", "rD2Q13", "rD3Q53", "rD3Q45", "rD3Q53-aniso"])
+@pytest.mark.parametrize("name", ["rD2Q25", "rD2Q13", "rD3Q53", "rD3Q45", "rD3Q53-aniso", "rD2Q9", "rD3Q27"])
 def test_bulk_viscosity_step(name, store):
     """Independent bulk viscosity (Eq. (4-27), k = 0): the normal second-order block of S couples
     the rows through s_b, also inside (I - S2/2) M2G (body force on)."""
@@ -438,9 +438,3 @@ def test_single_speed_taylor_green(lattice, n, store):
     assert rel_l2(r_g, r_o) <= TOL[store]
 
 
-def test_single_speed_rejects_bulk_block():
-    from paper_2512_16230_gb300 import lbm
-    spec = W.LATTICES["rD2Q9"]
-    gm = gpu_model(spec, "nse", (8, 8), np.ones(spec.R), store="f32")
-    with pytest.raises(lbm.LBMError, match="NOT_IMPLEMENTED"):
-        gm.set_bulk(1.2)

@@ -724,3 +724,64 @@ def test_single_speed_taylor_green_needs_axis_rates():
     good, bad = _single_speed_tgv_rate(True), _single_speed_tgv_rate(False)
     assert abs(good - 1) < 1e-2
     assert abs(bad - 1) > 5e-2
+
+
+def _single_speed_sound_bulk(axis, s_n=1.5, s_b=1.0, nsteps=400):
+    c, cs2 = (1.0, 4.0 / 3.0), (1.0 / 3.0, 1.0 / 3.0)
+    lat = L.build("rD2Q9", c, cs2)
+    s = np.ones(lat.R)
+    s[[3, 5]] = s_n
+    n = (48, 4) if axis == 0 else (4, 36)
+    m = M.Model(lat, "nse", n, s, 1.0, s_bulk=s_b)
+    xs = I.coords(n, c)
+    k = 2 * math.pi / (n[axis] * c[axis])
+    m.init_fields(1.0 + 1e-4 * np.cos(k * xs[axis]), np.zeros((2,) + xs[0].shape))
+
+    def energy():
+        r, u = m.fields()
+        return np.sum((r - 1.0) ** 2 * cs2[0] + r * (u ** 2).sum(0))
+
+    m.step(40)
+    e0 = energy()
+    m.step(nsteps)
+    gamma = math.log(e0 / energy()) / nsteps / 2
+    nu_long = (c[axis] ** 2 - cs2[0]) * ((1.0 / s_n - 0.5) + (1.0 / s_b - 1.0 / s_n) / 2)
+    return gamma / (k * k * nu_long / 2)
+
+
+def test_single_speed_bulk_block_k1():
+    """Eq. (4-27) with the printed a_a = (1/s_b - 1/s_sa)(c_a^2 - c_s^2), b_b = 1/(c_b^2 - c_s^2)
+    (k = 1): on rectangular rD2Q9 a sound wave along a is damped with the longitudinal viscosity
+    (c_a^2 - c_s^2)((1/s_n - 1/2) + (1/s_b - 1/s_n)/d), along both axes (2%)."""
+    rx, ry = _single_speed_sound_bulk(0), _single_speed_sound_bulk(1)
+    assert abs(rx - 1) < 2e-2 and abs(ry - 1) < 2e-2
+
+
+@pytest.mark.parametrize("s_n,s_b", [(1.5, 1.0), (1.2, 1.8)])
+def test_single_speed_bulk_block_stress(s_n, s_b):
+    """The printed factors of Eq. (4-27) matter only off the diagonal: for a compression wave along
+    y on rectangular rD2Q9 the non-equilibrium normal moments follow the first-order relation
+    M2^ne = -dt S2^(1) (d_t M2 + div M3) with d_t M2_aa + div M3_aa = rho (c_a^2 - c_s^2) d_a u_a,
+    i.e. M2^ne_yy = -(c_y^2 - c_s^2)(1/s_n + (1/s_b - 1/s_n)/d) d_y u_y and
+    M2^ne_xx = -(1/s_b - 1/s_n)(c_x^2 - c_s^2) d_y u_y / d (0.1%, measured at peak velocity). Without
+    the factors M2^ne_xx would carry c_y^2 - c_s^2 instead (2.17 times larger)."""
+    c, cs2 = (1.0, 4.0 / 3.0), (1.0 / 3.0, 1.0 / 3.0)
+    lat = L.build("rD2Q9", c, cs2)
+    s = np.ones(lat.R)
+    s[[3, 5]] = s_n
+    n = (4, 96)
+    m = M.Model(lat, "nse", n, s, 1.0, s_bulk=s_b)
+    xs = I.coords(n, c)
+    ky = 2 * math.pi / (n[1] * c[1])
+    m.init_fields(1.0 + 1e-4 * np.cos(ky * xs[1]), np.zeros((2,) + xs[0].shape))
+    m.step(int(round(math.pi / 2 / (math.sqrt(cs2[0]) * ky))))
+    rho, u = m.fields()
+    fne = m.f - m.equilibrium(rho, u)
+    mxx = np.tensordot(lat.cvel[:, 0] ** 2, fne, axes=(0, 0))[:, 0]
+    myy = np.tensordot(lat.cvel[:, 1] ** 2, fne, axes=(0, 0))[:, 0]
+    kk = 2 * np.pi * np.fft.fftfreq(n[1], d=c[1])
+    duy = np.real(np.fft.ifft(1j * kk * np.fft.fft(u[1][:, 0])))
+    D = np.array([c[0] ** 2 - cs2[0], c[1] ** 2 - cs2[0]])
+    fit = lambda a, b: float(np.dot(a, b) / np.dot(b, b))
+    assert abs(fit(myy, -D[1] * (1 / s_n + (1 / s_b - 1 / s_n) / 2) * duy) - 1) < 1e-3
+    assert abs(fit(mxx, -(1 / s_b - 1 / s_n) * D[0] * duy / 2) - 1) < 1e-3
