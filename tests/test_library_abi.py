@@ -41,3 +41,23 @@ def test_missing_library_fails_loudly(tmp_path):
             lbm.load(str(tmp_path / "nope.so"))
     finally:
         lbm._lib = saved
+
+
+def _header_enum(name):
+    """name -> value of the enumerators of the C typedef enum ``name`` in the header."""
+    import re
+    text = open(lbm.HEADER).read()
+    body = re.search(r"typedef enum \{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"(LBM_\w+)\s*=\s*(\d+)", body)}
+
+
+def test_binding_enums_match_the_header():
+    """The ctypes binding passes enum values by number: they must be the header's."""
+    kinds = _header_enum("lbm_kind")
+    assert {("LBM_" + k.upper()): v for k, v in lbm.KINDS.items()} == kinds
+    dtypes = _header_enum("lbm_dtype")
+    assert {"LBM_" + k.upper(): v for k, v in lbm.DTYPES.items()} == dtypes
+    assert {"LBM_" + k.upper(): v for k, v in lbm.EQS.items()} == _header_enum("lbm_eq")
+    assert {"LBM_NCDE_" + k.upper(): v for k, v in lbm.NCDE_VARIANTS.items()} == _header_enum("lbm_ncde_variant")
+    assert {v: k for k, v in _header_enum("lbm_status").items()} == lbm.STATUS
