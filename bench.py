@@ -375,18 +375,28 @@ def bench_ours(args):
     e2e_value = job_throughput(cells, args.steps, ws, reduce_max(e2e_s, ws, dev))
     io_bytes = (rho_h.numel() + u_h.numel()) * 8
 
-    # the full Q x Q collision with one rate per order >= 4 (k_step_high) on the same solve
+    # the full Q x Q collision with one rate per order >= 4 on the same solve: the CUDA-core
+    # kernel with explicit higher rows (k_step_high), then the higher rows on tcgen05
     model.set_high_rates([HIGH_RATES[k] for k in sorted(HIGH_RATES)])
-    model.step(3)
     vsteps = min(args.steps, VARIANT_STEPS)
     v0 = torch.cuda.Event(enable_timing=True)
     v1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    v0.record(stream)
-    model.step(vsteps)
-    v1.record(stream)
-    barrier()
-    high_ms = v0.elapsed_time(v1) / vsteps
+
+    def time_steps(mdl):
+        mdl.step(3)
+        barrier()
+        v0.record(stream)
+        mdl.step(vsteps)
+        v1.record(stream)
+        barrier()
+        return v0.elapsed_time(v1) / vsteps
+
+    model.set_tensor_cores(0)
+    high_ms = time_steps(model)
+    high_tc_ms = None
+    if args.store != "f64":
+        model.set_tensor_cores(1)
+        high_tc_ms = time_steps(model)
 
     if rank == 0:
         peak, peak_src = _peaks()
@@ -421,6 +431,12 @@ def bench_ours(args):
                     "rates": {str(k): v for k, v in HIGH_RATES.items()}, "steps": vsteps,
                     "ms_per_step": high_ms, "mlups": cells / high_ms / 1e3,
                     "hbm_frac": algo_bytes / (high_ms / 1e3) / 1e9 / peak},
+                "high_order_rates_tensor_cores": None if high_tc_ms is None else {
+                    "kernel": "k_step_tc32_high<rD3Q53, NSE> (CUDA-core reduced form + higher rows on tcgen05, "
+                              "FP16 high/low splits)",
+                    "rates": {str(k): v for k, v in HIGH_RATES.items()}, "steps": vsteps,
+                    "ms_per_step": high_tc_ms, "mlups": cells / high_tc_ms / 1e3,
+                    "hbm_frac": algo_bytes / (high_tc_ms / 1e3) / 1e9 / peak},
             },
         }
         if cpu is not None:
@@ -433,13 +449,7 @@ def bench_ours(args):
     m16.set_relaxation(wl.s, wl.s_high)
     m16.set_high_rates([HIGH_RATES[k] for k in sorted(HIGH_RATES)])
     m16.init_fields(rho_d, u_d)
-    m16.step(3)
-    barrier()
-    v0.record(stream)
-    m16.step(vsteps)
-    v1.record(stream)
-    barrier()
-    high16_ms = v0.elapsed_time(v1) / vsteps
+    high16_ms = time_steps(m16)
     m16.close()
     del m16
     torch.cuda.empty_cache()

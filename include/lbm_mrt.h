@@ -194,20 +194,23 @@ lbm_status lbm_model_set_bulk(lbm_model* m, double s_bulk);
  *         LBM_ERR_NOT_IMPLEMENTED (the model is in a batch). */
 lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_orders);
 
-/* Tensor-core collision for 16-bit deviation storage (BF16_DEV / F16_DEV): the two contractions
+/* Tensor-core (tcgen05) collision. For 16-bit deviation storage (BF16_DEV / F16_DEV) the two contractions
  * of the Hermite-moment collision (Eq. (H-MRT-LB-1)) run as tcgen05 matrix products over tiles
  * of 128 cells with the integer monomial table mono_k(e_i) as the other operand (exact in 16 bits);
  * the per-cell moment-space arithmetic stays in FP32. enable = 0 selects the CUDA-core kernel.
  * With distinct rates for the orders >= 4 (lbm_model_set_high_rates) the higher rows join both
- * products as dense 16-bit operands (the full Q x Q collision). Default, until this is called:
- * the tensor cores for 16-bit storage with distinct higher-order rates (there they are the faster
- * kernel), the CUDA cores otherwise.
+ * products as dense 16-bit operands (the full Q x Q collision). On FP32 storage only those
+ * higher rows run on the tensor cores, as FP16 high/low splits of per-cell power-of-two scaled
+ * operands (three products per contraction, about 22 bits), next to the CUDA-core reduced form;
+ * without per-order rates FP32 storage always uses the CUDA-core kernel. Default, until this is
+ * called: the tensor cores with distinct higher-order rates (there they are the faster kernel),
+ * the CUDA cores otherwise.
  * Device-side waits are bounded; a timeout is latched in the model's status word and returned as
  * LBM_ERR_TIMEOUT by the next lbm_model_synchronize / read / get / sums call.
  * enable = 2 is a test hook for that path: the kernel issues no matrix product, every wait runs
  * out after a short limit, the CTAs free their tensor memory and return, and the populations
  * are left undefined.
- * Errors: LBM_ERR_ARG (storage is not 16-bit, enable not in {0, 1, 2}). */
+ * Errors: LBM_ERR_ARG (FP64 storage, enable not in {0, 1, 2}). */
 lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable);
 
 /* Equation of state p = rho * cs2_eq (NSE, Eq. (M-NSEs-6-1)) or the prefactor of the diffusion

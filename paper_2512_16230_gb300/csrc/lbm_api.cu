@@ -492,7 +492,7 @@ lbm_status lbm_model_create(const lbm_lattice* L, lbm_eq eq, const int64_t* n, l
     m->cs2_eq = L->cs2[0];
     m->rho_ref = eq == LBM_NSE ? 1.0 : 0.0;
     m->force_b = -1;
-    m->tc_auto = store == LBM_BF16_DEV || store == LBM_F16_DEV;
+    m->tc_auto = store != LBM_F64;
     *out = m;
     return LBM_OK;
   } catch (...) {
@@ -546,8 +546,8 @@ lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_o
 lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable) {
   if (!m) return set_error(LBM_ERR_ARG, "NULL model");
   if (enable < 0 || enable > 2) return set_error(LBM_ERR_ARG, "enable must be 0, 1 or 2");
-  if (enable && m->store != LBM_BF16_DEV && m->store != LBM_F16_DEV)
-    return set_error(LBM_ERR_ARG, "the tensor-core collision needs 16-bit deviation storage");
+  if (enable && m->store == LBM_F64)
+    return set_error(LBM_ERR_ARG, "the tensor-core collision needs FP32 or 16-bit deviation storage");
   m->tensor_cores = enable != 0;
   m->tc_no_issue = enable == 2;
   m->tc_auto = false;

@@ -60,7 +60,7 @@ struct lbm_model {
   int ncde_variant;  // lbm_ncde_variant
   double a1;         // mixed-derivative coefficient A1 = a1 I (Eq. (GNCDE))
   bool tensor_cores; // 16-bit storage: contractions on tcgen05 (k_step_tc)
-  bool tc_auto;      // no explicit choice yet: tcgen05 for 16-bit storage with per-order rates
+  bool tc_auto;      // no explicit choice yet: tcgen05 with per-order rates (FP32 or 16-bit storage)
   bool tc_no_issue;  // test hook: k_step_tc issues no matrix product, so its waits run out
   int* status;       // device status word: non-zero after a device-side wait ran out
   int64_t steps, launches;

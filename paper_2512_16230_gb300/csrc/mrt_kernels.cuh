@@ -848,9 +848,10 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
   const bool high = collide_on && has_high_rates(m);
   HighParams<CT> hp;
   if (high) make_high_params<CT>(m, &hp);
-  // tcgen05 when asked for, and by default for 16-bit storage with per-order rates (where the
-  // dense higher rows make it the faster kernel)
+  // tcgen05 when asked for, and by default with per-order rates (where the dense higher rows make
+  // it the faster kernel); on FP32 storage only the higher rows go to the tensor cores
   [[maybe_unused]] const bool tensor = collide_on && (m->tensor_cores || (m->tc_auto && high));
+  [[maybe_unused]] const bool tensor32 = std::is_same<ST, float>::value && tensor && high;
   TcParams tp;
   int tgrid = 0;
   size_t tsmem = 0;
@@ -876,6 +877,15 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
       }
     }
   }
+  if constexpr (std::is_same<ST, float>::value) {
+    if (tensor32) {
+      make_tc_params(m, &tp);
+      tsmem = sizeof(Tc32Smem<L>);
+      const void* k = m->eq == LBM_NSE ? reinterpret_cast<const void*>(k_step_tc32_high<L, LBM_NSE>)
+                                       : reinterpret_cast<const void*>(k_step_tc32_high<L, LBM_NCDE>);
+      tgrid = tc_grid(m, tp.ntiles, k, 3, tsmem);
+    }
+  }
   for (int64_t s = 0; s < nsteps; ++s) {
     const ST* fin = static_cast<const ST*>(m->f[m->cur]);
     ST* fout = static_cast<ST*>(m->f[m->cur ^ 1]);
@@ -893,6 +903,15 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
           else
             k_step_tc<L, ST, LBM_NCDE, false><<<tgrid, 128, tsmem, m->stream>>>(p, tp, fin, fout, phi);
         }
+        done = true;
+      }
+    }
+    if constexpr (std::is_same<ST, float>::value) {
+      if (tensor32) {
+        if (m->eq == LBM_NSE)
+          k_step_tc32_high<L, LBM_NSE><<<tgrid, 128, tsmem, m->stream>>>(p, tp, fin, fout, phi);
+        else
+          k_step_tc32_high<L, LBM_NCDE><<<tgrid, 128, tsmem, m->stream>>>(p, tp, fin, fout, phi);
         done = true;
       }
     }

@@ -315,11 +315,14 @@ def test_high_rows_need_nonzero_weights():
 HIGH_RATES = {4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25}
 
 
-@pytest.mark.parametrize("store", ["f64", "f32"])
-@pytest.mark.parametrize("name", ["rD2Q25", "rD2Q17", "rD2Q13", "rD3Q53", "rD3Q45", "rD3Q33", "rD3Q53-aniso"])
-def test_high_order_rates_step(name, store):
-    """The full Q x Q collision with one rate per order >= 4 (explicit higher rows in the kernel)
-    against the oracle's Lambda = H^{-1} S H with the same per-order rates, body force on."""
+@pytest.mark.parametrize("store,tensor", [("f64", 0), ("f32", 0), ("f32", 1)])
+@pytest.mark.parametrize("name", ["rD2Q25", "rD2Q17", "rD2Q13", "rD3Q53", "rD3Q45", "rD3Q33", "rD3Q53-aniso",
+                                  "rD2Q9", "rD3Q27"])
+def test_high_order_rates_step(name, store, tensor):
+    """The full Q x Q collision with one rate per order >= 4 against the oracle's
+    Lambda = H^{-1} S H with the same per-order rates, body force on: the CUDA-core kernel with
+    explicit higher rows (tensor = 0) and, on FP32, the higher rows on tcgen05 as FP16 high/low
+    splits next to the CUDA-core reduced form (tensor = 1, the default with per-order rates)."""
     spec = ALL_SPECS[name]
     d = spec.d
     n = RAGGED[d]
@@ -327,6 +330,8 @@ def test_high_order_rates_step(name, store):
     kw = dict(s_high=1.15, force=(d - 1, 0, 2e-3, 1, 0.1), s_orders=HIGH_RATES)
     om = oracle_model(spec, "nse", n, s, **kw)
     gm = gpu_model(spec, "nse", n, s, store=store, **kw)
+    if store != "f64":
+        gm.set_tensor_cores(tensor)
     f0 = round_to_store(I.random_populations(n, om.lat.Q, seed=23), store)
     om.set_populations(f0)
     gm.set_populations(f0)

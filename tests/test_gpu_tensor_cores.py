@@ -119,10 +119,10 @@ def test_tensor_core_timeout_is_reported():
     assert np.allclose(rho, 1.0, atol=1e-3) and np.abs(u).max() < 1e-3
 
 
-def test_tensor_cores_need_16bit_storage():
+def test_tensor_cores_not_for_fp64():
     from paper_2512_16230_gb300 import lbm
     spec = W.LATTICES["rD2Q13"]
-    gm = gpu_model(spec, "nse", (8, 8), np.ones(spec.R), store="f32")
+    gm = gpu_model(spec, "nse", (8, 8), np.ones(spec.R), store="f64")
     with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
         gm.set_tensor_cores(1)
 
