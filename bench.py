@@ -459,6 +459,9 @@ def bench_ours(args):
             "rates": {str(k): v for k, v in HIGH_RATES.items()}, "steps": vsteps,
             "ms_per_step": high16_ms, "mlups": cells / high16_ms / 1e3,
             "hbm_frac": 2 * Q * 2 * cells / (high16_ms / 1e3) / 1e9 / peak}
+    other = run_other_configs(lbm, W_stream=stream, barrier=barrier)
+    if rank == 0:
+        line["other_configs"] = other
     if args.serving_requests > 0:
         serving = run_serving(args.serving_requests)
         if rank == 0:
@@ -468,6 +471,45 @@ def bench_ours(args):
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_other_configs(lbm, W_stream, barrier):
+    """The smaller configurations at full size, timed the same way (CUDA events over a run of
+    steps): the rD2Q13 nonlinear CDE hill (1024 x 768, FP32 and FP64, the full 5000 steps; 104 or
+    208 B of populations plus 8 or 16 B of phi history per cell update) and the rD2Q25
+    Taylor-Green vortex (64 x 48, FP64, 200 steps; 1.2 MB of state, resident in L2, so not an HBM
+    measurement)."""
+    import numpy as np
+    import torch
+    from paper_2512_16230_gb300 import workloads as W
+    peak, _ = _peaks()
+    out = {}
+    cases = [("ncde_hill_rD2Q13_1024x768_f32", W.ncde_hill(store="f32"), 4),
+             ("ncde_hill_rD2Q13_1024x768_f64", W.ncde_hill(store="f64"), 8),
+             ("taylor_green_rD2Q25_64x48_f64", W.taylor_green_2d(), 8)]
+    for name, wl, nbytes in cases:
+        spec = wl.lattice
+        lat = lbm.Lattice(spec.kind, spec.c, spec.cs2, spec.free_w)
+        m = lbm.Model(lat, wl.eq, wl.n, store=wl.store, stream=W_stream.cuda_stream)
+        m.set_relaxation(wl.s, wl.s_high)
+        if wl.u_const is not None:
+            m.set_ncde(wl.u_const, wl.nonlin)
+        rho, u = wl.fields()
+        m.init_fields(rho, None if u is None else np.ascontiguousarray(u))
+        m.step(10)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        a.record(W_stream)
+        m.step(wl.steps)
+        b.record(W_stream)
+        barrier()
+        ms = a.elapsed_time(b) / wl.steps
+        per_cell = 2 * lat.Q * nbytes + (2 * nbytes if wl.eq == "ncde" else 0)
+        out[name] = {"steps": wl.steps, "ms_per_step": ms, "mlups": wl.ncells / ms / 1e3,
+                     "algorithmic_bytes_per_cell": per_cell,
+                     "hbm_frac": per_cell * wl.ncells / (ms / 1e3) / 1e9 / peak}
+        m.close()
+    return out
 
 
 def run_serving(n_requests, rate_per_s=20.0, seed=0):
