@@ -33,6 +33,12 @@ Readings of points the paper leaves open (each is listed in the design notes):
 * rows of order >= 4 (left to the designer by the paper) relax with one shared rate s_high, or
   with ``s_orders`` one rate per order k on the graded block: the W-orthogonal complement of the
   lower orders inside the lattice functions spanned by the monomials of degree <= k.
+* the anisotropy term of Eq. (M2Ga) on the single-speed lattices (``m2g_aniso``): the bracket
+  of M2G gains (delta4 . u) . grad rho, which is diagonal, (c_a^2 - 3 cs2_eq) u_a d_a rho on the
+  normal row of axis a (delta4_aaaa = c_a^2 - 3 c_s^2, zero elsewhere, Sec. 3.4). grad rho is
+  the second-order central difference, over the cell spacing c_a dt, of the density of the
+  previous step; the first step after init_fields / set_populations takes the density of that
+  state (rho^{-1} = rho^0, as for phi).
 * bulk viscosity (Eq. (4-27)): with ``s_bulk`` the normal second-order rows relax through
   the inverse of S2^(1) = diag(1/s_s) + a b^T / d, with a = 1/s_b - 1/s_s, b = 1 on the
   multispeed lattices (k = 0) and the printed (c_a^2 - c_s^2) factors on the single-speed ones.
@@ -164,8 +170,10 @@ class Model:
     s_orders: dict | None = None             # rate of each order >= 4 ({4: s4, 5: s5, ...}; else s_high)
     ncde_mode: str = "moment"                # NCDE: "moment", "rate" (per-cell s1(phi)) or "cde"
     a1: float = 0.0                          # NCDE: A1 = a1 I of Eq. (GNCDE) with B-bar = u phi
+    m2g_aniso: bool = False                  # NSE, single speed: (delta4 . u) . grad rho in M2G
     f: np.ndarray = field(default=None, repr=False)          # f-bar, shape (Q, *grid)
     phi_prev: np.ndarray = field(default=None, repr=False)   # NCDE: phi at the previous step
+    rho_prev: np.ndarray = field(default=None, repr=False)   # NSE: rho at the previous step
     step_count: int = 0
 
     def __post_init__(self):
@@ -186,6 +194,8 @@ class Model:
         self.shape = grid_shape(self.n)
         if self.u_const is not None:
             self.u_const = np.asarray(self.u_const, dtype=np.float64)
+        if self.m2g_aniso and (self.eq != "nse" or self.lat.kind not in L.SINGLE_SPEED):
+            raise ValueError("the delta4 term of M2G is the single-speed (k = 1) NSE case")
 
     def normal_block(self):
         """Eq. (4-27): the relaxation of the normal second moments is the inverse of
@@ -271,12 +281,26 @@ class Model:
         rho_or_phi = np.asarray(rho_or_phi, dtype=np.float64)
         self.f = self.equilibrium(rho_or_phi, None if u is None else np.asarray(u, dtype=np.float64))
         self.phi_prev = rho_or_phi.copy() if self.eq == "ncde" else None
+        self.rho_prev = rho_or_phi.copy() if self.eq == "nse" else None
         self.step_count = 0
 
     def set_populations(self, f):
         self.f = np.array(f, dtype=np.float64, copy=True)
         if self.eq == "ncde" and self.phi_prev is None:
             self.phi_prev = np.sum(self.f, axis=0)
+        if self.eq == "nse":
+            self.rho_prev = np.sum(self.f, axis=0)
+
+    def density_gradient(self):
+        """grad rho from the density of the previous step: second-order central differences on
+        the periodic grid, d_a rho = (rho(x + e_a) - rho(x - e_a)) / (2 c_a dt), c_a dt being the
+        cell spacing along axis a (dt = 1)."""
+        d = self.lat.d
+        g = np.zeros((d,) + self.shape)
+        for a in range(d):
+            ax = axis_of(a, d, lead=0)
+            g[a] = (np.roll(self.rho_prev, -1, axis=ax) - np.roll(self.rho_prev, 1, axis=ax)) / (2.0 * self.lat.c[a])
+        return g
 
     # -- sources --------------------------------------------------------------------------------
     def source_moments(self, fields):
@@ -287,17 +311,22 @@ class Model:
         mF = np.zeros((R, ncell))
         mG = np.zeros((R, ncell))
         if self.eq == "nse":
-            if self.force is None:
+            if self.force is None and not self.m2g_aniso:
                 return mF, mG
             F = self.force_field().reshape(lat.d, -1)
             u = fields[1].reshape(lat.d, -1)
             S2 = self.S[:R, :R]
             raw = np.zeros((R, ncell))          # uF + Fu on the second-order rows
+            if self.m2g_aniso:
+                grad = self.density_gradient().reshape(lat.d, -1)
             for r, poly in enumerate(lat.polys):
                 if lat.orders[r] == 2:
                     axes = [a for a, k in enumerate(max(poly, key=sum)) for _ in range(k)]
                     a, b = axes
                     raw[r] = u[a] * F[b] + F[a] * u[b]
+                    if self.m2g_aniso and a == b:
+                        # Eq. (M2Ga): [(delta4 . u) . grad rho]_aa = (c_a^2 - 3 c_s^2) u_a d_a rho
+                        raw[r] = raw[r] + (lat.c[a] ** 2 - 3.0 * self.cs2_eq) * u[a] * grad[a]
             for r, poly in enumerate(lat.polys):
                 o = lat.orders[r]
                 if o == 1:
@@ -305,7 +334,8 @@ class Model:
                     (ex,) = poly.keys()
                     mF[r] = F[ex.index(1)]
                 elif o == 2:
-                    # M2G = (I - S2/2)(uF + Fu) (Eq. (M2Ga-1), S = 0), M0G = 0 so the H2
+                    # M2G = (I - S2/2)(uF + Fu) (Eq. (M2Ga-1), S = 0; with m2g_aniso the
+                    # bracket of Eq. (M2Ga) carries the delta4 term too), M0G = 0 so the H2
                     # Hermite moment equals the raw second moment; S2 is the second-order block
                     # of S (diagonal, or with the bulk coupling of Eq. (4-27))
                     rows2 = [q for q in range(R) if lat.orders[q] == 2]
@@ -348,6 +378,8 @@ class Model:
                 ft = ft - np.outer(self.Hinv[:, r], lat.Hfull[r] @ fne) * ds[None, :]
         if self.eq == "ncde":
             self.phi_prev = rho_or_phi.copy()
+        elif self.m2g_aniso:
+            self.rho_prev = rho_or_phi.copy()
         return ft.reshape(self.f.shape)
 
     def stream(self, ft):
