@@ -459,9 +459,10 @@ def bench_ours(args):
             "rates": {str(k): v for k, v in HIGH_RATES.items()}, "steps": vsteps,
             "ms_per_step": high16_ms, "mlups": cells / high16_ms / 1e3,
             "hbm_frac": 2 * Q * 2 * cells / (high16_ms / 1e3) / 1e9 / peak}
-    other = run_other_configs(lbm, W_stream=stream, barrier=barrier)
-    if rank == 0:
-        line["other_configs"] = other
+    if not args.no_other_configs:
+        other = run_other_configs(lbm, W_stream=stream, barrier=barrier)
+        if rank == 0:
+            line["other_configs"] = other
     if args.serving_requests > 0:
         serving = run_serving(args.serving_requests)
         if rank == 0:
@@ -477,12 +478,14 @@ def run_other_configs(lbm, W_stream, barrier):
     """The smaller configurations at full size, timed the same way (CUDA events over a run of
     steps): the rD2Q13 nonlinear CDE hill (1024 x 768, FP32 and FP64, the full 5000 steps; 104 or
     208 B of populations plus 8 or 16 B of phi history per cell update) and the rD2Q25
-    Taylor-Green vortex (64 x 48, FP64, 200 steps; 1.2 MB of state, resident in L2, so not an HBM
-    measurement)."""
+    Taylor-Green vortex (64 x 48, FP64, 200 steps). The FP32 hill (82 MB of state) and the vortex
+    (1.2 MB) stay resident in L2, so their hbm_frac is not an HBM measurement (l2_resident marks
+    them); the FP64 hill (164 MB) is bound by the FP64 pipe, not by HBM."""
     import numpy as np
     import torch
     from paper_2512_16230_gb300 import workloads as W
     peak, _ = _peaks()
+    l2_bytes = getattr(torch.cuda.get_device_properties(torch.cuda.current_device()), "L2_cache_size", 126 << 20)
     out = {}
     cases = [("ncde_hill_rD2Q13_1024x768_f32", W.ncde_hill(store="f32"), 4),
              ("ncde_hill_rD2Q13_1024x768_f64", W.ncde_hill(store="f64"), 8),
@@ -505,8 +508,10 @@ def run_other_configs(lbm, W_stream, barrier):
         barrier()
         ms = a.elapsed_time(b) / wl.steps
         per_cell = 2 * lat.Q * nbytes + (2 * nbytes if wl.eq == "ncde" else 0)
+        state = (2 * lat.Q + (1 if wl.eq == "ncde" else 0)) * nbytes * wl.ncells
         out[name] = {"steps": wl.steps, "ms_per_step": ms, "mlups": wl.ncells / ms / 1e3,
-                     "algorithmic_bytes_per_cell": per_cell,
+                     "algorithmic_bytes_per_cell": per_cell, "state_bytes": state,
+                     "l2_resident": bool(state < l2_bytes),
                      "hbm_frac": per_cell * wl.ncells / (ms / 1e3) / 1e9 / peak}
         m.close()
     return out
@@ -547,6 +552,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=160,
                     help="requests of the seeded serving mix (config 5) served after the step benchmark; 0 skips")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the full-size runs of the smaller configurations (profiling commands)")
     ap.add_argument("--store", choices=sorted(STORE_DTYPE), default="f32",
                     help="population storage (the benchmark is FP32; 16-bit deviations for the reduced-precision path)")
     ap.add_argument("--tensor-cores", action="store_true",

@@ -149,7 +149,8 @@ lbm_status lbm_lattice_destroy(lbm_lattice* lat);
  * ------------------------------------------------------------------------------------------ */
 
 /* Device bytes a model needs: two population buffers (Q * ncells * sizeof(store)), the NCDE
- * previous-step field, the body-force profile and the reduction scratch, each 256-byte aligned. */
+ * previous-step field (or, for the NSE on rD2Q9 / rD3Q27, two previous-step density fields), the
+ * body-force profile and the reduction scratch, each 256-byte aligned. */
 lbm_status lbm_model_workspace_bytes(const lbm_lattice* lat, lbm_eq eq, const int64_t* n,
                                      lbm_dtype store, size_t* bytes);
 
@@ -246,6 +247,18 @@ lbm_status lbm_model_set_ncde(lbm_model* m, const double* u_const, double nonlin
  * Errors: LBM_ERR_ARG (not an NCDE model, unknown variant, a1 with the CDE, non-finite a1),
  *         LBM_ERR_NOT_IMPLEMENTED (rate or CDE variant inside a batch). */
 lbm_status lbm_model_set_ncde_variant(lbm_model* m, lbm_ncde_variant variant, double a1);
+
+/* The anisotropy term of M2G on the single-speed lattices (Eq. (M2Ga), Sec. 3.4, k = 1): the
+ * bracket of M2G gains (delta4 . u) . grad rho, where delta4_aaaa = c_a^2 - 3 c_s^2 (c_s^2 =
+ * cs2_eq) and every other component is zero, so the term is (c_a^2 - 3 c_s^2) u_a d_a rho on the
+ * normal second moment of axis a. Eq. (M2Ga-1), the default (enable = 0), drops it as O(Ma^3).
+ * d_a rho is the second-order central difference, over the cell spacing c_a dt, of the density of
+ * the previous step, which the step kernel stores (one field read at the 2d neighbours and one
+ * written per cell; FP32 or FP64 as the compute dtype). Enabling takes the density of the current
+ * state as the previous one, as init_fields and set_populations do (rho^{-1} = rho^0).
+ * Errors: LBM_ERR_ARG (not an NSE model on rD2Q9 / rD3Q27, enable not 0 or 1),
+ *         LBM_ERR_NOT_IMPLEMENTED (enabling inside a batch), LBM_ERR_CUDA. */
+lbm_status lbm_model_set_m2g_anisotropy(lbm_model* m, int enable);
 
 /* f-bar(t = 0) = f^eq of the given fields (Eq. (feq-1)); for the NCDE phi^{-1} = phi^0.
  * rho_or_phi[ncells], u[d*ncells] (NSE only; ignored and may be NULL for the NCDE). Resets

@@ -100,7 +100,7 @@ __global__ void k_fields(const GenParams p, const GenTables<CT> t, const ST* __r
   for (int a = 0; a < p.d; ++a) u_out[size_t(a) * N + cell] = double(fma(CT(0.5), F[a], j[a]) / rho);
 }
 
-// NCDE: phi_prev(x) = sum_i f-bar_i(x)
+// NCDE: phi_prev(x) = sum_i f-bar_i(x); for the NSE (S = 0) the same sum is the density
 template <class ST, class CT>
 __global__ void k_phi(const GenParams p, const GenTables<CT> t, const ST* __restrict__ A, CT* __restrict__ phi) {
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,6 +264,19 @@ lbm_status launch_phi_from_populations(lbm_model* m) {
     k_phi<ST, CT><<<grid, 128, 0, m->stream>>>(p, gen_tables<CT>(p), static_cast<const ST*>(m->f[m->cur]),
                                                  static_cast<CT*>(m->phi_prev));
     return after_launch(m, "phi launch");
+  });
+}
+
+lbm_status launch_density_history(lbm_model* m) {
+  GenParams p;
+  gen_params(m, &p);
+  const int grid = (m->ncells + 127) / 128;
+  return dispatch_store(m, [&](auto st, auto ct) {
+    using ST = decltype(st);
+    using CT = decltype(ct);
+    k_phi<ST, CT><<<grid, 128, 0, m->stream>>>(p, gen_tables<CT>(p), static_cast<const ST*>(m->f[m->cur]),
+                                                 static_cast<CT*>(m->rho_hist[m->hist_cur]));
+    return after_launch(m, "density history launch");
   });
 }
 

@@ -119,6 +119,11 @@ void make_step_params(const lbm_model* m, StepParams<CT>* p) {
     p->a1 = CT(m->a1);
     p->half0 = CT(1.0 - 0.5 * m->s[0]);
   }
+  // (delta4 . u) . grad rho of Eq. (M2Ga) on the single-speed lattices: delta4_aaaa = c_a^2 - 3 c_s^2,
+  // d_a rho by the central difference over the cell spacing c_a (dt = 1)
+  p->aniso = m->m2g_aniso ? 1 : 0;
+  if (m->m2g_aniso)
+    for (int a = 0; a < L->d; ++a) p->dgrad[a] = CT((L->c[a] * L->c[a] - 3.0 * m->cs2_eq) / (2.0 * L->c[a]));
   p->sh_rho_ref = CT(m->s_high * rho_ref);
   p->s_high = CT(m->s_high);
   p->one_minus_sh = CT(1.0 - m->s_high);
@@ -232,7 +237,9 @@ Layout layout(const lbm_lattice* L, int eq, const int64_t* n, int store) {
   Layout lo;
   lo.f_bytes = align_up(size_t(L->Q) * size_t(ncells) * dtype_bytes(store));
   lo.phi_off = 2 * lo.f_bytes;
-  const size_t phi_bytes = eq == LBM_NCDE ? align_up(size_t(ncells) * cbytes) : 0;
+  // NCDE: phi of the previous step; single-speed NSE: two density fields for the M2G gradient
+  const size_t fields = eq == LBM_NCDE ? 1 : (lattice_single(L->kind) ? 2 : 0);
+  const size_t phi_bytes = fields * align_up(size_t(ncells) * cbytes);
   lo.force_off = lo.phi_off + phi_bytes;
   lo.part_off = lo.force_off + align_up(size_t(nmax) * cbytes);
   lo.sums_off = lo.part_off + align_up(size_t(kRedBlocks) * 4 * sizeof(double));
@@ -477,6 +484,11 @@ lbm_status lbm_model_create(const lbm_lattice* L, lbm_eq eq, const int64_t* n, l
     m->f[0] = base;
     m->f[1] = base + lo.f_bytes;
     m->phi_prev = eq == LBM_NCDE ? base + lo.phi_off : nullptr;
+    if (eq == LBM_NSE && lattice_single(L->kind)) {
+      const size_t cbytes = store == LBM_F64 ? 8 : 4;
+      m->rho_hist[0] = base + lo.phi_off;
+      m->rho_hist[1] = base + lo.phi_off + align_up(size_t(m->ncells) * cbytes);
+    }
     m->force_tab = base + lo.force_off;
     m->partials = reinterpret_cast<double*>(base + lo.part_off);
     m->sums = reinterpret_cast<double*>(base + lo.sums_off);
@@ -601,6 +613,23 @@ lbm_status lbm_model_set_ncde_variant(lbm_model* m, lbm_ncde_variant variant, do
   return LBM_OK;
 }
 
+lbm_status lbm_model_set_m2g_anisotropy(lbm_model* m, int enable) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (m->eq != LBM_NSE || !lattice_single(m->lat->kind))
+    return set_error(LBM_ERR_ARG, "the delta4 term of M2G applies to the NSE on rD2Q9 / rD3Q27");
+  if (enable != 0 && enable != 1) return set_error(LBM_ERR_ARG, "enable must be 0 or 1");
+  if (m->batch && enable)
+    return set_error(LBM_ERR_NOT_IMPLEMENTED, "the density-gradient term of M2G is not available inside a batch");
+  DeviceGuard guard(m->device);
+  if (enable && !m->m2g_aniso) {
+    // the previous-step density starts as the density of the current state
+    lbm_status st = launch_density_history(m);
+    if (st != LBM_OK) return st;
+  }
+  m->m2g_aniso = enable != 0;
+  return LBM_OK;
+}
+
 lbm_status lbm_model_init_fields(lbm_model* m, const double* rho_or_phi, const double* u, int on_device) {
   if (!m || !rho_or_phi) return set_error(LBM_ERR_ARG, "NULL argument");
   if (m->eq == LBM_NSE && !u) return set_error(LBM_ERR_ARG, "the NSE model needs a velocity field");
@@ -644,6 +673,7 @@ lbm_status lbm_model_set_populations(lbm_model* m, const double* f, int on_devic
     }
     lbm_status s2 = launch_scatter(m, src);
     if (s2 == LBM_OK && m->eq == LBM_NCDE) s2 = launch_phi_from_populations(m);
+    if (s2 == LBM_OK && m->rho_hist[0]) s2 = launch_density_history(m);
     return s2;
   });
   if (st != LBM_OK) return st;

@@ -45,6 +45,12 @@ struct lbm_model {
   void* f[2];  // ping-pong population buffers (storage dtype), f[cur] is the current state
   int cur;
   void* phi_prev;   // NCDE: phi at the previous step (compute dtype)
+  // single-speed NSE: the density of the previous step for the (delta4 . u) . grad rho term of
+  // M2G, Eq. (M2Ga) (two fields in the compute dtype: a step reads rho_hist[hist_cur] at the
+  // neighbours and writes rho_hist[hist_cur ^ 1])
+  void* rho_hist[2];
+  int hist_cur;
+  bool m2g_aniso;
   void* force_tab;  // NSE: F_a as a function of the cell index along axis b (compute dtype)
   double* partials; // reduction scratch of the conservation sums
   double* sums;     // 4 doubles
@@ -102,6 +108,13 @@ struct StepParams {
   CT nonlin_rate, a1;
   CT cde_coef[3];
   CT half0;
+  // single-speed NSE with the delta4 term of M2G: dgrad_a = (c_a^2 - 3 cs2_eq) / (2 c_a) turns the
+  // central difference of the previous-step density (rho_in) along axis a into
+  // (c_a^2 - 3 cs2_eq) d_a rho; the step writes its density to rho_out
+  int aniso;
+  CT dgrad[3];
+  const CT* rho_in;
+  CT* rho_out;
   int n[3];
   int ncells;
   unsigned div_m[2];     // cell index -> (x, y, z): q = umulhi(v, div_m) >> div_s exactly divides
@@ -288,6 +301,7 @@ lbm_status launch_scatter(lbm_model* m, const double* in);    // stored array fr
 lbm_status launch_fields(lbm_model* m, double* rho, double* u);
 lbm_status launch_sums(lbm_model* m);                          // into m->sums (device)
 lbm_status launch_phi_from_populations(lbm_model* m);          // NCDE: phi_prev = sum f-bar
+lbm_status launch_density_history(lbm_model* m);               // single-speed NSE: rho_hist[hist_cur] = sum f-bar
 // The conservation-sum kernels with caller-provided reduction scratch (partial_slots x 4
 // doubles, at least kRedBlocks slots) and result (4 doubles, device memory).
 lbm_status launch_sums_into(lbm_model* m, double* partials, int partial_slots, double* out);

@@ -259,12 +259,14 @@ struct NcdeCell {
 
 // g_r / N_r with g = s_h m^eq - (S - s_h I)(m - m^eq) + sigma. S is diagonal except on the normal
 // second-order rows, where the d x d block S_n carries the bulk coupling of Eq. (4-27).
-// sigma: NSE (I - S/2) M1F = (1 - s/2) F on order 1 and M2G = (I - S2/2)(uF + Fu) on order 2;
-// NCDE M1G = (I - S1/2) u d_t phi - S1 A1 d_t(u phi) on order 1 (factor half1) and, for the
+// sigma: NSE (I - S/2) M1F = (1 - s/2) F on order 1 and M2G = (I - S2/2)(uF + Fu) on order 2,
+// plus, given gr (single-speed lattices), the diagonal (delta4 . u) . grad rho of Eq. (M2Ga) with
+// gr_a = (c_a^2 - 3 c_s^2) d_a rho; NCDE M1G = (I - S1/2) u d_t phi - S1 A1 d_t(u phi) on order 1 (factor half1) and, for the
 // CDE variant, M0G = (1 - s0/2) S_G on order 0.
 template <class L, class CT, int EQ, int r, class P>
 __device__ __forceinline__ CT row_update(const P& p, const CT (&meq)[L::R], const CT (&neq)[L::R],
-                                         const CT (&u)[3], const CT (&F)[3], CT dphi, const NcdeCell<CT>& nc) {
+                                         const CT (&u)[3], const CT (&F)[3], CT dphi, const NcdeCell<CT>& nc,
+                                         const CT* gr) {
   constexpr int deg = degree(mono<L::D>(r));
   constexpr int na = normal_index<L::D>(r);
   CT relax, sig = CT(0);
@@ -273,7 +275,11 @@ __device__ __forceinline__ CT row_update(const P& p, const CT (&meq)[L::R], cons
     static_for<L::D>([&](auto b) {
       constexpr int B = decltype(b)::value;
       relax = fma(p.sdn[na][B], neq[normal_row<L::D>(B)], relax);
-      if constexpr (EQ == LBM_NSE) sig = fma(p.halfn[na][B], CT(2) * u[B] * F[B], sig);
+      if constexpr (EQ == LBM_NSE) {
+        CT t = CT(2) * u[B] * F[B];
+        if (gr != nullptr) t = fma(u[B], gr[B], t);
+        sig = fma(p.halfn[na][B], t, sig);
+      }
     });
   } else {
     relax = p.sd[r] * neq[r];
@@ -436,9 +442,10 @@ struct NoHigh {};
 
 // The collision in moment space: from the raw moments mu_k = sum_i mono_k(e_i) f_i (k < R) to
 // the monomial-basis coefficients h of the update f*_i = (1 - s_h) f_i + w_i sum_k mono_k(e_i) h_k.
+// phi_now receives phi (NCDE) or rho (NSE); gr, if given, the M2G density-gradient term.
 template <class L, class CT, int EQ, bool DEV, class P>
 __device__ __forceinline__ void collide_moments(CT (&mu)[L::R], const P& p, const CT (&F)[3], CT phi_prev,
-                                                CT& phi_now, CT (&h)[L::R]) {
+                                                CT& phi_now, CT (&h)[L::R], const CT* gr = nullptr) {
   constexpr int R = L::R, D = L::D;
   if constexpr (DEV) {
     static_for<R>([&](auto k) {
@@ -467,6 +474,7 @@ __device__ __forceinline__ void collide_moments(CT (&mu)[L::R], const P& p, cons
       u[A] = j[A] * inv;
     });
     eq_raw_nse<L>(rho, j, u, rho * p.cs2_eq, me);
+    phi_now = rho;
   } else {
     // Eq. (2-4-1) with S = 0: phi = sum f (+ S_G / 2, lambda = 1, for the CDE variant)
     CT phi = mu[0];
@@ -505,7 +513,7 @@ __device__ __forceinline__ void collide_moments(CT (&mu)[L::R], const P& p, cons
   CT gN[R];
   static_for<R>([&](auto r) {
     constexpr int Rr = decltype(r)::value;
-    gN[Rr] = row_update<L, CT, EQ, Rr>(p, meq, neq, u, F, dphi, nc);
+    gN[Rr] = row_update<L, CT, EQ, Rr>(p, meq, neq, u, F, dphi, nc, gr);
   });
   hermite_to_monomial<L>(p, gN, h);
   if constexpr (DEV) h[0] -= p.sh_rho_ref;
@@ -513,13 +521,13 @@ __device__ __forceinline__ void collide_moments(CT (&mu)[L::R], const P& p, cons
 
 template <class L, class CT, int EQ, bool DEV = false, class P, class HP = NoHigh>
 __device__ __forceinline__ void collide(CT (&f)[L::Q], const P& p, const CT (&F)[3],
-                                        CT phi_prev, CT& phi_now, HP* hp = nullptr) {
+                                        CT phi_prev, CT& phi_now, HP* hp = nullptr, const CT* gr = nullptr) {
   constexpr bool HI = !std::is_same<HP, NoHigh>::value;
   if constexpr (HI) high_moments<L>(f, *hp);
   CT mu[L::R];
   raw_moments<L>(f, mu);
   CT h[L::R];
-  collide_moments<L, CT, EQ, DEV>(mu, p, F, phi_prev, phi_now, h);
+  collide_moments<L, CT, EQ, DEV>(mu, p, F, phi_prev, phi_now, h, gr);
   back_project<L>(f, p, h, p.one_minus_sh);
   if constexpr (HI) high_back<L>(f, p, *hp);
 }
@@ -613,6 +621,31 @@ __device__ __forceinline__ void body_force(int force_a, int force_b, const CT* f
   }
 }
 
+// The M2G term of Eq. (M2Ga) on the single-speed lattices needs grad rho: gr_a =
+// (c_a^2 - 3 c_s^2) d_a rho from the central difference of the previous step's density (p.rho_in)
+// at the periodic neighbours of cell (x, y, z); zero when the term is off.
+template <class L, class CT, int EQ>
+struct M2gGradient {
+  static constexpr bool kOn = L::SINGLE && EQ == LBM_NSE;
+};
+template <class L, class CT>
+__device__ __forceinline__ void m2g_density_gradient(const StepParams<CT>& p, int cell, int x, int y, int z,
+                                                     CT (&gr)[3]) {
+  gr[0] = gr[1] = gr[2] = CT(0);
+  if (!p.aniso) return;
+  const int nx = p.n[0], ny = p.n[1];
+  const CT* r = p.rho_in;
+  const int xp = x + 1 == nx ? -x : 1, xm = x == 0 ? nx - 1 : -1;
+  gr[0] = p.dgrad[0] * (r[cell + xp] - r[cell + xm]);
+  const int yp = (y + 1 == ny ? -y : 1) * nx, ym = (y == 0 ? ny - 1 : -1) * nx;
+  gr[1] = p.dgrad[1] * (r[cell + yp] - r[cell + ym]);
+  if constexpr (L::D == 3) {
+    const int nz = p.n[2], nxy = nx * ny;
+    const int zp = (z + 1 == nz ? -z : 1) * nxy, zm = (z == 0 ? nz - 1 : -1) * nxy;
+    gr[2] = p.dgrad[2] * (r[cell + zp] - r[cell + zm]);
+  }
+}
+
 // K1 (COLLIDE) / K2 (stream only): pull gather, collide, aligned store.
 template <class L, class CT, class ST, int EQ, bool COLLIDE>
 __global__ void __launch_bounds__(kBlock, LBM_K1_MIN_BLOCKS) k_step(const StepParams<CT> p,
@@ -634,8 +667,14 @@ __global__ void __launch_bounds__(kBlock, LBM_K1_MIN_BLOCKS) k_step(const StepPa
     body_force(p.force_a, p.force_b, p.force_tab, nb.x, nb.y, nb.z, F);
     CT phi_prev = CT(0), phi_now = CT(0);
     if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
-    collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now);
+    constexpr bool AG = M2gGradient<L, CT, EQ>::kOn;
+    CT gr[3];
+    if constexpr (AG) m2g_density_gradient<L>(p, cell, nb.x, nb.y, nb.z, gr);
+    collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, static_cast<NoHigh*>(nullptr), AG ? gr : nullptr);
     if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
+    if constexpr (AG) {
+      if (p.aniso) p.rho_out[cell] = phi_now;
+    }
   }
   static_for<L::Q>([&](auto i) {
     constexpr int I = decltype(i)::value;
@@ -670,8 +709,14 @@ __global__ void __launch_bounds__(kBlock, 3) k_step_high(const StepParams<CT> p,
   body_force(p.force_a, p.force_b, p.force_tab, nb.x, nb.y, nb.z, F);
   CT phi_prev = CT(0), phi_now = CT(0);
   if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
-  collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, &tab);
+  constexpr bool AG = M2gGradient<L, CT, EQ>::kOn;
+  CT gr[3];
+  if constexpr (AG) m2g_density_gradient<L>(p, cell, nb.x, nb.y, nb.z, gr);
+  collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, &tab, AG ? gr : nullptr);
   if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
+  if constexpr (AG) {
+    if (p.aniso) p.rho_out[cell] = phi_now;
+  }
   static_for<L::Q>([&](auto i) {
     constexpr int I = decltype(i)::value;
     if constexpr (DEV) k1_store(fout + size_t(I) * N + cell, RawCodec<ST>::enc(f[I]));
@@ -680,7 +725,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_step_high(const StepParams<CT> p,
 }
 
 // Initialisation: f-bar(t=0) = f^eq(fields), written to the stored array at x - e_i so that the
-// next pull gather yields it; the NCDE previous-step field starts at phi^0.
+// next pull gather yields it; the NCDE previous-step field starts at phi^0, the previous-step
+// density of the single-speed NSE (phi non-null) at rho^0.
 template <class L, class CT, class ST, int EQ>
 __global__ void __launch_bounds__(kBlock) k_init(const StepParams<CT> p, const double* rho_or_phi,
                                                  const double* u, ST* __restrict__ fout,
@@ -693,6 +739,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const StepParams<CT> p, const d
   CT uu[3] = {CT(0), CT(0), CT(0)};
   if constexpr (EQ == LBM_NSE) {
     for (int a = 0; a < L::D; ++a) uu[a] = CT(u[size_t(a) * N + cell]);
+    if (phi != nullptr) phi[cell] = r;
   } else {
     phi[cell] = r;
   }
@@ -886,9 +933,15 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
       tgrid = tc_grid(m, tp.ntiles, k, 3, tsmem);
     }
   }
+  const bool hist = collide_on && m->m2g_aniso;
   for (int64_t s = 0; s < nsteps; ++s) {
     const ST* fin = static_cast<const ST*>(m->f[m->cur]);
     ST* fout = static_cast<ST*>(m->f[m->cur ^ 1]);
+    if (hist) {
+      p.rho_in = static_cast<const CT*>(m->rho_hist[m->hist_cur]);
+      p.rho_out = static_cast<CT*>(m->rho_hist[m->hist_cur ^ 1]);
+    }
+    p.aniso = hist ? 1 : 0;
     bool done = false;
     if constexpr (is_deviation_storage<ST>()) {
       if (tensor) {
@@ -931,6 +984,7 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_error(err, "collide-stream launch");
     m->cur ^= 1;
+    if (hist) m->hist_cur ^= 1;
     m->launches += 1;
     if (collide_on) m->steps += 1;
   }
@@ -943,7 +997,7 @@ lbm_status launch_init_typed(lbm_model* m, const double* rho_or_phi, const doubl
   make_step_params<CT>(m, &p);
   const int grid = (m->ncells + kBlock - 1) / kBlock;
   ST* fout = static_cast<ST*>(m->f[m->cur]);
-  CT* phi = static_cast<CT*>(m->phi_prev);
+  CT* phi = static_cast<CT*>(m->eq == LBM_NSE ? m->rho_hist[m->hist_cur] : m->phi_prev);
   if (m->eq == LBM_NSE)
     k_init<L, CT, ST, LBM_NSE><<<grid, kBlock, 0, m->stream>>>(p, rho_or_phi, u, fout, phi);
   else

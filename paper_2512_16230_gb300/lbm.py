@@ -50,6 +50,7 @@ SIGNATURES = {
     "lbm_model_set_force": (c_int, [_P, c_int, c_int, c_double, c_int, c_double]),
     "lbm_model_set_ncde": (c_int, [_P, _PD, c_double]),
     "lbm_model_set_ncde_variant": (c_int, [_P, c_int, c_double]),
+    "lbm_model_set_m2g_anisotropy": (c_int, [_P, c_int]),
     "lbm_model_set_tensor_cores": (c_int, [_P, c_int]),
     "lbm_model_init_fields": (c_int, [_P, _P, _P, c_int]),
     "lbm_model_set_populations": (c_int, [_P, _P, c_int]),
@@ -275,6 +276,11 @@ class Model:
         CDE); a1 is the mixed-derivative coefficient of Eq. (GNCDE)."""
         _check(load().lbm_model_set_ncde_variant(self.handle, NCDE_VARIANTS[variant], float(a1)),
                "lbm_model_set_ncde_variant")
+
+    def set_m2g_anisotropy(self, enable=1):
+        """rD2Q9 / rD3Q27 NSE: add (delta4 . u) . grad rho to M2G (Eq. (M2Ga)), with grad rho
+        from the previous step's density."""
+        _check(load().lbm_model_set_m2g_anisotropy(self.handle, int(enable)), "lbm_model_set_m2g_anisotropy")
 
     # -- state ---------------------------------------------------------------------------------
 

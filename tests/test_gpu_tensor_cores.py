@@ -170,3 +170,28 @@ def test_tensor_core_high_order_rates_flow():
     om.step(wl.steps)
     gm.step(wl.steps)
     assert rel_l2(gm.read_fields()[1], om.fields()[1]) <= 1e-3
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+@pytest.mark.parametrize("name", ["rD2Q9", "rD3Q27"])
+def test_tensor_core_m2g_anisotropy_step(name, store):
+    """The density-gradient term of Eq. (M2Ga) in the 16-bit tensor-core kernel: one step against
+    the FP64 oracle fed the stored deviations (the previous-step density is the density of that
+    state on both sides), within the rounding of input and output."""
+    spec = ALL_SPECS[name]
+    d = spec.d
+    n = RAGGED[d]
+    s = np.random.default_rng(41).uniform(0.6, 1.9, spec.R)
+    kw = dict(s_high=1.3, force=(0, d - 1, 1e-3, 1, 0.2), m2g_aniso=True)
+    gm = gpu_model(spec, "nse", n, s, store=store, **kw)
+    om = oracle_model(spec, "nse", n, s, **kw)
+    gm.set_tensor_cores(1)
+    w = om.lat.w.reshape((-1,) + (1,) * d)
+    r = np.random.default_rng(7).uniform(-0.1, 0.1, size=(gm.Q,) + n[::-1])
+    f_in = w * (1.0 + r)
+    gm.set_populations(f_in)
+    om.set_populations(w + _stored_deviation(f_in, w, store))
+    gm.step(1)
+    om.step(1)
+    err = rel_l2(gm.get_populations() - w, om.f - w)
+    assert err <= 4 * UNIT[store]
