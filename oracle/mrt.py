@@ -29,7 +29,10 @@ Readings of points the paper leaves open (each is listed in the design notes):
   lambda = 1, S_G = -u . grad phi from the local gradient of Eq. (M-NCDE-3-00), M0G =
   (1 - s0/2) S_G); ``a1`` adds the mixed-derivative term of Eq. (GNCDE) with A1 = a1 I and
   B-bar = u phi, whose coefficient is dt A1 by the derivation (the printed K1 = dt S1 A1 carries
-  the same slip as the printed K).
+  the same slip as the printed K). ``a2`` with ``psi`` adds the cross-diffusion term of
+  Eq. (GNCDE): A2 = a2 I and D-bar = psi I for a prescribed cell field psi, so M1G gains
+  -S1 A2 grad psi (grad psi by central differences over the cell spacing c_a dt) and the
+  equation gains div(dt A2 grad psi) (K2 = dt A2 by the derivation, as for K1).
 * rows of order >= 4 (left to the designer by the paper) relax with one shared rate s_high, or
   with ``s_orders`` one rate per order k on the graded block: the W-orthogonal complement of the
   lower orders inside the lattice functions spanned by the monomials of degree <= k.
@@ -171,6 +174,8 @@ class Model:
     ncde_mode: str = "moment"                # NCDE: "moment", "rate" (per-cell s1(phi)) or "cde"
     a1: float = 0.0                          # NCDE: A1 = a1 I of Eq. (GNCDE) with B-bar = u phi
     m2g_aniso: bool = False                  # NSE, single speed: (delta4 . u) . grad rho in M2G
+    a2: float = 0.0                          # NCDE: A2 = a2 I of Eq. (GNCDE) with D-bar = psi I
+    psi: np.ndarray | None = None            # NCDE: the prescribed field of D-bar (grid shape)
     f: np.ndarray = field(default=None, repr=False)          # f-bar, shape (Q, *grid)
     phi_prev: np.ndarray = field(default=None, repr=False)   # NCDE: phi at the previous step
     rho_prev: np.ndarray = field(default=None, repr=False)   # NSE: rho at the previous step
@@ -196,6 +201,8 @@ class Model:
             self.u_const = np.asarray(self.u_const, dtype=np.float64)
         if self.m2g_aniso and (self.eq != "nse" or self.lat.kind not in L.SINGLE_SPEED):
             raise ValueError("the delta4 term of M2G is the single-speed (k = 1) NSE case")
+        if self.a2 != 0.0 and (self.eq != "ncde" or self.ncde_mode == "cde" or self.psi is None):
+            raise ValueError("the cross-diffusion term needs the NCDE (not the CDE variant) and psi")
 
     def normal_block(self):
         """Eq. (4-27): the relaxation of the normal second moments is the inverse of
@@ -291,16 +298,20 @@ class Model:
         if self.eq == "nse":
             self.rho_prev = np.sum(self.f, axis=0)
 
-    def density_gradient(self):
-        """grad rho from the density of the previous step: second-order central differences on
-        the periodic grid, d_a rho = (rho(x + e_a) - rho(x - e_a)) / (2 c_a dt), c_a dt being the
-        cell spacing along axis a (dt = 1)."""
+    def central_gradient(self, g):
+        """Second-order central differences on the periodic grid,
+        d_a g = (g(x + e_a) - g(x - e_a)) / (2 c_a dt), c_a dt being the cell spacing along axis a
+        (dt = 1)."""
         d = self.lat.d
-        g = np.zeros((d,) + self.shape)
+        out = np.zeros((d,) + self.shape)
         for a in range(d):
             ax = axis_of(a, d, lead=0)
-            g[a] = (np.roll(self.rho_prev, -1, axis=ax) - np.roll(self.rho_prev, 1, axis=ax)) / (2.0 * self.lat.c[a])
-        return g
+            out[a] = (np.roll(g, -1, axis=ax) - np.roll(g, 1, axis=ax)) / (2.0 * self.lat.c[a])
+        return out
+
+    def density_gradient(self):
+        """grad rho from the density of the previous step (central differences)."""
+        return self.central_gradient(self.rho_prev)
 
     # -- sources --------------------------------------------------------------------------------
     def source_moments(self, fields):
@@ -345,16 +356,19 @@ class Model:
             # App. A special case (3): M0G = (1 - s0/2) S_G (Eq. (M-NCDE-4), lambda = 1), M1G = 0
             mG[0] = (1.0 - 0.5 * self.s[0]) * self.cde_source(self.f).reshape(-1)
             return mF, mG
-        # NCDE: M1G = (I - S1/2) u d_t phi - S1 A1 d_t(u phi) (Eq. (M-NCDE-6) with M20 = 0,
-        # B-bar = u phi, A2 = 0); S1 per cell in the "rate" reading
+        # NCDE: M1G = (I - S1/2) u d_t phi - S1 (A1 d_t(u phi) + A2 div(psi I)) (Eq. (M-NCDE-6)
+        # with M20 = 0, B-bar = u phi, D-bar = psi I); S1 per cell in the "rate" reading
         phi = fields[0].reshape(-1)
         dphi = phi - self.phi_prev.reshape(-1)
+        gpsi = self.central_gradient(self.psi).reshape(lat.d, -1) if self.a2 != 0.0 else None
         for r, poly in enumerate(lat.polys):
             if lat.orders[r] == 1:
                 (ex,) = poly.keys()
                 a = ex.index(1)
                 s1 = self.rate_of(r, phi) if self.ncde_mode == "rate" else self.s[r]
                 mG[r] = (1.0 - 0.5 * s1 - s1 * self.a1) * self.u_const[a] * dphi
+                if gpsi is not None:
+                    mG[r] = mG[r] - s1 * self.a2 * gpsi[a]
         return mF, mG
 
     # -- one step --------------------------------------------------------------------------------
