@@ -149,8 +149,9 @@ lbm_status lbm_lattice_destroy(lbm_lattice* lat);
  * ------------------------------------------------------------------------------------------ */
 
 /* Device bytes a model needs: two population buffers (Q * ncells * sizeof(store)), the NCDE
- * previous-step field (or, for the NSE on rD2Q9 / rD3Q27, two previous-step density fields), the
- * body-force profile and the reduction scratch, each 256-byte aligned. */
+ * previous-step field and cross-diffusion field psi (or, for the NSE on rD2Q9 / rD3Q27, two
+ * previous-step density fields), the body-force profile and the reduction scratch, each 256-byte
+ * aligned. */
 lbm_status lbm_model_workspace_bytes(const lbm_lattice* lat, lbm_eq eq, const int64_t* n,
                                      lbm_dtype store, size_t* bytes);
 
@@ -244,9 +245,23 @@ lbm_status lbm_model_set_ncde(lbm_model* m, const double* u_const, double nonlin
  * a1: the mixed-derivative term of Eq. (GNCDE) with A1 = a1 I and B-bar = u phi, i.e. M1G gains
  *     -S1 A1 d_t(u phi) and the equation gains div(a1 dt d_t(u phi)) (moment and rate variants;
  *     must be 0 for the CDE).
- * Errors: LBM_ERR_ARG (not an NCDE model, unknown variant, a1 with the CDE, non-finite a1),
+ * Errors: LBM_ERR_ARG (not an NCDE model, unknown variant, a1 or a cross-diffusion term with the
+ *         CDE, non-finite a1),
  *         LBM_ERR_NOT_IMPLEMENTED (rate or CDE variant inside a batch). */
 lbm_status lbm_model_set_ncde_variant(lbm_model* m, lbm_ncde_variant variant, double a1);
+
+/* The cross-diffusion term of Eq. (GNCDE): A2 = a2 I and D-bar = psi I for a prescribed cell
+ * field psi, so that M1G gains -S1 A2 div(D-bar) = -S1 a2 grad psi (Eq. (M-NCDE-6)) and the
+ * recovered equation gains div(K2 grad psi) with K2 = dt A2 (the derivation; the printed
+ * K2 = dt S1 A2 carries the same slip as the printed K). grad psi is the second-order central
+ * difference over the cell spacing c_a dt, read at the 2d neighbours every step; with the rate
+ * variant S1 is the per-cell S1(phi). psi[ncells] (grid order, x fastest; host or device per
+ * on_device) is copied into the model in the compute dtype and stays until the next call;
+ * a2 = 0 removes the term (psi may then be NULL).
+ * Errors: LBM_ERR_ARG (not an NCDE model, the CDE variant, non-finite a2, NULL psi with a2 != 0),
+ *         LBM_ERR_NOT_IMPLEMENTED (inside a batch), LBM_ERR_CUDA. */
+lbm_status lbm_model_set_ncde_cross_diffusion(lbm_model* m, double a2, const double* psi,
+                                              int on_device);
 
 /* The anisotropy term of M2G on the single-speed lattices (Eq. (M2Ga), Sec. 3.4, k = 1): the
  * bracket of M2G gains (delta4 . u) . grad rho, where delta4_aaaa = c_a^2 - 3 c_s^2 (c_s^2 =

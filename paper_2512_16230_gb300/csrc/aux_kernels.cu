@@ -267,6 +267,21 @@ lbm_status launch_phi_from_populations(lbm_model* m) {
   });
 }
 
+template <class CT>
+__global__ void k_to_compute(const double* __restrict__ src, CT* __restrict__ dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = CT(src[i]);
+}
+
+lbm_status launch_to_compute(lbm_model* m, const double* src, void* dst) {
+  const int grid = (m->ncells + 127) / 128;
+  if (m->store == LBM_F64)
+    k_to_compute<double><<<grid, 128, 0, m->stream>>>(src, static_cast<double*>(dst), m->ncells);
+  else
+    k_to_compute<float><<<grid, 128, 0, m->stream>>>(src, static_cast<float*>(dst), m->ncells);
+  return after_launch(m, "field conversion launch");
+}
+
 lbm_status launch_density_history(lbm_model* m) {
   GenParams p;
   gen_params(m, &p);

@@ -294,6 +294,8 @@ lbm_status lbm_batch_add(lbm_batch* b, lbm_model* m) {
     return set_error(LBM_ERR_NOT_IMPLEMENTED, "the rate and CDE variants are not available inside a batch");
   if (m->m2g_aniso)
     return set_error(LBM_ERR_NOT_IMPLEMENTED, "the density-gradient term of M2G is not available inside a batch");
+  if (m->a2 != 0.0)
+    return set_error(LBM_ERR_NOT_IMPLEMENTED, "the cross-diffusion term is not available inside a batch");
   for (int k = 4; k <= kMaxOrder; ++k)
     if (m->s_order[k] > 0.0)
       return set_error(LBM_ERR_NOT_IMPLEMENTED, "distinct higher-order rates are not available inside a batch");

@@ -121,9 +121,16 @@ void make_step_params(const lbm_model* m, StepParams<CT>* p) {
   }
   // (delta4 . u) . grad rho of Eq. (M2Ga) on the single-speed lattices: delta4_aaaa = c_a^2 - 3 c_s^2,
   // d_a rho by the central difference over the cell spacing c_a (dt = 1)
-  p->aniso = m->m2g_aniso ? 1 : 0;
-  if (m->m2g_aniso)
-    for (int a = 0; a < L->d; ++a) p->dgrad[a] = CT((L->c[a] * L->c[a] - 3.0 * m->cs2_eq) / (2.0 * L->c[a]));
+  // (the step launcher points grad_in / rho_out at the density history); the cross diffusion of
+  // the NCDE, -S1 A2 grad psi in M1G with A2 = a2 I (Eq. (M-NCDE-6)), from the prescribed psi
+  if (m->eq == LBM_NSE && m->m2g_aniso) {
+    p->grad_on = 1;
+    for (int a = 0; a < L->d; ++a) p->gscale[a] = CT((L->c[a] * L->c[a] - 3.0 * m->cs2_eq) / (2.0 * L->c[a]));
+  } else if (m->eq == LBM_NCDE && m->a2 != 0.0) {
+    p->grad_on = 1;
+    for (int a = 0; a < L->d; ++a) p->gscale[a] = CT(m->a2 / (2.0 * L->c[a]));
+    p->grad_in = static_cast<const CT*>(m->psi);
+  }
   p->sh_rho_ref = CT(m->s_high * rho_ref);
   p->s_high = CT(m->s_high);
   p->one_minus_sh = CT(1.0 - m->s_high);
@@ -237,8 +244,9 @@ Layout layout(const lbm_lattice* L, int eq, const int64_t* n, int store) {
   Layout lo;
   lo.f_bytes = align_up(size_t(L->Q) * size_t(ncells) * dtype_bytes(store));
   lo.phi_off = 2 * lo.f_bytes;
-  // NCDE: phi of the previous step; single-speed NSE: two density fields for the M2G gradient
-  const size_t fields = eq == LBM_NCDE ? 1 : (lattice_single(L->kind) ? 2 : 0);
+  // NCDE: phi of the previous step and psi of the cross diffusion; single-speed NSE: two density
+  // fields for the M2G gradient
+  const size_t fields = eq == LBM_NCDE || lattice_single(L->kind) ? 2 : 0;
   const size_t phi_bytes = fields * align_up(size_t(ncells) * cbytes);
   lo.force_off = lo.phi_off + phi_bytes;
   lo.part_off = lo.force_off + align_up(size_t(nmax) * cbytes);
@@ -484,10 +492,11 @@ lbm_status lbm_model_create(const lbm_lattice* L, lbm_eq eq, const int64_t* n, l
     m->f[0] = base;
     m->f[1] = base + lo.f_bytes;
     m->phi_prev = eq == LBM_NCDE ? base + lo.phi_off : nullptr;
+    const size_t field_bytes = align_up(size_t(m->ncells) * (store == LBM_F64 ? 8 : 4));
+    if (eq == LBM_NCDE) m->psi = base + lo.phi_off + field_bytes;
     if (eq == LBM_NSE && lattice_single(L->kind)) {
-      const size_t cbytes = store == LBM_F64 ? 8 : 4;
       m->rho_hist[0] = base + lo.phi_off;
-      m->rho_hist[1] = base + lo.phi_off + align_up(size_t(m->ncells) * cbytes);
+      m->rho_hist[1] = base + lo.phi_off + field_bytes;
     }
     m->force_tab = base + lo.force_off;
     m->partials = reinterpret_cast<double*>(base + lo.part_off);
@@ -605,11 +614,43 @@ lbm_status lbm_model_set_ncde_variant(lbm_model* m, lbm_ncde_variant variant, do
   if (int(variant) < LBM_NCDE_MOMENT || int(variant) > LBM_NCDE_CDE) return set_error(LBM_ERR_ARG, "unknown NCDE variant");
   if (!std::isfinite(a1)) return set_error(LBM_ERR_ARG, "a1 must be finite");
   if (variant == LBM_NCDE_CDE && a1 != 0.0) return set_error(LBM_ERR_ARG, "the CDE variant has no mixed-derivative term");
+  if (variant == LBM_NCDE_CDE && m->a2 != 0.0) return set_error(LBM_ERR_ARG, "the CDE variant has no cross-diffusion term");
   if (m->batch && variant != LBM_NCDE_MOMENT)
     return set_error(LBM_ERR_NOT_IMPLEMENTED, "the rate and CDE variants are not available inside a batch");
   m->ncde_variant = variant;
   m->a1 = a1;
   batch_mark_dirty(m->batch);
+  return LBM_OK;
+}
+
+lbm_status lbm_model_set_ncde_cross_diffusion(lbm_model* m, double a2, const double* psi, int on_device) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (m->eq != LBM_NCDE) return set_error(LBM_ERR_ARG, "the cross-diffusion term applies to the NCDE model");
+  if (!std::isfinite(a2)) return set_error(LBM_ERR_ARG, "a2 must be finite");
+  if (a2 == 0.0) {
+    m->a2 = 0.0;
+    return LBM_OK;
+  }
+  if (!psi) return set_error(LBM_ERR_ARG, "psi is NULL");
+  if (m->ncde_variant == LBM_NCDE_CDE) return set_error(LBM_ERR_ARG, "the CDE variant has no cross-diffusion term");
+  if (m->batch) return set_error(LBM_ERR_NOT_IMPLEMENTED, "the cross-diffusion term is not available inside a batch");
+  DeviceGuard guard(m->device);
+  const size_t bytes = size_t(m->ncells) * sizeof(double);
+  lbm_status st = with_staging(m, bytes, !on_device, [&](void* tmp) -> lbm_status {
+    const double* src = psi;
+    if (tmp) {
+      cudaError_t err = cudaMemcpyAsync(tmp, psi, bytes, cudaMemcpyHostToDevice, m->stream);
+      if (err != cudaSuccess) return cuda_error(err, "psi upload");
+      src = static_cast<const double*>(tmp);
+    }
+    return launch_to_compute(m, src, m->psi);
+  });
+  if (st != LBM_OK) return st;
+  if (!on_device) {
+    cudaError_t err = cudaStreamSynchronize(m->stream);
+    if (err != cudaSuccess) return cuda_error(err, "psi upload");
+  }
+  m->a2 = a2;
   return LBM_OK;
 }
 

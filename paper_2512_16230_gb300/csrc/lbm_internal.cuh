@@ -51,6 +51,10 @@ struct lbm_model {
   void* rho_hist[2];
   int hist_cur;
   bool m2g_aniso;
+  // NCDE: the prescribed field psi of the cross-diffusion term (D-bar = psi I, compute dtype) and
+  // its coefficient A2 = a2 I (Eq. (GNCDE)); a2 = 0: no term
+  void* psi;
+  double a2;
   void* force_tab;  // NSE: F_a as a function of the cell index along axis b (compute dtype)
   double* partials; // reduction scratch of the conservation sums
   double* sums;     // 4 doubles
@@ -108,12 +112,14 @@ struct StepParams {
   CT nonlin_rate, a1;
   CT cde_coef[3];
   CT half0;
-  // single-speed NSE with the delta4 term of M2G: dgrad_a = (c_a^2 - 3 cs2_eq) / (2 c_a) turns the
-  // central difference of the previous-step density (rho_in) along axis a into
-  // (c_a^2 - 3 cs2_eq) d_a rho; the step writes its density to rho_out
-  int aniso;
-  CT dgrad[3];
-  const CT* rho_in;
+  // A central-difference gradient term (grad_on): gr_a = gscale_a (g(x + e_a) - g(x - e_a)) of the
+  // cell field g = grad_in. NSE on rD2Q9 / rD3Q27: g is the previous step's density and
+  // gscale_a = (c_a^2 - 3 cs2_eq) / (2 c_a), the delta4 term of M2G (Eq. (M2Ga)); the step writes
+  // its own density to rho_out. NCDE: g = psi of the cross diffusion D-bar = psi I and
+  // gscale_a = a2 / (2 c_a), the A2 term of M1G (Eq. (M-NCDE-6)).
+  int grad_on;
+  CT gscale[3];
+  const CT* grad_in;
   CT* rho_out;
   int n[3];
   int ncells;
@@ -302,6 +308,7 @@ lbm_status launch_fields(lbm_model* m, double* rho, double* u);
 lbm_status launch_sums(lbm_model* m);                          // into m->sums (device)
 lbm_status launch_phi_from_populations(lbm_model* m);          // NCDE: phi_prev = sum f-bar
 lbm_status launch_density_history(lbm_model* m);               // single-speed NSE: rho_hist[hist_cur] = sum f-bar
+lbm_status launch_to_compute(lbm_model* m, const double* src, void* dst);  // a cell field in the compute dtype
 // The conservation-sum kernels with caller-provided reduction scratch (partial_slots x 4
 // doubles, at least kRedBlocks slots) and result (4 doubles, device memory).
 lbm_status launch_sums_into(lbm_model* m, double* partials, int partial_slots, double* out);

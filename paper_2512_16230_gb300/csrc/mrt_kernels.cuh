@@ -261,8 +261,9 @@ struct NcdeCell {
 // second-order rows, where the d x d block S_n carries the bulk coupling of Eq. (4-27).
 // sigma: NSE (I - S/2) M1F = (1 - s/2) F on order 1 and M2G = (I - S2/2)(uF + Fu) on order 2,
 // plus, given gr (single-speed lattices), the diagonal (delta4 . u) . grad rho of Eq. (M2Ga) with
-// gr_a = (c_a^2 - 3 c_s^2) d_a rho; NCDE M1G = (I - S1/2) u d_t phi - S1 A1 d_t(u phi) on order 1 (factor half1) and, for the
-// CDE variant, M0G = (1 - s0/2) S_G on order 0.
+// gr_a = (c_a^2 - 3 c_s^2) d_a rho; NCDE M1G = (I - S1/2) u d_t phi - S1 A1 d_t(u phi) on order 1
+// (factor half1), minus S1 A2 grad psi given gr_a = a2 d_a psi (Eq. (M-NCDE-6), D-bar = psi I),
+// and, for the CDE variant, M0G = (1 - s0/2) S_G on order 0.
 template <class L, class CT, int EQ, int r, class P>
 __device__ __forceinline__ CT row_update(const P& p, const CT (&meq)[L::R], const CT (&neq)[L::R],
                                          const CT (&u)[3], const CT (&F)[3], CT dphi, const NcdeCell<CT>& nc,
@@ -290,6 +291,7 @@ __device__ __forceinline__ CT row_update(const P& p, const CT (&meq)[L::R], cons
       } else {
         relax = nc.sd1[a] * neq[r];
         sig = nc.half1[a] * p.u_const[a] * dphi;
+        if (gr != nullptr) sig = fma(-(nc.sd1[a] + p.s_high), gr[a], sig);
       }
     } else if constexpr (deg == 0 && EQ == LBM_NCDE && P::kNcdeVariants) {
       sig = p.half0 * nc.sg;
@@ -621,28 +623,29 @@ __device__ __forceinline__ void body_force(int force_a, int force_b, const CT* f
   }
 }
 
-// The M2G term of Eq. (M2Ga) on the single-speed lattices needs grad rho: gr_a =
-// (c_a^2 - 3 c_s^2) d_a rho from the central difference of the previous step's density (p.rho_in)
-// at the periodic neighbours of cell (x, y, z); zero when the term is off.
-template <class L, class CT, int EQ>
-struct M2gGradient {
-  static constexpr bool kOn = L::SINGLE && EQ == LBM_NSE;
+// Gradient terms of the source moments: the delta4 term of M2G (Eq. (M2Ga)) on the single-speed
+// lattices needs grad rho, the cross-diffusion term of M1G (Eq. (M-NCDE-6)) grad psi. Both take
+// gr_a = gscale_a (g(x + e_a) - g(x - e_a)), the central difference of the cell field p.grad_in at
+// the periodic neighbours of cell (x, y, z); zero when the term is off.
+template <class L, int EQ>
+struct GradTerm {
+  static constexpr bool kOn = (L::SINGLE && EQ == LBM_NSE) || EQ == LBM_NCDE;
 };
 template <class L, class CT>
-__device__ __forceinline__ void m2g_density_gradient(const StepParams<CT>& p, int cell, int x, int y, int z,
-                                                     CT (&gr)[3]) {
+__device__ __forceinline__ void cell_field_gradient(const StepParams<CT>& p, int cell, int x, int y, int z,
+                                                    CT (&gr)[3]) {
   gr[0] = gr[1] = gr[2] = CT(0);
-  if (!p.aniso) return;
+  if (!p.grad_on) return;
   const int nx = p.n[0], ny = p.n[1];
-  const CT* r = p.rho_in;
+  const CT* g = p.grad_in;
   const int xp = x + 1 == nx ? -x : 1, xm = x == 0 ? nx - 1 : -1;
-  gr[0] = p.dgrad[0] * (r[cell + xp] - r[cell + xm]);
+  gr[0] = p.gscale[0] * (g[cell + xp] - g[cell + xm]);
   const int yp = (y + 1 == ny ? -y : 1) * nx, ym = (y == 0 ? ny - 1 : -1) * nx;
-  gr[1] = p.dgrad[1] * (r[cell + yp] - r[cell + ym]);
+  gr[1] = p.gscale[1] * (g[cell + yp] - g[cell + ym]);
   if constexpr (L::D == 3) {
     const int nz = p.n[2], nxy = nx * ny;
     const int zp = (z + 1 == nz ? -z : 1) * nxy, zm = (z == 0 ? nz - 1 : -1) * nxy;
-    gr[2] = p.dgrad[2] * (r[cell + zp] - r[cell + zm]);
+    gr[2] = p.gscale[2] * (g[cell + zp] - g[cell + zm]);
   }
 }
 
@@ -667,13 +670,13 @@ __global__ void __launch_bounds__(kBlock, LBM_K1_MIN_BLOCKS) k_step(const StepPa
     body_force(p.force_a, p.force_b, p.force_tab, nb.x, nb.y, nb.z, F);
     CT phi_prev = CT(0), phi_now = CT(0);
     if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
-    constexpr bool AG = M2gGradient<L, CT, EQ>::kOn;
+    constexpr bool AG = GradTerm<L, EQ>::kOn;
     CT gr[3];
-    if constexpr (AG) m2g_density_gradient<L>(p, cell, nb.x, nb.y, nb.z, gr);
+    if constexpr (AG) cell_field_gradient<L>(p, cell, nb.x, nb.y, nb.z, gr);
     collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, static_cast<NoHigh*>(nullptr), AG ? gr : nullptr);
     if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
-    if constexpr (AG) {
-      if (p.aniso) p.rho_out[cell] = phi_now;
+    if constexpr (AG && EQ == LBM_NSE) {
+      if (p.grad_on) p.rho_out[cell] = phi_now;
     }
   }
   static_for<L::Q>([&](auto i) {
@@ -709,13 +712,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_step_high(const StepParams<CT> p,
   body_force(p.force_a, p.force_b, p.force_tab, nb.x, nb.y, nb.z, F);
   CT phi_prev = CT(0), phi_now = CT(0);
   if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
-  constexpr bool AG = M2gGradient<L, CT, EQ>::kOn;
+  constexpr bool AG = GradTerm<L, EQ>::kOn;
   CT gr[3];
-  if constexpr (AG) m2g_density_gradient<L>(p, cell, nb.x, nb.y, nb.z, gr);
+  if constexpr (AG) cell_field_gradient<L>(p, cell, nb.x, nb.y, nb.z, gr);
   collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, &tab, AG ? gr : nullptr);
   if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
-  if constexpr (AG) {
-    if (p.aniso) p.rho_out[cell] = phi_now;
+  if constexpr (AG && EQ == LBM_NSE) {
+    if (p.grad_on) p.rho_out[cell] = phi_now;
   }
   static_for<L::Q>([&](auto i) {
     constexpr int I = decltype(i)::value;
@@ -934,14 +937,14 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
     }
   }
   const bool hist = collide_on && m->m2g_aniso;
+  p.grad_on = collide_on && p.grad_on;
   for (int64_t s = 0; s < nsteps; ++s) {
     const ST* fin = static_cast<const ST*>(m->f[m->cur]);
     ST* fout = static_cast<ST*>(m->f[m->cur ^ 1]);
     if (hist) {
-      p.rho_in = static_cast<const CT*>(m->rho_hist[m->hist_cur]);
+      p.grad_in = static_cast<const CT*>(m->rho_hist[m->hist_cur]);
       p.rho_out = static_cast<CT*>(m->rho_hist[m->hist_cur ^ 1]);
     }
-    p.aniso = hist ? 1 : 0;
     bool done = false;
     if constexpr (is_deviation_storage<ST>()) {
       if (tensor) {

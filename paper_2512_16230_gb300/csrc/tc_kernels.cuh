@@ -222,17 +222,17 @@ __global__ void __launch_bounds__(128, TcShape<L, HI>::CTAS)
       });
     }
     float h[R];
-    constexpr bool AG = M2gGradient<L, float, EQ>::kOn;
+    constexpr bool AG = GradTerm<L, EQ>::kOn;
     float gr[3] = {0.f, 0.f, 0.f};
     if constexpr (AG) {
-      if (live) m2g_density_gradient<L>(p, cell, x, y, z, gr);
+      if (live) cell_field_gradient<L>(p, cell, x, y, z, gr);
     }
     collide_moments<L, float, EQ, true>(mu, p, F, phi_prev, phi_now, h, AG ? gr : nullptr);
     if constexpr (EQ == LBM_NCDE) {
       if (live) phi[cell] = phi_now;
     }
-    if constexpr (AG) {
-      if (live && p.aniso) p.rho_out[cell] = phi_now;
+    if constexpr (AG && EQ == LBM_NSE) {
+      if (live && p.grad_on) p.rho_out[cell] = phi_now;
     }
     // per-cell power-of-two scale, then h = high + low in 16 bits each (z rides with h's scale)
     float hmax = 0.f;
@@ -468,17 +468,17 @@ __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<floa
     body_force(p.force_a, p.force_b, p.force_tab, x, y, z, F);
     float phi_prev = 0.f, phi_now = 0.f;
     if constexpr (EQ == LBM_NCDE) phi_prev = live ? phi[cell] : 0.f;
-    constexpr bool AG = M2gGradient<L, float, EQ>::kOn;
+    constexpr bool AG = GradTerm<L, EQ>::kOn;
     float gr[3] = {0.f, 0.f, 0.f};
     if constexpr (AG) {
-      if (live) m2g_density_gradient<L>(p, cell, x, y, z, gr);
+      if (live) cell_field_gradient<L>(p, cell, x, y, z, gr);
     }
     collide<L, float, EQ, false>(f, p, F, phi_prev, phi_now, static_cast<NoHigh*>(nullptr), AG ? gr : nullptr);
     if constexpr (EQ == LBM_NCDE) {
       if (live) phi[cell] = phi_now;
     }
-    if constexpr (AG) {
-      if (live && p.aniso) p.rho_out[cell] = phi_now;
+    if constexpr (AG && EQ == LBM_NSE) {
+      if (live && p.grad_on) p.rho_out[cell] = phi_now;
     }
     bool ok = tc::mbar_wait_bounded(&sm.mbar, phase, tp.wait_limit);
     phase ^= 1u;

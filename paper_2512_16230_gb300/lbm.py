@@ -51,6 +51,7 @@ SIGNATURES = {
     "lbm_model_set_ncde": (c_int, [_P, _PD, c_double]),
     "lbm_model_set_ncde_variant": (c_int, [_P, c_int, c_double]),
     "lbm_model_set_m2g_anisotropy": (c_int, [_P, c_int]),
+    "lbm_model_set_ncde_cross_diffusion": (c_int, [_P, c_double, _P, c_int]),
     "lbm_model_set_tensor_cores": (c_int, [_P, c_int]),
     "lbm_model_init_fields": (c_int, [_P, _P, _P, c_int]),
     "lbm_model_set_populations": (c_int, [_P, _P, c_int]),
@@ -276,6 +277,21 @@ class Model:
         CDE); a1 is the mixed-derivative coefficient of Eq. (GNCDE)."""
         _check(load().lbm_model_set_ncde_variant(self.handle, NCDE_VARIANTS[variant], float(a1)),
                "lbm_model_set_ncde_variant")
+
+    def set_ncde_cross_diffusion(self, a2, psi=None):
+        """NCDE: the cross-diffusion term of Eq. (GNCDE) with A2 = a2 I and D-bar = psi I (psi: a
+        host or device field of the grid's shape, FP64)."""
+        if psi is None:
+            _check(load().lbm_model_set_ncde_cross_diffusion(self.handle, float(a2), None, 0),
+                   "lbm_model_set_ncde_cross_diffusion")
+            return
+        if int(np.prod(np.shape(psi))) != self.ncells:
+            raise ValueError("psi must hold one value per cell")
+        p, dev, keep = _ptr(psi)
+        _check(load().lbm_model_set_ncde_cross_diffusion(self.handle, float(a2), c_void_p(p), int(dev)),
+               "lbm_model_set_ncde_cross_diffusion")
+        if dev:
+            self._keep = keep
 
     def set_m2g_anisotropy(self, enable=1):
         """rD2Q9 / rD3Q27 NSE: add (delta4 . u) . grad rho to M2G (Eq. (M2Ga)), with grad rho

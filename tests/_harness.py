@@ -30,15 +30,17 @@ def gpu_lattice(spec):
 
 
 def oracle_model(spec, eq, n, s, s_high=1.0, force=None, u_const=None, nonlin=0.0, cs2_eq=None, lat=None,
-                 s_bulk=None, s_orders=None, ncde_mode="moment", a1=0.0, m2g_aniso=False):
+                 s_bulk=None, s_orders=None, ncde_mode="moment", a1=0.0, m2g_aniso=False, a2=0.0, psi=None):
     lat = lat or oracle_lattice(spec)
     return OM.Model(lat, eq, n, np.asarray(s, dtype=float), s_high, cs2_eq=cs2_eq, force=force,
                     u_const=None if u_const is None else np.asarray(u_const, dtype=float), nonlin=nonlin,
-                    s_bulk=s_bulk, s_orders=s_orders, ncde_mode=ncde_mode, a1=a1, m2g_aniso=m2g_aniso)
+                    s_bulk=s_bulk, s_orders=s_orders, ncde_mode=ncde_mode, a1=a1, m2g_aniso=m2g_aniso,
+                    a2=a2, psi=psi)
 
 
 def gpu_model(spec, eq, n, s, s_high=1.0, force=None, u_const=None, nonlin=0.0, cs2_eq=None, store="f32",
-              lat=None, s_bulk=None, s_orders=None, ncde_mode="moment", a1=0.0, m2g_aniso=False):
+              lat=None, s_bulk=None, s_orders=None, ncde_mode="moment", a1=0.0, m2g_aniso=False, a2=0.0,
+              psi=None):
     from paper_2512_16230_gb300 import lbm
     lat = lat or gpu_lattice(spec)
     m = lbm.Model(lat, eq, n, store=store)
@@ -57,6 +59,8 @@ def gpu_model(spec, eq, n, s, s_high=1.0, force=None, u_const=None, nonlin=0.0, 
         m.set_ncde_variant(ncde_mode, a1)
     if m2g_aniso:
         m.set_m2g_anisotropy(1)
+    if a2:
+        m.set_ncde_cross_diffusion(a2, psi)
     return m
 
 

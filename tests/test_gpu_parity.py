@@ -539,3 +539,84 @@ def test_m2g_anisotropy_errors():
         gm.set_m2g_anisotropy(2)
     gm.set_m2g_anisotropy(1)
     gm.set_m2g_anisotropy(0)
+
+
+CROSS_VARIANTS = [  # (store, NCDE variant, a1, per-order rates, tensor cores)
+    ("f64", "moment", 0.0, False, 0), ("f32", "moment", 0.4, False, 0), ("f64", "rate", 0.0, False, 0),
+    ("f32", "rate", -0.3, False, 0), ("f32", "moment", 0.0, True, 0), ("f32", "moment", 0.0, True, 1)]
+
+
+@pytest.mark.parametrize("store,variant,a1,high,tensor", CROSS_VARIANTS)
+@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q25", "rD3Q33", "rD3Q53", "rD2Q9"])
+def test_ncde_cross_diffusion_steps(name, store, variant, a1, high, tensor):
+    """The cross-diffusion term of Eq. (GNCDE) (A2 = a2 I, D-bar = psi I, grad psi by central
+    differences) with a random psi on a ragged grid: three steps from far-from-equilibrium
+    populations against the oracle, with the moment and per-cell-rate variants, the mixed
+    derivative, the per-order-rate kernels and the FP32 tensor-core kernel. The term moves the
+    oracle's populations by more than 20 times the GPU-oracle difference."""
+    spec = ALL_SPECS[name]
+    d = spec.d
+    n = RAGGED[d]
+    s = _random_rates(spec.R, 19)
+    psi = round_to_store(I.random_scalar(n, seed=29), store)
+    kw = dict(s_high=1.2, u_const=tuple(np.linspace(0.04, 0.08, d)), nonlin=1.0, ncde_mode=variant, a1=a1,
+              s_orders=HIGH_RATES if high else None)
+    om = oracle_model(spec, "ncde", n, s, a2=0.05, psi=psi, **kw)
+    ref = oracle_model(spec, "ncde", n, s, **kw)
+    gm = gpu_model(spec, "ncde", n, s, store=store, a2=0.05, psi=psi, **kw)
+    if store != "f64":
+        gm.set_tensor_cores(tensor)
+    f0 = round_to_store(I.random_populations(n, om.lat.Q, seed=31), store)
+    for m in (om, ref, gm):
+        m.set_populations(f0)
+    for _ in range(3):
+        om.step(1)
+        ref.step(1)
+        gm.step(1)
+        err = rel_l2(gm.get_populations(), om.f)
+        assert err <= TOL[store]
+    assert rel_l2(ref.f, om.f) > max(20 * err, 1e-5)
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+def test_ncde_cross_diffusion_driven_mode(store):
+    """rD2Q13 at rest driven by psi = cos(k y) (the mode of the oracle pin, along the c = 1.25
+    axis): 300 steps against the oracle, phi within the per-dtype tolerance of its driven part."""
+    spec = ALL_SPECS["rD2Q13"]
+    n = (4, 64)
+    s = np.ones(spec.R)
+    s[1] = s[2] = 1.5
+    c = spec.c[1]
+    y = np.arange(n[1]) * c
+    psi = np.broadcast_to(np.cos(2 * math.pi * y / (n[1] * c)).reshape(n[1], 1), (n[1], n[0])).copy()
+    kw = dict(u_const=(0.0, 0.0), a2=0.02, psi=round_to_store(psi, store))
+    om = oracle_model(spec, "ncde", n, s, **kw)
+    gm = gpu_model(spec, "ncde", n, s, store=store, **kw)
+    phi0 = np.ones((n[1], n[0]))
+    om.init_fields(phi0)
+    gm.init_fields(phi0)
+    om.step(300)
+    gm.step(300)
+    phi_g, _ = gm.read_fields()
+    phi_o, _ = om.fields()
+    assert rel_l2(phi_g - 1.0, phi_o - 1.0) <= (1e-10 if store == "f64" else 1e-3)
+
+
+def test_ncde_cross_diffusion_errors():
+    from paper_2512_16230_gb300 import lbm
+    spec = ALL_SPECS["rD2Q13"]
+    gm = gpu_model(spec, "nse", (8, 8), np.ones(spec.R))
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        gm.set_ncde_cross_diffusion(0.1, np.zeros((8, 8)))
+    gm = gpu_model(spec, "ncde", (8, 8), np.ones(spec.R), u_const=(0.01, 0.0))
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        gm.set_ncde_cross_diffusion(0.1, None)
+    gm.set_ncde_cross_diffusion(0.1, np.zeros((8, 8)))
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        gm.set_ncde_variant("cde")
+    gm.set_ncde_cross_diffusion(0.0)
+    gm.set_ncde_variant("cde")
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        gm.set_ncde_cross_diffusion(0.1, np.zeros((8, 8)))
+    with pytest.raises(ValueError):
+        gm.set_ncde_cross_diffusion(0.1, np.zeros((4, 8)))

@@ -195,3 +195,29 @@ def test_tensor_core_m2g_anisotropy_step(name, store):
     om.step(1)
     err = rel_l2(gm.get_populations() - w, om.f - w)
     assert err <= 4 * UNIT[store]
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q25", "rD3Q53"])
+def test_tensor_core_ncde_cross_diffusion_step(name, store):
+    """The cross-diffusion term of Eq. (GNCDE) in the 16-bit tensor-core kernel (psi rounded to
+    FP32 on both sides): one step against the FP64 oracle fed the stored deviations."""
+    from _harness import round_to_store
+    spec = ALL_SPECS[name]
+    d = spec.d
+    n = RAGGED[d]
+    s = np.random.default_rng(43).uniform(0.6, 1.9, spec.R)
+    psi = round_to_store(I.random_scalar(n, seed=3), "f32")
+    kw = dict(s_high=1.3, u_const=tuple(np.linspace(0.03, 0.06, d)), nonlin=1.0, a2=0.05, psi=psi)
+    gm = gpu_model(spec, "ncde", n, s, store=store, **kw)
+    om = oracle_model(spec, "ncde", n, s, **kw)
+    gm.set_tensor_cores(1)
+    w = om.lat.w.reshape((-1,) + (1,) * d)
+    r = np.random.default_rng(8).uniform(-0.1, 0.1, size=(gm.Q,) + n[::-1])
+    f_in = w * (1.0 + r)
+    gm.set_populations(f_in)
+    om.set_populations(w + _stored_deviation(f_in, w, store))
+    gm.step(1)
+    om.step(1)
+    err = rel_l2(gm.get_populations() - w, om.f - w)
+    assert err <= 4 * UNIT[store]
