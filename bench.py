@@ -59,7 +59,10 @@ def _config(extra=None, grid=GRID, store="f32"):
                     f"{STORE_DTYPE[store][2]}",
         "lattice": "rD3Q53", "cells": int(math.prod(grid)), "grid": list(grid), "Q": Q,
         "store": store, "compute": "f32",
-        "l2": "inputs larger than L2 (2 x 2.67 GB population arrays vs 129 MB L2), no flush",
+        "l2": ("inputs larger than L2 (2 x {:.3g} GB population arrays vs 129 MB L2), no flush"
+               if Q * math.prod(grid) * STORE_DTYPE[store][1] > 129e6 else
+               "population arrays of 2 x {:.3g} GB fit in the 129 MB L2: not an HBM measurement").format(
+            Q * math.prod(grid) * STORE_DTYPE[store][1] / 1e9),
         "parallelism": "replicas",
     }
     if extra:
