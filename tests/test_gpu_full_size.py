@@ -1,0 +1,134 @@
+"""Parity at the full sizes of the benchmark configurations, in the launch configuration the
+benchmark times (one lbm.Model, default kernel choice, the workload's own storage).
+
+The oracle cannot run these grids, so the checks are (1) sampled outputs the oracle computes one
+by one: after the first step from the analytic initial fields, f_i(x) = f~_i(x - e_i), so the
+oracle collides just the source cells x - e_i of each sampled cell x (the equilibrium of the
+initial fields there), including cells on every face and corner of the periodic box; and (2)
+properties that hold at any size (conservation of mass and momentum, energy decay).
+"""
+import numpy as np
+import pytest
+
+from paper_2512_16230_gb300 import workloads as W
+
+from _harness import gpu_model, oracle_lattice, oracle_model, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(autouse=True)
+def _lib(lbm_lib):
+    return lbm_lib
+
+
+def _sample_cells(n, count, seed):
+    """Cell coordinates (x, y[, z]): every corner of the box plus seeded interior and face cells."""
+    rng = np.random.default_rng(seed)
+    d = len(n)
+    corners = [tuple((n[a] - 1) * ((k >> a) & 1) for a in range(d)) for k in range(2 ** d)]
+    rest = [tuple(int(rng.integers(0, n[a])) if a != (k % d) else int((n[a] - 1) * (k % 2))
+                  for a in range(d)) for k in range(count // 2)]
+    inner = [tuple(int(rng.integers(0, n[a])) for a in range(d)) for _ in range(count - count // 2)]
+    return corners + rest + inner
+
+
+def _oracle_first_step(wl, cells, rho, u):
+    """f_i(x) after one step for each sampled cell x: the oracle collides, on a one-dimensional
+    list of cells, the equilibrium of the initial fields at every source cell x - e_i."""
+    spec = wl.lattice
+    lat = oracle_lattice(spec)
+    d, Q = lat.d, lat.Q
+    n = wl.n
+    src = []
+    for x in cells:
+        for i in range(Q):
+            src.append(tuple((x[a] - int(lat.e[i, a])) % n[a] for a in range(d)))
+    idx = tuple(np.array([y[a] for y in src]) for a in reversed(range(d)))   # numpy order (z, y, x)
+    M = len(src)
+    grid = (M,) + (1,) * (d - 1)
+    shape = tuple(reversed(grid))
+    om = oracle_model(spec, wl.eq, grid, wl.s, wl.s_high, force=wl.force, u_const=wl.u_const,
+                      nonlin=wl.nonlin)
+    if wl.eq == "nse":
+        om.init_fields(rho[idx].reshape(shape), np.stack([u[a][idx] for a in range(d)]).reshape((d,) + shape))
+    else:
+        om.init_fields(rho[idx].reshape(shape))
+    ft = om.collide().reshape(Q, M)
+    return np.array([[ft[i, s * Q + i] for s in range(len(cells))] for i in range(Q)])
+
+
+def _gpu_first_step(wl, cells, rho, u):
+    import torch
+    spec = wl.lattice
+    gm = gpu_model(spec, wl.eq, wl.n, wl.s, wl.s_high, force=wl.force, u_const=wl.u_const, nonlin=wl.nonlin,
+                   store=wl.store)
+    gm.init_fields(rho, None if u is None else np.ascontiguousarray(u))
+    gm.step(1)
+    out = torch.empty((gm.Q,) + tuple(reversed(wl.n)), dtype=torch.float64, device="cuda")
+    gm.get_populations(out)
+    gm.synchronize()
+    idx = tuple(torch.tensor([x[a] for x in cells], device="cuda") for a in reversed(range(len(wl.n))))
+    got = out[(slice(None),) + idx].cpu().numpy()
+    del out
+    gm.close()
+    torch.cuda.empty_cache()
+    return got
+
+
+def test_config3_full_size_first_step_sampled():
+    """rD3Q53 Taylor-Green, 256 x 256 x 192, FP32 (the benchmark workload): one step from the
+    analytic fields, all 53 populations at 72 sampled cells (the 8 corners, cells on the faces and
+    inside) against the oracle's per-cell collisions, within the FP32 parity bound."""
+    wl = W.taylor_green_3d()
+    rho, u = wl.fields()
+    cells = _sample_cells(wl.n, 64, seed=5)
+    got = _gpu_first_step(wl, cells, rho, u)
+    want = _oracle_first_step(wl, cells, rho, u)
+    assert rel_l2(got, want) <= TOL["f32"]
+    assert np.abs(got - want).max() <= 10 * TOL["f32"] * np.abs(want).max()
+
+
+@pytest.mark.parametrize("store", ["f32", "f64"])
+def test_config2_full_size_first_step_sampled(store):
+    """rD2Q13 nonlinear CDE hill, 1024 x 768, FP32 and FP64: one step from the seeded fields at
+    68 sampled cells against the oracle's per-cell collisions (phi^{-1} = phi^0 on both sides)."""
+    wl = W.ncde_hill(store=store)
+    phi, _ = wl.fields()
+    cells = _sample_cells(wl.n, 64, seed=6)
+    got = _gpu_first_step(wl, cells, phi, None)
+    want = _oracle_first_step(wl, cells, phi, None)
+    assert rel_l2(got, want) <= TOL[store]
+
+
+def _mirror(a, axis):
+    """a(-x) along numpy axis `axis` of a periodic grid (cell i -> (n - i) mod n)."""
+    return np.roll(np.flip(a, axis=axis), 1, axis=axis)
+
+
+def test_config3_full_size_invariants():
+    """The benchmark workload over 100 steps: mass and momentum are conserved (no force, no net
+    momentum), and the mirror symmetries of the Taylor-Green field (x -> -x, y -> -y, z -> -z about
+    the origin of the periodic box, under which u_a is odd along axis a and even along the others,
+    and rho is even) survive on the symmetric lattice to FP32 rounding, through every wrap."""
+    wl = W.taylor_green_3d()
+    spec = wl.lattice
+    gm = gpu_model(spec, wl.eq, wl.n, wl.s, wl.s_high, store=wl.store)
+    rho, u = wl.fields()
+    gm.init_fields(rho, np.ascontiguousarray(u))
+    s0 = gm.conserved_sums()
+    gm.step(100)
+    s1 = gm.conserved_sums()
+    r, v = gm.read_fields()
+    gm.close()
+    u0 = wl.init["u0"]
+    assert abs(s1[0] - s0[0]) <= 1e-5 * s0[0]
+    assert np.abs(s1[1:]).max() <= 1e-5 * wl.ncells * u0
+    for a in range(3):
+        ax = 2 - a                                   # numpy axis of spatial axis a
+        assert np.abs(_mirror(r, ax) - r).max() <= 1e-5
+        for b in range(3):
+            sign = -1.0 if b == a else 1.0
+            assert np.abs(_mirror(v[b], ax) - sign * v[b]).max() <= 1e-5 * u0
