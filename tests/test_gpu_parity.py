@@ -207,6 +207,8 @@ def test_invalid_arguments_are_rejected():
     lat = gpu_lattice(spec)
     with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
         lbm.Model(lat, "nse", (1, 8, 8))
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):        # 2^31 cells: rejected before any allocation
+        lbm.Model(lat, "nse", (2048, 2048, 512))
     with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
         lbm.Lattice("rD3Q53", spec.c, spec.cs2, ())
     with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
