@@ -69,6 +69,33 @@ __device__ __forceinline__ uint16_t round16(float v) {
   else return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
+// Two values rounded to 16 bits in one packed conversion (a in the low half, b in the high half),
+// each rounded to nearest as round16 does; split16x2 adds the low parts v - high (also rounded).
+template <class ST>
+__device__ __forceinline__ uint32_t pack16x2(float a, float b) {
+  if constexpr (std::is_same<ST, __half>::value) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+template <class ST>
+__device__ __forceinline__ void split16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  float2 hf;
+  if constexpr (std::is_same<ST, __half>::value) {
+    const __half2 h = __floats2half2_rn(a, b);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    hf = __half22float2(h);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    hf = __bfloat1622float2(h);
+  }
+  lo = pack16x2<ST>(a - hf.x, b - hf.y);
+}
+
 constexpr int kTcCols = 128;  // TMEM columns per CTA: D1 in [0, N1), then D2 in [0, QP)
 
 template <class L, class ST, int EQ, bool HI>
@@ -242,20 +269,18 @@ __global__ void __launch_bounds__(128, TcShape<L, HI>::CTAS)
     const float sc = (live && hmax > 0.f && ex >= 1u && ex <= 252u) ? __uint_as_float((254u - ex) << 23) : 1.f;
     uint32_t hp[K2 / 2];
     static_for<K2 / 2>([&](auto j) { hp[decltype(j)::value] = 0u; });
-    static_for<R>([&](auto k) {
-      constexpr int K = decltype(k)::value;
-      const float v = live ? h[K] * sc : 0.f;
-      const uint16_t hi = round16<ST>(v);
-      const float hif = float(RawCodec<ST>::dec(from_bits16<ST>(hi)));
-      const uint16_t lo = round16<ST>(v - hif);
-      hp[K / 2] |= (K & 1) ? (uint32_t(hi) << 16) : uint32_t(hi);
-      hp[(RP + K) / 2] |= (K & 1) ? (uint32_t(lo) << 16) : uint32_t(lo);
+    static_for<RP / 2>([&](auto k) {  // h in pairs (K, K + 1): high parts, then low parts
+      constexpr int K = 2 * decltype(k)::value;
+      const float a = (K < R && live) ? h[K < R ? K : 0] * sc : 0.f;
+      const float b = (K + 1 < R && live) ? h[K + 1 < R ? K + 1 : 0] * sc : 0.f;
+      split16x2<ST>(a, b, hp[K / 2], hp[(RP + K) / 2]);
     });
     if constexpr (HI) {
-      static_for<NH>([&](auto k) {
-        constexpr int K = decltype(k)::value;
-        const uint16_t b = round16<ST>(live ? zr[K] * sc : 0.f);
-        hp[(2 * RP + K) / 2] |= (K & 1) ? (uint32_t(b) << 16) : uint32_t(b);
+      static_for<NHP / 2>([&](auto k) {
+        constexpr int K = 2 * decltype(k)::value;
+        const float a = (K < NH && live) ? zr[K < NH ? K : 0] * sc : 0.f;
+        const float b = (K + 1 < NH && live) ? zr[K + 1 < NH ? K + 1 : 0] * sc : 0.f;
+        hp[(2 * RP + K) / 2] = pack16x2<ST>(a, b);
       });
     }
     static_for<K2 / 8>([&](auto c) {
@@ -368,6 +393,7 @@ __device__ __forceinline__ void split16(float v, uint16_t& hi, uint16_t& lo) {
   lo = __half_as_ushort(__float2half_rn(v - __half2float(h)));
 }
 
+
 template <class L, int EQ>
 __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<float> p, const TcParams tp,
                                                            const float* __restrict__ fin, float* __restrict__ fout,
@@ -441,11 +467,9 @@ __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<floa
       uint32_t wh[4], wl[4];
       static_for<4>([&](auto j) {
         constexpr int I0 = 8 * C + 2 * decltype(j)::value;
-        uint16_t h0 = 0, l0 = 0, h1 = 0, l1 = 0;
-        if constexpr (I0 < Q) split16(f[I0 < Q ? I0 : 0] * sa, h0, l0);
-        if constexpr (I0 + 1 < Q) split16(f[I0 + 1 < Q ? I0 + 1 : 0] * sa, h1, l1);
-        wh[decltype(j)::value] = uint32_t(h0) | (uint32_t(h1) << 16);
-        wl[decltype(j)::value] = uint32_t(l0) | (uint32_t(l1) << 16);
+        const float a = I0 < Q ? f[I0 < Q ? I0 : 0] * sa : 0.f;
+        const float b = I0 + 1 < Q ? f[I0 + 1 < Q ? I0 + 1 : 0] * sa : 0.f;
+        split16x2<__half>(a, b, wh[decltype(j)::value], wl[decltype(j)::value]);
       });
       *reinterpret_cast<uint4*>(sm.u.a.hi + kmajor_off(tid, 8 * C, QP)) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
       *reinterpret_cast<uint4*>(sm.u.a.lo + kmajor_off(tid, 8 * C, QP)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
@@ -487,7 +511,9 @@ __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<floa
       break;
     }
     tc::fence_after_sync();
-    // z_r = a_r y_r, y = D1 / sa; then its own scale and split
+    // z_r = a_r y_r, y = D1 / sa (sa a power of two, so the reciprocal is exact); then its own
+    // scale and split
+    const float inv_sa = 1.f / sa;
     float zr[NH];
     static_for<NHP / 16>([&](auto c) {
       constexpr int C = decltype(c)::value;
@@ -496,7 +522,7 @@ __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<floa
       tc::wait_ld();
       static_for<16>([&](auto j) {
         constexpr int K = 16 * C + decltype(j)::value;
-        if constexpr (K < NH) zr[K] = tp.ah[K] * (v[decltype(j)::value] / sa);
+        if constexpr (K < NH) zr[K] = tp.ah[K] * (v[decltype(j)::value] * inv_sa);
       });
     });
     float zmax = 0.f;
@@ -507,11 +533,9 @@ __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<floa
       uint32_t wh[4], wl[4];
       static_for<4>([&](auto j) {
         constexpr int K0 = 8 * C + 2 * decltype(j)::value;
-        uint16_t h0 = 0, l0 = 0, h1 = 0, l1 = 0;
-        if constexpr (K0 < NH) split16(live ? zr[K0 < NH ? K0 : 0] * sz : 0.f, h0, l0);
-        if constexpr (K0 + 1 < NH) split16(live ? zr[K0 + 1 < NH ? K0 + 1 : 0] * sz : 0.f, h1, l1);
-        wh[decltype(j)::value] = uint32_t(h0) | (uint32_t(h1) << 16);
-        wl[decltype(j)::value] = uint32_t(l0) | (uint32_t(l1) << 16);
+        const float a = (K0 < NH && live) ? zr[K0 < NH ? K0 : 0] * sz : 0.f;
+        const float b = (K0 + 1 < NH && live) ? zr[K0 + 1 < NH ? K0 + 1 : 0] * sz : 0.f;
+        split16x2<__half>(a, b, wh[decltype(j)::value], wl[decltype(j)::value]);
       });
       *reinterpret_cast<uint4*>(sm.u.a2.hi + kmajor_off(tid, 8 * C, NHP)) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
       *reinterpret_cast<uint4*>(sm.u.a2.lo + kmajor_off(tid, 8 * C, NHP)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
