@@ -245,9 +245,9 @@ lbm_status lbm_model_set_ncde(lbm_model* m, const double* u_const, double nonlin
  * a1: the mixed-derivative term of Eq. (GNCDE) with A1 = a1 I and B-bar = u phi, i.e. M1G gains
  *     -S1 A1 d_t(u phi) and the equation gains div(a1 dt d_t(u phi)) (moment and rate variants;
  *     must be 0 for the CDE).
+ * Works inside a batch (the batched step follows the variant too).
  * Errors: LBM_ERR_ARG (not an NCDE model, unknown variant, a1 or a cross-diffusion term with the
- *         CDE, non-finite a1),
- *         LBM_ERR_NOT_IMPLEMENTED (rate or CDE variant inside a batch). */
+ *         CDE, non-finite a1). */
 lbm_status lbm_model_set_ncde_variant(lbm_model* m, lbm_ncde_variant variant, double a1);
 
 /* The cross-diffusion term of Eq. (GNCDE): A2 = a2 I and D-bar = psi I for a prescribed cell
@@ -259,7 +259,7 @@ lbm_status lbm_model_set_ncde_variant(lbm_model* m, lbm_ncde_variant variant, do
  * on_device) is copied into the model in the compute dtype and stays until the next call;
  * a2 = 0 removes the term (psi may then be NULL).
  * Errors: LBM_ERR_ARG (not an NCDE model, the CDE variant, non-finite a2, NULL psi with a2 != 0),
- *         LBM_ERR_NOT_IMPLEMENTED (inside a batch), LBM_ERR_CUDA. */
+ *         LBM_ERR_CUDA. Works inside a batch. */
 lbm_status lbm_model_set_ncde_cross_diffusion(lbm_model* m, double a2, const double* psi,
                                               int on_device);
 
@@ -272,7 +272,7 @@ lbm_status lbm_model_set_ncde_cross_diffusion(lbm_model* m, double a2, const dou
  * written per cell; FP32 or FP64 as the compute dtype). Enabling takes the density of the current
  * state as the previous one, as init_fields and set_populations do (rho^{-1} = rho^0).
  * Errors: LBM_ERR_ARG (not an NSE model on rD2Q9 / rD3Q27, enable not 0 or 1),
- *         LBM_ERR_NOT_IMPLEMENTED (enabling inside a batch), LBM_ERR_CUDA. */
+ *         LBM_ERR_CUDA. Works inside a batch (the history then alternates with the batch's steps). */
 lbm_status lbm_model_set_m2g_anisotropy(lbm_model* m, int enable);
 
 /* f-bar(t = 0) = f^eq of the given fields (Eq. (feq-1)); for the NCDE phi^{-1} = phi^0.
@@ -341,7 +341,9 @@ lbm_status lbm_batch_create(void* stream, int max_solves, lbm_batch** out);
  * model runs on the batch's stream until it is removed; while a member it is advanced only by
  * lbm_batch_step (lbm_model_step returns LBM_ERR_ARG) but every other model call works (on the
  * batch's stream). Members are grouped by (lattice handle, storage dtype, equation); share one
- * lattice handle between solves of the same lattice setting so that they form one group. */
+ * lattice handle between solves of the same lattice setting so that they form one group. Every
+ * model setting carries over (NCDE variants, the cross-diffusion and M2G gradient terms) except
+ * distinct rates for the orders >= 4 (LBM_ERR_NOT_IMPLEMENTED), and FP64 storage. */
 lbm_status lbm_batch_add(lbm_batch* b, lbm_model* m);
 
 /* Remove a model (synchronizes the batch's stream; the model returns to its own stream). */

@@ -138,6 +138,25 @@ void fill_desc(const lbm_model* m, SolveDesc<float>* d) {
   d->f[0] = m->f[m->cur];
   d->f[1] = m->f[m->cur ^ 1];
   d->phi = static_cast<float*>(m->phi_prev);
+  d->ncde_variant = p.ncde_variant;
+  for (int a = 0; a < 3; ++a) {
+    d->kfac[a] = p.kfac[a];
+    d->cde_coef[a] = p.cde_coef[a];
+    d->gscale[a] = p.gscale[a];
+  }
+  d->nonlin_rate = p.nonlin_rate;
+  d->a1 = p.a1;
+  d->half0 = p.half0;
+  d->grad_on = p.grad_on;
+  if (m->eq == LBM_NSE && m->m2g_aniso) {
+    // the density history ping-pongs with the populations: parity k reads hist[k], writes hist[k ^ 1]
+    d->grad_in[0] = static_cast<const float*>(m->rho_hist[m->hist_cur]);
+    d->grad_in[1] = static_cast<const float*>(m->rho_hist[m->hist_cur ^ 1]);
+    d->rho_out[0] = static_cast<float*>(m->rho_hist[m->hist_cur ^ 1]);
+    d->rho_out[1] = static_cast<float*>(m->rho_hist[m->hist_cur]);
+  } else if (p.grad_on) {
+    d->grad_in[0] = d->grad_in[1] = p.grad_in;   // the cross-diffusion field psi
+  }
 }
 
 lbm_status launch_group(const GroupHost& gh, int parity, cudaStream_t stream) {
@@ -290,12 +309,6 @@ lbm_status lbm_batch_add(lbm_batch* b, lbm_model* m) {
   if (m->batch) return set_error(LBM_ERR_ARG, "model is already in a batch");
   if (m->device != b->device) return set_error(LBM_ERR_ARG, "model and batch are on different devices");
   if (m->store == LBM_F64) return set_error(LBM_ERR_NOT_IMPLEMENTED, "batched execution supports F32 and 16-bit storage");
-  if (m->eq == LBM_NCDE && m->ncde_variant != LBM_NCDE_MOMENT)
-    return set_error(LBM_ERR_NOT_IMPLEMENTED, "the rate and CDE variants are not available inside a batch");
-  if (m->m2g_aniso)
-    return set_error(LBM_ERR_NOT_IMPLEMENTED, "the density-gradient term of M2G is not available inside a batch");
-  if (m->a2 != 0.0)
-    return set_error(LBM_ERR_NOT_IMPLEMENTED, "the cross-diffusion term is not available inside a batch");
   for (int k = 4; k <= kMaxOrder; ++k)
     if (m->s_order[k] > 0.0)
       return set_error(LBM_ERR_NOT_IMPLEMENTED, "distinct higher-order rates are not available inside a batch");
@@ -363,8 +376,14 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     // every model's current buffer flipped: swap the descriptors' buffers (the graph reads them)
     for (auto& gh : b->groups) {
       for (size_t j = 0; j < gh.members.size(); ++j) {
-        gh.members[j]->cur ^= 1;
+        lbm_model* m = gh.members[j];
+        m->cur ^= 1;
         std::swap(gh.desc[j].f[0], gh.desc[j].f[1]);
+        if (m->eq == LBM_NSE && m->m2g_aniso) {
+          m->hist_cur ^= 1;
+          std::swap(gh.desc[j].grad_in[0], gh.desc[j].grad_in[1]);
+          std::swap(gh.desc[j].rho_out[0], gh.desc[j].rho_out[1]);
+        }
       }
       lbm_status st = upload_desc(b, gh);
       if (st != LBM_OK) return st;

@@ -615,8 +615,6 @@ lbm_status lbm_model_set_ncde_variant(lbm_model* m, lbm_ncde_variant variant, do
   if (!std::isfinite(a1)) return set_error(LBM_ERR_ARG, "a1 must be finite");
   if (variant == LBM_NCDE_CDE && a1 != 0.0) return set_error(LBM_ERR_ARG, "the CDE variant has no mixed-derivative term");
   if (variant == LBM_NCDE_CDE && m->a2 != 0.0) return set_error(LBM_ERR_ARG, "the CDE variant has no cross-diffusion term");
-  if (m->batch && variant != LBM_NCDE_MOMENT)
-    return set_error(LBM_ERR_NOT_IMPLEMENTED, "the rate and CDE variants are not available inside a batch");
   m->ncde_variant = variant;
   m->a1 = a1;
   batch_mark_dirty(m->batch);
@@ -629,11 +627,11 @@ lbm_status lbm_model_set_ncde_cross_diffusion(lbm_model* m, double a2, const dou
   if (!std::isfinite(a2)) return set_error(LBM_ERR_ARG, "a2 must be finite");
   if (a2 == 0.0) {
     m->a2 = 0.0;
+    batch_mark_dirty(m->batch);
     return LBM_OK;
   }
   if (!psi) return set_error(LBM_ERR_ARG, "psi is NULL");
   if (m->ncde_variant == LBM_NCDE_CDE) return set_error(LBM_ERR_ARG, "the CDE variant has no cross-diffusion term");
-  if (m->batch) return set_error(LBM_ERR_NOT_IMPLEMENTED, "the cross-diffusion term is not available inside a batch");
   DeviceGuard guard(m->device);
   const size_t bytes = size_t(m->ncells) * sizeof(double);
   lbm_status st = with_staging(m, bytes, !on_device, [&](void* tmp) -> lbm_status {
@@ -651,6 +649,7 @@ lbm_status lbm_model_set_ncde_cross_diffusion(lbm_model* m, double a2, const dou
     if (err != cudaSuccess) return cuda_error(err, "psi upload");
   }
   m->a2 = a2;
+  batch_mark_dirty(m->batch);
   return LBM_OK;
 }
 
@@ -659,8 +658,6 @@ lbm_status lbm_model_set_m2g_anisotropy(lbm_model* m, int enable) {
   if (m->eq != LBM_NSE || !lattice_single(m->lat->kind))
     return set_error(LBM_ERR_ARG, "the delta4 term of M2G applies to the NSE on rD2Q9 / rD3Q27");
   if (enable != 0 && enable != 1) return set_error(LBM_ERR_ARG, "enable must be 0 or 1");
-  if (m->batch && enable)
-    return set_error(LBM_ERR_NOT_IMPLEMENTED, "the density-gradient term of M2G is not available inside a batch");
   DeviceGuard guard(m->device);
   if (enable && !m->m2g_aniso) {
     // the previous-step density starts as the density of the current state
@@ -668,6 +665,7 @@ lbm_status lbm_model_set_m2g_anisotropy(lbm_model* m, int enable) {
     if (st != LBM_OK) return st;
   }
   m->m2g_aniso = enable != 0;
+  batch_mark_dirty(m->batch);
   return LBM_OK;
 }
 

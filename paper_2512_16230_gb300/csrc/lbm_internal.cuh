@@ -270,6 +270,18 @@ struct __align__(16) SolveDesc {
   const CT* force_tab;
   void* f[2];
   CT* phi;
+  // NCDE variants (as in StepParams)
+  int ncde_variant;
+  CT kfac[3];
+  CT nonlin_rate, a1;
+  CT cde_coef[3];
+  CT half0;
+  // gradient terms (as in StepParams): a step launched with parity k reads grad_in[k] and, for the
+  // delta4 term of M2G, writes its density to rho_out[k]
+  int grad_on;
+  CT gscale[3];
+  const CT* grad_in[2];
+  CT* rho_out[2];
 };
 
 struct Tile {

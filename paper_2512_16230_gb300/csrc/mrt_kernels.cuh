@@ -631,9 +631,8 @@ template <class L, int EQ>
 struct GradTerm {
   static constexpr bool kOn = (L::SINGLE && EQ == LBM_NSE) || EQ == LBM_NCDE;
 };
-template <class L, class CT>
-__device__ __forceinline__ void cell_field_gradient(const StepParams<CT>& p, int cell, int x, int y, int z,
-                                                    CT (&gr)[3]) {
+template <class L, class CT, class P>
+__device__ __forceinline__ void cell_field_gradient(const P& p, int cell, int x, int y, int z, CT (&gr)[3]) {
   gr[0] = gr[1] = gr[2] = CT(0);
   if (!p.grad_on) return;
   const int nx = p.n[0], ny = p.n[1];
@@ -770,11 +769,23 @@ struct BatchView {
   const CT (&halfn)[3][3];
   const CT (&u_const)[3];
   CT s_high, one_minus_sh, sh_rho_ref, cs2_eq, nonlin_third;
-  static constexpr bool kNcdeVariants = false;  // batched NCDE solves use the moment variant
-  __device__ __forceinline__ BatchView(const BatchTables<CT>& t, const SolveDesc<CT>& d)
+  int ncde_variant;
+  const CT (&kfac)[3];
+  CT nonlin_rate, a1;
+  const CT (&cde_coef)[3];
+  CT half0;
+  const int (&n)[3];
+  int grad_on;
+  const CT (&gscale)[3];
+  const CT* grad_in;
+  CT* rho_out;
+  static constexpr bool kNcdeVariants = true;
+  __device__ __forceinline__ BatchView(const BatchTables<CT>& t, const SolveDesc<CT>& d, int parity)
       : T(t.T), D(t.D), invN(t.invN), w(t.w), wref(t.wref), wmom_ref(t.wmom_ref), sd(d.sd), half(d.half),
         sdn(d.sdn), halfn(d.halfn), u_const(d.u_const), s_high(d.s_high), one_minus_sh(d.one_minus_sh), sh_rho_ref(d.sh_rho_ref),
-        cs2_eq(d.cs2_eq), nonlin_third(d.nonlin_third) {}
+        cs2_eq(d.cs2_eq), nonlin_third(d.nonlin_third), ncde_variant(d.ncde_variant), kfac(d.kfac),
+        nonlin_rate(d.nonlin_rate), a1(d.a1), cde_coef(d.cde_coef), half0(d.half0), n(d.n), grad_on(d.grad_on),
+        gscale(d.gscale), grad_in(d.grad_in[parity]), rho_out(d.rho_out[parity]) {}
 };
 
 // K6: persistent batched collide-stream. The grid is the resident capacity of the GPU; each
@@ -810,7 +821,7 @@ __global__ void __launch_bounds__(BLOCK, batch_min_blocks<BLOCK>())
     const size_t N = size_t(sd.ncells);
     const ST* __restrict__ fin = static_cast<const ST*>(sd.f[parity]);
     ST* __restrict__ fout = static_cast<ST*>(sd.f[parity ^ 1]);
-    const BatchView<CT> p(t, sd);
+    const BatchView<CT> p(t, sd, parity);
     constexpr bool DEV = is_deviation_storage<ST>();
     CT f[L::Q];
     static_for<L::Q>([&](auto i) {
@@ -822,8 +833,14 @@ __global__ void __launch_bounds__(BLOCK, batch_min_blocks<BLOCK>())
     body_force(sd.force_a, sd.force_b, sd.force_tab, nb.x, nb.y, nb.z, F);
     CT phi_prev = CT(0), phi_now = CT(0);
     if constexpr (EQ == LBM_NCDE) phi_prev = sd.phi[cell];
-    collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now);
+    constexpr bool AG = GradTerm<L, EQ>::kOn;
+    CT gr[3];
+    if constexpr (AG) cell_field_gradient<L>(p, cell, nb.x, nb.y, nb.z, gr);
+    collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, static_cast<NoHigh*>(nullptr), AG ? gr : nullptr);
     if constexpr (EQ == LBM_NCDE) sd.phi[cell] = phi_now;
+    if constexpr (AG && EQ == LBM_NSE) {
+      if (p.grad_on) p.rho_out[cell] = phi_now;
+    }
     static_for<L::Q>([&](auto i) {
       constexpr int I = decltype(i)::value;
       if constexpr (DEV) k1_store(fout + size_t(I) * N + cell, RawCodec<ST>::enc(f[I]));

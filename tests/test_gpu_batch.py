@@ -154,3 +154,76 @@ def test_serving_results_same_alone_and_in_the_mix():
         assert rel_l2(b[0], a[0]) <= tol, req
         if a[1] is not None:
             assert rel_l2(b[1], a[1]) <= tol, req
+
+
+# (lattice, eq, grid, store, settings): the model settings beyond the base scheme inside a batch
+VARIANTS = [
+    ("rD2Q13", "ncde", (33, 27), "f32", dict(ncde_mode="rate", a1=-0.3)),
+    ("rD2Q25", "ncde", (29, 31), "f32", dict(ncde_mode="cde")),
+    ("rD2Q17", "ncde", (30, 26), "f16_dev", dict(ncde_mode="moment", a1=0.4, a2=0.05)),
+    ("rD2Q13", "ncde", (25, 24), "f32", dict(ncde_mode="rate", a2=-0.04)),
+    ("rD2Q9", "nse", (37, 29), "f32", dict(m2g_aniso=True)),
+    ("rD3Q27", "nse", (13, 11, 9), "f16_dev", dict(m2g_aniso=True)),
+    ("rD3Q27", "nse", (9, 12, 10), "f32", dict(m2g_aniso=True, s_bulk=0.9)),
+]
+
+
+def _make_variant(lat_cache, name, eq, n, store, settings, seed):
+    from paper_2512_16230_gb300 import lbm
+    spec = W.LATTICES[name]
+    if name not in lat_cache:
+        lat_cache[name] = lbm.Lattice(spec.kind, spec.c, spec.cs2, spec.free_w)
+    s = np.random.default_rng(seed).uniform(0.8, 1.8, spec.R)
+    d = spec.d
+    kw = dict(settings)
+    if "a2" in kw:
+        kw["psi"] = I.random_scalar(n, seed=seed + 50)
+    if eq == "nse":
+        kw["force"] = (0, d - 1, 2e-4, 1, 0.3)
+    else:
+        kw["u_const"] = tuple([0.03, 0.02, 0.01][:d])
+        kw["nonlin"] = 0.0 if kw.get("ncde_mode") == "cde" else 1.0
+    m = gpu_model(spec, eq, n, s, 1.1, store=store, lat=lat_cache[name], **kw)
+    if eq == "nse":
+        rho, u = I.random_fields(n, d, seed=seed, rho_amp=0.01, u_amp=0.03)
+        m.init_fields(rho, u)
+    else:
+        m.init_fields(I.gaussian_hill(n, spec.c, max(2.0, n[0] / 6), 1.0, noise=1e-3, seed=seed))
+    return m
+
+
+def test_batch_carries_model_variants():
+    """The NCDE variants (per-cell rates, CDE, mixed derivative), the cross-diffusion term and the
+    delta4 term of M2G with its density history, in one batch with mixed groups: after 13 steps
+    (one graph replay and an odd remainder, so the populations and the density history swap) and
+    9 more, every member equals the same model stepped alone."""
+    from paper_2512_16230_gb300 import lbm
+    cache = {}
+    alone = [_make_variant(cache, *v, seed=10 + i) for i, v in enumerate(VARIANTS)]
+    batched = [_make_variant(cache, *v, seed=10 + i) for i, v in enumerate(VARIANTS)]
+    b = lbm.Batch(16)
+    for m in batched:
+        b.add(m)
+    b.step(13)
+    b.synchronize()
+    for m in alone:
+        m.step(13)
+    for x, y, v in zip(alone, batched, VARIANTS):
+        _compare(x, y, v[3])
+    b.step(9)
+    b.synchronize()
+    for m in alone:
+        m.step(9)
+    for x, y, v in zip(alone, batched, VARIANTS):
+        _compare(x, y, v[3])
+    b.close()
+
+
+def test_batch_rejects_per_order_rates():
+    from paper_2512_16230_gb300 import lbm
+    spec = W.LATTICES["rD2Q25"]
+    m = gpu_model(spec, "nse", (16, 12), np.ones(spec.R), s_orders={4: 0.9, 5: 1.2})
+    b = lbm.Batch(2)
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_NOT_IMPLEMENTED"):
+        b.add(m)
+    b.close()
