@@ -203,6 +203,49 @@ def cpu_baseline_worker(nx, ny, nz, steps):
     print(json.dumps({"mlups": nx * ny * nz * steps / dt / 1e6, "seconds": dt}))
 
 
+ORACLE_CONFIG_STEPS = {"taylor_green_rD2Q25_64x48_f64": 200, "ncde_hill_rD2Q13_1024x768": 10}
+
+
+def oracle_config_worker(name, steps):
+    """Time the FP64 oracle, as it stands, on one of the smaller configurations at full size (run in
+    a fresh process; prints one JSON object)."""
+    from oracle import lattice as OL
+    from oracle import mrt as OM
+    from paper_2512_16230_gb300 import workloads as W
+    wl = W.taylor_green_2d() if name.startswith("taylor_green") else W.ncde_hill(store="f64")
+    spec = wl.lattice
+    lat = OL.build(spec.kind, spec.c, spec.cs2, spec.free_w)
+    m = OM.Model(lat, wl.eq, wl.n, wl.s, wl.s_high, force=wl.force, u_const=wl.u_const, nonlin=wl.nonlin)
+    rho, u = wl.fields()
+    m.init_fields(rho, u)
+    t0 = time.perf_counter()
+    m.step(steps)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"mlups": wl.ncells * steps / dt / 1e6, "seconds": dt}))
+
+
+def run_oracle_configs(threads=None):
+    """The oracle on the smaller configurations at full size: config 1 for all its 200 steps,
+    config 2 (FP64) for a 10-step sample of its 5000."""
+    threads = threads or os.cpu_count() or 1
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = str(threads)
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    out = {}
+    for name, steps in ORACLE_CONFIG_STEPS.items():
+        code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
+                f"bench.oracle_config_worker({name!r}, {steps})")
+        res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+        if res.returncode != 0:
+            out[name] = {"error": res.stderr[-300:]}
+            continue
+        r = json.loads(res.stdout.strip().splitlines()[-1])
+        out[name] = {"kind": "oracle", "mlups": r["mlups"], "steps": steps, "seconds": r["seconds"],
+                     "cores": threads}
+    return out
+
+
 def _oracle_timing(threads, grid, steps):
     env = dict(os.environ)
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -465,6 +508,10 @@ def bench_ours(args):
     if not args.no_other_configs:
         other = run_other_configs(lbm, W_stream=stream, barrier=barrier)
         if rank == 0:
+            if ws == 1 and not args.no_cpu_baseline:
+                oc = run_oracle_configs()
+                other["taylor_green_rD2Q25_64x48_f64"]["oracle"] = oc["taylor_green_rD2Q25_64x48_f64"]
+                other["ncde_hill_rD2Q13_1024x768_f64"]["oracle"] = oc["ncde_hill_rD2Q13_1024x768"]
             line["other_configs"] = other
     if args.serving_requests > 0:
         serving = run_serving(args.serving_requests)
