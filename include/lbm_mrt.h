@@ -192,8 +192,8 @@ lbm_status lbm_model_set_bulk(lbm_model* m, double s_bulk);
  * equilibrium and the sources have no moments of order >= 4, the update adds
  * -w_i sum_r (s_r - s_high) H_r(c_i) (sum_j H_r(c_j) f_j) / N_r over those rows, which costs the
  * step two more contractions with them. n_orders = 0 restores the shared rate.
- * Errors: LBM_ERR_ARG, LBM_ERR_LATTICE_INFEASIBLE (lattice without complete higher rows),
- *         LBM_ERR_NOT_IMPLEMENTED (the model is in a batch). */
+ * Inside a batch the solve joins a group of solves with per-order rates (CUDA cores).
+ * Errors: LBM_ERR_ARG, LBM_ERR_LATTICE_INFEASIBLE (lattice without complete higher rows). */
 lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_orders);
 
 /* Tensor-core (tcgen05) collision. For 16-bit deviation storage (BF16_DEV / F16_DEV) the two contractions
@@ -342,8 +342,9 @@ lbm_status lbm_batch_create(void* stream, int max_solves, lbm_batch** out);
  * lbm_batch_step (lbm_model_step returns LBM_ERR_ARG) but every other model call works (on the
  * batch's stream). Members are grouped by (lattice handle, storage dtype, equation); share one
  * lattice handle between solves of the same lattice setting so that they form one group. Every
- * model setting carries over (NCDE variants, the cross-diffusion and M2G gradient terms) except
- * distinct rates for the orders >= 4 (LBM_ERR_NOT_IMPLEMENTED), and FP64 storage. */
+ * model setting carries over: the NCDE variants, the cross-diffusion and M2G gradient terms, and
+ * distinct rates for the orders >= 4 (such solves form their own groups, with tiles of 128
+ * cells, on the CUDA cores). FP64 storage is not batched (LBM_ERR_NOT_IMPLEMENTED). */
 lbm_status lbm_batch_add(lbm_batch* b, lbm_model* m);
 
 /* Remove a model (synchronizes the batch's stream; the model returns to its own stream). */

@@ -1,6 +1,7 @@
 // Batched execution of many solves: the runtime behind lbm_batch_* (include/lbm_mrt.h).
 //
-// Members are grouped by (lattice object, storage dtype, equation). Each group gets its lattice
+// Members are grouped by (lattice object, storage dtype, equation, per-order rates or not). Each
+// group gets its lattice
 // tables (kernel parameter), one descriptor per solve and a tile work-list covering every cell of
 // every solve; one persistent launch per group advances all its solves by one time step. The
 // launches of CHUNK consecutive steps are captured once in a CUDA graph and replayed; membership or
@@ -22,6 +23,7 @@ struct GroupHost {
   lbm::BatchGroup g;
   lbm::BatchTables<float> tables;
   std::vector<lbm::SolveDesc<float>> desc;
+  std::vector<lbm::HighParams<float>> high;  // per solve, for a group with per-order rates
   std::vector<lbm_model*> members;
 };
 
@@ -32,6 +34,8 @@ struct DeviceBuffers {
   size_t desc_cap = 0;
   void* tiles = nullptr;
   size_t tiles_cap = 0;
+  void* high = nullptr;
+  size_t high_cap = 0;
 };
 
 struct lbm_batch {
@@ -47,7 +51,7 @@ struct lbm_batch {
   bool stable = false;  // no change since the last step call: capture a graph
   cudaGraphExec_t graph = nullptr;
   // work-list buffers by group key, kept across rebuilds and grown geometrically
-  std::map<std::tuple<const lbm_lattice*, int, int>, DeviceBuffers> buffers;
+  std::map<std::tuple<const lbm_lattice*, int, int, int>, DeviceBuffers> buffers;
   int64_t steps = 0, launches = 0, rebuilds = 0, captures = 0;
 };
 
@@ -91,6 +95,7 @@ void free_buffers(lbm_batch* b) {
   for (auto& kv : b->buffers) {
     if (kv.second.desc) cudaFree(kv.second.desc);
     if (kv.second.tiles) cudaFree(kv.second.tiles);
+    if (kv.second.high) cudaFree(kv.second.high);
   }
   b->buffers.clear();
 }
@@ -173,9 +178,10 @@ lbm_status upload_desc(lbm_batch* b, GroupHost& gh) {
 
 lbm_status rebuild(lbm_batch* b) {
   free_groups(b);
-  std::map<std::tuple<const lbm_lattice*, int, int>, size_t> index;
+  std::map<std::tuple<const lbm_lattice*, int, int, int>, size_t> index;
   for (lbm_model* m : b->members) {
-    auto key = std::make_tuple(m->lat, m->store, m->eq);
+    const int high = has_high_rates(m) ? 1 : 0;
+    auto key = std::make_tuple(m->lat, m->store, m->eq, high);
     auto it = index.find(key);
     if (it == index.end()) {
       index[key] = b->groups.size();
@@ -186,8 +192,9 @@ lbm_status rebuild(lbm_batch* b) {
       gh.g.store = m->store;
       gh.g.eq = m->eq;
       gh.g.lat = m->lat;
+      gh.g.high = high;
       auto t = b->tile.find(std::make_tuple(m->lat->kind, m->store, m->eq));
-      gh.g.block = t == b->tile.end() ? kBlock : t->second;
+      gh.g.block = high || t == b->tile.end() ? kBlock : t->second;
       StepParams<float> p;
       make_step_params<float>(m, &p);
       std::memcpy(gh.tables.T, p.T, sizeof(p.T));
@@ -204,29 +211,37 @@ lbm_status rebuild(lbm_batch* b) {
   for (auto& gh : b->groups) {
     gh.g.tables = &gh.tables;
     gh.desc.resize(gh.members.size());
+    gh.high.resize(gh.g.high ? gh.members.size() : 0);
     std::vector<Tile> tiles;
     for (size_t j = 0; j < gh.members.size(); ++j) {
       fill_desc(gh.members[j], &gh.desc[j]);
+      if (gh.g.high) make_high_params<float>(gh.members[j], &gh.high[j]);
       for (int c0 = 0; c0 < gh.members[j]->ncells; c0 += gh.g.block) tiles.push_back(Tile{int(j), c0});
     }
     gh.g.nsolves = int(gh.members.size());
     gh.g.ntiles = int(tiles.size());
-    DeviceBuffers& buf = b->buffers[std::make_tuple(gh.g.lat, gh.g.store, gh.g.eq)];
+    DeviceBuffers& buf = b->buffers[std::make_tuple(gh.g.lat, gh.g.store, gh.g.eq, gh.g.high)];
     cudaError_t err = cudaStreamSynchronize(b->stream);   // the previous work-list may still be read
     if (err == cudaSuccess) err = ensure(&buf.desc, &buf.desc_cap, gh.desc.size() * sizeof(SolveDesc<float>));
     if (err == cudaSuccess) err = ensure(&buf.tiles, &buf.tiles_cap, tiles.size() * sizeof(Tile));
+    if (err == cudaSuccess && gh.g.high)
+      err = ensure(&buf.high, &buf.high_cap, gh.high.size() * sizeof(HighParams<float>));
     gh.g.d_desc = buf.desc;
     gh.g.d_tiles = static_cast<Tile*>(buf.tiles);
+    gh.g.d_high = gh.g.high ? buf.high : nullptr;
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(gh.g.d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
                             b->stream);
+    if (err == cudaSuccess && gh.g.high)
+      err = cudaMemcpyAsync(gh.g.d_high, gh.high.data(), gh.high.size() * sizeof(HighParams<float>),
+                            cudaMemcpyHostToDevice, b->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(b->stream);
     if (err != cudaSuccess) return cuda_error(err, "batch work-list allocation");
     lbm_status st = upload_desc(b, gh);
     if (st != LBM_OK) return st;
     int per_sm = 0;
     st = dispatch_batch_kind(gh.g.kind, [&](auto kc) {
-      return BatchLaunch<decltype(kc)::value>::occupancy(gh.g.store, gh.g.eq, gh.g.block, &per_sm);
+      return BatchLaunch<decltype(kc)::value>::occupancy(gh.g.store, gh.g.eq, gh.g.block, gh.g.high, &per_sm);
     });
     if (st != LBM_OK) return st;
     gh.g.grid = std::max(1, std::min(gh.g.ntiles, std::max(1, per_sm) * b->num_sms));
@@ -309,9 +324,6 @@ lbm_status lbm_batch_add(lbm_batch* b, lbm_model* m) {
   if (m->batch) return set_error(LBM_ERR_ARG, "model is already in a batch");
   if (m->device != b->device) return set_error(LBM_ERR_ARG, "model and batch are on different devices");
   if (m->store == LBM_F64) return set_error(LBM_ERR_NOT_IMPLEMENTED, "batched execution supports F32 and 16-bit storage");
-  for (int k = 4; k <= kMaxOrder; ++k)
-    if (m->s_order[k] > 0.0)
-      return set_error(LBM_ERR_NOT_IMPLEMENTED, "distinct higher-order rates are not available inside a batch");
   if (int(b->members.size()) >= b->max_solves) return set_error(LBM_ERR_ARG, "batch is full");
   DeviceScope scope(b->device);
   cudaError_t err = cudaStreamSynchronize(m->stream);

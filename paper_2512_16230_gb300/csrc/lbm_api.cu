@@ -547,8 +547,6 @@ lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_o
     return set_error(LBM_ERR_ARG, "n_orders must lie in [0, " + std::to_string(kMaxOrder - 3) + "]");
   for (int k = 0; k < n_orders; ++k)
     if (!(s_order[k] > 0.0 && s_order[k] <= 2.0)) return set_error(LBM_ERR_ARG, "rates must lie in (0, 2]");
-  if (m->batch && n_orders > 0)
-    return set_error(LBM_ERR_NOT_IMPLEMENTED, "distinct higher-order rates are not available inside a batch");
   double next[kMaxOrder + 1] = {};
   for (int k = 0; k < n_orders; ++k) next[4 + k] = s_order[k];
   bool differ = false;
@@ -561,6 +559,7 @@ lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_o
                                                      ? "the graded monomials do not complete the Hermite matrix"
                                                      : "a higher-order row has zero W-norm (zero weights)");
   for (int k = 0; k <= kMaxOrder; ++k) m->s_order[k] = next[k];
+  batch_mark_dirty(m->batch);
   return LBM_OK;
 }
 

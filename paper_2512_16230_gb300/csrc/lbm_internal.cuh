@@ -292,9 +292,11 @@ struct Tile {
 // A group of solves advanced by one batched launch per step.
 struct BatchGroup {
   int kind, store, eq, block;
+  int high;         // the solves have one rate per order >= 4 (k_step_batch_high, tiles of kBlock cells)
   const lbm_lattice* lat;
   void* tables;     // host copy of BatchTables<CT>
   void* d_desc;     // device SolveDesc<CT>[nsolves]
+  void* d_high;     // device HighParams<CT>[nsolves] (high groups)
   Tile* d_tiles;    // device work-list
   int nsolves, ntiles, grid;
 };
@@ -302,7 +304,7 @@ struct BatchGroup {
 template <int KIND>
 struct BatchLaunch {
   static lbm_status launch(const BatchGroup& g, int parity, cudaStream_t stream);
-  static lbm_status occupancy(int store, int eq, int block, int* blocks_per_sm);
+  static lbm_status occupancy(int store, int eq, int block, int high, int* blocks_per_sm);
 };
 
 // Per-lattice launchers, defined in the k_<lattice>.cu translation units.

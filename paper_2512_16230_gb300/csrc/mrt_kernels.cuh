@@ -797,55 +797,95 @@ constexpr int batch_min_blocks() {
   return BLOCK >= 256 ? 2 : (BLOCK >= 128 ? LBM_K1_MIN_BLOCKS : 10);
 }
 
+// One cell of a batched step: the same gather / collide / store as k_step, with the solve's
+// parameters from its staged descriptor (HP: the higher-row table of a per-order-rate group).
+template <class L, class CT, class ST, int EQ, class HP>
+__device__ __forceinline__ void batch_cell(const BatchTables<CT>& t, const SolveDesc<CT>& sd, int cell, int parity,
+                                           HP* hp) {
+  const Neigh<L> nb(cell, sd.n, sd.div_m, sd.div_s);
+  const size_t N = size_t(sd.ncells);
+  const ST* __restrict__ fin = static_cast<const ST*>(sd.f[parity]);
+  ST* __restrict__ fout = static_cast<ST*>(sd.f[parity ^ 1]);
+  const BatchView<CT> p(t, sd, parity);
+  constexpr bool DEV = is_deviation_storage<ST>();
+  CT f[L::Q];
+  static_for<L::Q>([&](auto i) {
+    constexpr int I = decltype(i)::value;
+    if constexpr (DEV) f[I] = RawCodec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()));
+    else f[I] = Codec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()), p.wref[I]);
+  });
+  CT F[3];
+  body_force(sd.force_a, sd.force_b, sd.force_tab, nb.x, nb.y, nb.z, F);
+  CT phi_prev = CT(0), phi_now = CT(0);
+  if constexpr (EQ == LBM_NCDE) phi_prev = sd.phi[cell];
+  constexpr bool AG = GradTerm<L, EQ>::kOn;
+  CT gr[3];
+  if constexpr (AG) cell_field_gradient<L>(p, cell, nb.x, nb.y, nb.z, gr);
+  collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, hp, AG ? gr : nullptr);
+  if constexpr (EQ == LBM_NCDE) sd.phi[cell] = phi_now;
+  if constexpr (AG && EQ == LBM_NSE) {
+    if (p.grad_on) p.rho_out[cell] = phi_now;
+  }
+  static_for<L::Q>([&](auto i) {
+    constexpr int I = decltype(i)::value;
+    if constexpr (DEV) k1_store(fout + size_t(I) * N + cell, RawCodec<ST>::enc(f[I]));
+    else k1_store(fout + size_t(I) * N + cell, Codec<ST>::enc(f[I], p.wref[I]));
+  });
+}
+
+// Stage the descriptor of solve `solve` in shared memory (block-wide; call with the whole block).
+template <class CT, int BLOCK>
+__device__ __forceinline__ void stage_desc(SolveDesc<CT>& sd, const SolveDesc<CT>* __restrict__ descs, int solve) {
+  constexpr int kWords = int(sizeof(SolveDesc<CT>) / sizeof(int4));
+  static_assert(sizeof(SolveDesc<CT>) % sizeof(int4) == 0, "descriptor must be a whole number of int4");
+  const int4* src = reinterpret_cast<const int4*>(descs + solve);
+  int4* dst = reinterpret_cast<int4*>(&sd);
+  for (int w = threadIdx.x; w < kWords; w += BLOCK) dst[w] = src[w];
+}
+
 template <class L, class CT, class ST, int EQ, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, batch_min_blocks<BLOCK>())
     k_step_batch(const BatchTables<CT> t, const SolveDesc<CT>* __restrict__ descs,
                  const Tile* __restrict__ tiles, int ntiles, int parity) {
   __shared__ SolveDesc<CT> sd;
-  constexpr int kWords = int(sizeof(SolveDesc<CT>) / sizeof(int4));
-  static_assert(sizeof(SolveDesc<CT>) % sizeof(int4) == 0, "descriptor must be a whole number of int4");
   int staged = -1;
   for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
     const Tile tile = tiles[ti];
     if (tile.solve != staged) {
       __syncthreads();
-      const int4* src = reinterpret_cast<const int4*>(descs + tile.solve);
-      int4* dst = reinterpret_cast<int4*>(&sd);
-      for (int w = threadIdx.x; w < kWords; w += BLOCK) dst[w] = src[w];
+      stage_desc<CT, BLOCK>(sd, descs, tile.solve);
       __syncthreads();
       staged = tile.solve;
     }
     const int cell = tile.cell0 + int(threadIdx.x);
     if (cell >= sd.ncells) continue;
-    const Neigh<L> nb(cell, sd.n, sd.div_m, sd.div_s);
-    const size_t N = size_t(sd.ncells);
-    const ST* __restrict__ fin = static_cast<const ST*>(sd.f[parity]);
-    ST* __restrict__ fout = static_cast<ST*>(sd.f[parity ^ 1]);
-    const BatchView<CT> p(t, sd, parity);
-    constexpr bool DEV = is_deviation_storage<ST>();
-    CT f[L::Q];
-    static_for<L::Q>([&](auto i) {
-      constexpr int I = decltype(i)::value;
-      if constexpr (DEV) f[I] = RawCodec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()));
-      else f[I] = Codec<ST>::dec(k1_load(fin + size_t(I) * N + nb.template src<I>()), p.wref[I]);
-    });
-    CT F[3];
-    body_force(sd.force_a, sd.force_b, sd.force_tab, nb.x, nb.y, nb.z, F);
-    CT phi_prev = CT(0), phi_now = CT(0);
-    if constexpr (EQ == LBM_NCDE) phi_prev = sd.phi[cell];
-    constexpr bool AG = GradTerm<L, EQ>::kOn;
-    CT gr[3];
-    if constexpr (AG) cell_field_gradient<L>(p, cell, nb.x, nb.y, nb.z, gr);
-    collide<L, CT, EQ, DEV>(f, p, F, phi_prev, phi_now, static_cast<NoHigh*>(nullptr), AG ? gr : nullptr);
-    if constexpr (EQ == LBM_NCDE) sd.phi[cell] = phi_now;
-    if constexpr (AG && EQ == LBM_NSE) {
-      if (p.grad_on) p.rho_out[cell] = phi_now;
+    batch_cell<L, CT, ST, EQ>(t, sd, cell, parity, static_cast<NoHigh*>(nullptr));
+  }
+}
+
+// The batched step of a group whose solves have one rate per order >= 4: tiles of kBlock cells,
+// and the solve's higher-row table (rows of the lattice, rates of the solve) staged in shared
+// memory with its descriptor, as k_step_high does for one solve.
+template <class L, class CT, class ST, int EQ>
+__global__ void __launch_bounds__(kBlock, 3)
+    k_step_batch_high(const BatchTables<CT> t, const SolveDesc<CT>* __restrict__ descs,
+                      const HighParams<CT>* __restrict__ highs, const Tile* __restrict__ tiles, int ntiles,
+                      int parity) {
+  __shared__ SolveDesc<CT> sd;
+  __shared__ HighTable<L, CT> tab;
+  int staged = -1;
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const Tile tile = tiles[ti];
+    if (tile.solve != staged) {
+      __syncthreads();
+      stage_desc<CT, kBlock>(sd, descs, tile.solve);
+      tab.fill(highs[tile.solve]);
+      __syncthreads();
+      staged = tile.solve;
     }
-    static_for<L::Q>([&](auto i) {
-      constexpr int I = decltype(i)::value;
-      if constexpr (DEV) k1_store(fout + size_t(I) * N + cell, RawCodec<ST>::enc(f[I]));
-      else k1_store(fout + size_t(I) * N + cell, Codec<ST>::enc(f[I], p.wref[I]));
-    });
+    const int cell = tile.cell0 + int(threadIdx.x);
+    if (cell >= sd.ncells) continue;
+    batch_cell<L, CT, ST, EQ>(t, sd, cell, parity, &tab);
   }
 }
 
@@ -863,6 +903,23 @@ lbm_status batch_by_block(int block, F&& fn) {
     case 256: return fn(k_step_batch<L, CT, ST, EQ, 256>);
   }
   return set_error(LBM_ERR_ARG, "batched tile size must be 64, 128 or 256 cells");
+}
+
+template <class L, class F>
+lbm_status batch_kernel_high(int store, int eq, F&& fn) {
+  if (store == LBM_F32) {
+    if (eq == LBM_NSE) return fn(k_step_batch_high<L, float, float, LBM_NSE>);
+    return fn(k_step_batch_high<L, float, float, LBM_NCDE>);
+  }
+  if (store == LBM_F16_DEV) {
+    if (eq == LBM_NSE) return fn(k_step_batch_high<L, float, __half, LBM_NSE>);
+    return fn(k_step_batch_high<L, float, __half, LBM_NCDE>);
+  }
+  if (store == LBM_BF16_DEV) {
+    if (eq == LBM_NSE) return fn(k_step_batch_high<L, float, __nv_bfloat16, LBM_NSE>);
+    return fn(k_step_batch_high<L, float, __nv_bfloat16, LBM_NCDE>);
+  }
+  return set_error(LBM_ERR_NOT_IMPLEMENTED, "batched execution supports F32, F16_DEV and BF16_DEV storage");
 }
 
 template <class L, class F>
@@ -885,6 +942,16 @@ lbm_status batch_kernel(int store, int eq, int block, F&& fn) {
 template <int KIND>
 lbm_status BatchLaunch<KIND>::launch(const BatchGroup& g, int parity, cudaStream_t stream) {
   using L = Lat<KIND>;
+  if (g.high) {
+    return batch_kernel_high<L>(g.store, g.eq, [&](auto kernel) -> lbm_status {
+      const BatchTables<float>& t = *static_cast<const BatchTables<float>*>(g.tables);
+      kernel<<<g.grid, kBlock, 0, stream>>>(t, static_cast<const SolveDesc<float>*>(g.d_desc),
+                                            static_cast<const HighParams<float>*>(g.d_high), g.d_tiles, g.ntiles,
+                                            parity);
+      cudaError_t err = cudaGetLastError();
+      return err == cudaSuccess ? LBM_OK : cuda_error(err, "batched step launch");
+    });
+  }
   return batch_kernel<L>(g.store, g.eq, g.block, [&](auto kernel) -> lbm_status {
     using Kern = decltype(kernel);
     (void)sizeof(Kern);
@@ -897,8 +964,14 @@ lbm_status BatchLaunch<KIND>::launch(const BatchGroup& g, int parity, cudaStream
 }
 
 template <int KIND>
-lbm_status BatchLaunch<KIND>::occupancy(int store, int eq, int block, int* blocks_per_sm) {
+lbm_status BatchLaunch<KIND>::occupancy(int store, int eq, int block, int high, int* blocks_per_sm) {
   using L = Lat<KIND>;
+  if (high) {
+    return batch_kernel_high<L>(store, eq, [&](auto kernel) -> lbm_status {
+      cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, kBlock, 0);
+      return err == cudaSuccess ? LBM_OK : cuda_error(err, "occupancy query");
+    });
+  }
   return batch_kernel<L>(store, eq, block, [&](auto kernel) -> lbm_status {
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, block, 0);
     return err == cudaSuccess ? LBM_OK : cuda_error(err, "occupancy query");

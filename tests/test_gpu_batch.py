@@ -165,6 +165,9 @@ VARIANTS = [
     ("rD2Q9", "nse", (37, 29), "f32", dict(m2g_aniso=True)),
     ("rD3Q27", "nse", (13, 11, 9), "f16_dev", dict(m2g_aniso=True)),
     ("rD3Q27", "nse", (9, 12, 10), "f32", dict(m2g_aniso=True, s_bulk=0.9)),
+    ("rD2Q25", "nse", (27, 22), "f32", dict(s_orders={4: 0.9, 5: 1.3, 6: 1.6})),
+    ("rD3Q53", "nse", (11, 9, 10), "f16_dev", dict(s_orders={4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25})),
+    ("rD2Q13", "ncde", (26, 21), "f32", dict(ncde_mode="rate", s_orders={4: 1.4, 5: 0.7})),
 ]
 
 
@@ -184,6 +187,8 @@ def _make_variant(lat_cache, name, eq, n, store, settings, seed):
         kw["u_const"] = tuple([0.03, 0.02, 0.01][:d])
         kw["nonlin"] = 0.0 if kw.get("ncde_mode") == "cde" else 1.0
     m = gpu_model(spec, eq, n, s, 1.1, store=store, lat=lat_cache[name], **kw)
+    if store != "f64":
+        m.set_tensor_cores(0)   # batched solves run on the CUDA cores; compare like with like
     if eq == "nse":
         rho, u = I.random_fields(n, d, seed=seed, rho_amp=0.01, u_amp=0.03)
         m.init_fields(rho, u)
@@ -193,10 +198,11 @@ def _make_variant(lat_cache, name, eq, n, store, settings, seed):
 
 
 def test_batch_carries_model_variants():
-    """The NCDE variants (per-cell rates, CDE, mixed derivative), the cross-diffusion term and the
-    delta4 term of M2G with its density history, in one batch with mixed groups: after 13 steps
-    (one graph replay and an odd remainder, so the populations and the density history swap) and
-    9 more, every member equals the same model stepped alone."""
+    """The NCDE variants (per-cell rates, CDE, mixed derivative), the cross-diffusion term, the
+    delta4 term of M2G with its density history and per-order rates (their own groups, with the
+    higher-row table staged per solve), in one batch: after 13 steps (one graph replay and an odd
+    remainder, so the populations and the density history swap) and 9 more, every member equals
+    the same model stepped alone; changing a member's per-order rates moves it between groups."""
     from paper_2512_16230_gb300 import lbm
     cache = {}
     alone = [_make_variant(cache, *v, seed=10 + i) for i, v in enumerate(VARIANTS)]
@@ -216,14 +222,12 @@ def test_batch_carries_model_variants():
         m.step(9)
     for x, y, v in zip(alone, batched, VARIANTS):
         _compare(x, y, v[3])
-    b.close()
-
-
-def test_batch_rejects_per_order_rates():
-    from paper_2512_16230_gb300 import lbm
-    spec = W.LATTICES["rD2Q25"]
-    m = gpu_model(spec, "nse", (16, 12), np.ones(spec.R), s_orders={4: 0.9, 5: 1.2})
-    b = lbm.Batch(2)
-    with pytest.raises(lbm.LBMError, match="LBM_ERR_NOT_IMPLEMENTED"):
-        b.add(m)
+    for m in (alone[0], batched[0]):
+        m.set_high_rates([1.2, 0.8])
+    b.step(5)
+    b.synchronize()
+    for m in alone:
+        m.step(5)
+    for x, y, v in zip(alone, batched, VARIANTS):
+        _compare(x, y, v[3])
     b.close()
