@@ -505,6 +505,23 @@ def bench_ours(args):
             "rates": {str(k): v for k, v in HIGH_RATES.items()}, "steps": vsteps,
             "ms_per_step": high16_ms, "mlups": cells / high16_ms / 1e3,
             "hbm_frac": 2 * Q * 2 * cells / (high16_ms / 1e3) / 1e9 / peak}
+    # the same workload with 16-bit deviation storage (the reduced-precision configuration): FP16
+    # and BF16 on the CUDA cores, FP16 with the contractions on tcgen05
+    for key, store, tc, kern in (("f16_deviations", "f16_dev", 0, "k_step<rD3Q53, f16_dev, NSE>"),
+                                 ("bf16_deviations", "bf16_dev", 0, "k_step<rD3Q53, bf16_dev, NSE>"),
+                                 ("f16_deviations_tensor_cores", "f16_dev", 1, "k_step_tc<rD3Q53, f16_dev, NSE>")):
+        mr = lbm.Model(lat, "nse", wl.n, store=store, stream=stream.cuda_stream)
+        mr.set_relaxation(wl.s, wl.s_high)
+        mr.set_tensor_cores(tc)
+        mr.init_fields(rho_d, u_d)
+        r_ms = time_steps(mr)
+        mr.close()
+        del mr
+        torch.cuda.empty_cache()
+        if rank == 0:
+            line["variants"][key] = {"kernel": kern, "steps": vsteps, "ms_per_step": r_ms,
+                                     "mlups": cells / r_ms / 1e3,
+                                     "hbm_frac": 2 * Q * 2 * cells / (r_ms / 1e3) / 1e9 / peak}
     if not args.no_other_configs:
         other = run_other_configs(lbm, W_stream=stream, barrier=barrier)
         if rank == 0:

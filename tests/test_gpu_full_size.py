@@ -91,6 +91,21 @@ def test_config3_full_size_first_step_sampled():
     assert np.abs(got - want).max() <= 10 * TOL["f32"] * np.abs(want).max()
 
 
+@pytest.mark.parametrize("store,unit", [("f16_dev", 2.0 ** -11), ("bf16_dev", 2.0 ** -8)])
+def test_config4_full_size_first_step_sampled(store, unit):
+    """The reduced-precision configuration: the benchmark workload with 16-bit deviation storage
+    (f - w rho_ref stored, collision in FP32). One step at 72 sampled cells against the oracle's
+    per-cell collisions of the FP64 equilibrium: the deviations agree within the rounding of the
+    stored input and output (4 units of the 16-bit format)."""
+    wl = W.taylor_green_3d(store=store)
+    rho, u = wl.fields()
+    cells = _sample_cells(wl.n, 64, seed=7)
+    got = _gpu_first_step(wl, cells, rho, u)
+    want = _oracle_first_step(wl, cells, rho, u)
+    w = oracle_lattice(wl.lattice).w[:, None]
+    assert rel_l2(got - w, want - w) <= 4 * unit
+
+
 @pytest.mark.parametrize("store", ["f32", "f64"])
 def test_config2_full_size_first_step_sampled(store):
     """rD2Q13 nonlinear CDE hill, 1024 x 768, FP32 and FP64: one step from the seeded fields at
