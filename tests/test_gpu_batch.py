@@ -77,6 +77,7 @@ def test_batch_equals_single_solve_path():
     c = b.counters()
     assert c["groups"] == len({(name, st) for name, _, _, st in MIX}) and c["steps"] == 13
     exact = [_compare(x, y, spec[3]) for x, y, spec in zip(alone, batched, MIX)]
+    assert all(exact)   # the same per-cell code: bitwise the same fields
     # membership changes: drop two solves, add a fresh one, keep stepping
     b.remove(batched[1])
     b.remove(batched[4])
