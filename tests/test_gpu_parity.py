@@ -621,4 +621,3 @@ def test_ncde_cross_diffusion_errors():
         gm.set_ncde_cross_diffusion(0.1, np.zeros((8, 8)))
     with pytest.raises(ValueError):
         gm.set_ncde_cross_diffusion(0.1, np.zeros((4, 8)))
-
