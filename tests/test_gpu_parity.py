@@ -621,3 +621,38 @@ def test_ncde_cross_diffusion_errors():
         gm.set_ncde_cross_diffusion(0.1, np.zeros((8, 8)))
     with pytest.raises(ValueError):
         gm.set_ncde_cross_diffusion(0.1, np.zeros((4, 8)))
+
+
+COMBINED = [  # (lattice, eq, settings): several extensions on one solve
+    ("rD2Q25", "nse", dict(s_bulk=0.9, s_orders={4: 0.8, 5: 1.35, 6: 1.6}, cs2_eq=0.7, force=(1, 0, 2e-3, 1, 0.1))),
+    ("rD3Q53", "nse", dict(s_bulk=1.1, s_orders={4: 0.9, 5: 1.2, 6: 1.5, 7: 1.0, 8: 1.3}, force=(2, 0, 2e-3, 1, 0.1))),
+    ("rD3Q27", "nse", dict(s_bulk=0.95, s_orders={4: 0.85, 5: 1.25, 6: 1.4}, m2g_aniso=True, force=(0, 2, 2e-3, 1, 0.1))),
+    ("rD2Q13", "ncde", dict(ncde_mode="rate", a1=-0.2, a2=0.03, s_orders={4: 1.3, 5: 0.8},
+                            u_const=(0.04, 0.02), nonlin=1.0)),
+]
+
+
+@pytest.mark.parametrize("store,tensor", [("f64", 0), ("f32", 0), ("f32", 1)])
+@pytest.mark.parametrize("name,eq,settings", COMBINED)
+def test_combined_extensions_step(name, eq, settings, store, tensor):
+    """The extensions together on one solve (bulk block, per-order rates, p = rho RT, body force,
+    the M2G density-gradient term; NCDE per-cell rates with the mixed-derivative and
+    cross-diffusion terms and per-order rates): three steps from far-from-equilibrium populations
+    against the oracle, on the CUDA cores and (FP32) with the higher rows on tcgen05."""
+    spec = ALL_SPECS[name]
+    n = RAGGED[spec.d]
+    s = _random_rates(spec.R, 51)
+    kw = dict(settings)
+    if "a2" in kw:
+        kw["psi"] = round_to_store(I.random_scalar(n, seed=9), store)
+    om = oracle_model(spec, eq, n, s, 1.15, **kw)
+    gm = gpu_model(spec, eq, n, s, 1.15, store=store, **kw)
+    if store != "f64":
+        gm.set_tensor_cores(tensor)
+    f0 = round_to_store(I.random_populations(n, om.lat.Q, seed=27), store)
+    om.set_populations(f0)
+    gm.set_populations(f0)
+    for _ in range(3):
+        om.step(1)
+        gm.step(1)
+        assert rel_l2(gm.get_populations(), om.f) <= TOL[store]
