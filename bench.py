@@ -522,6 +522,9 @@ def bench_ours(args):
             line["variants"][key] = {"kernel": kern, "steps": vsteps, "ms_per_step": r_ms,
                                      "mlups": cells / r_ms / 1e3,
                                      "hbm_frac": 2 * Q * 2 * cells / (r_ms / 1e3) / 1e9 / peak}
+    ext = run_extensions(lbm, args, stream, time_steps)
+    if rank == 0:
+        line["extensions"] = ext
     if not args.no_other_configs:
         other = run_other_configs(lbm, W_stream=stream, barrier=barrier)
         if rank == 0:
@@ -539,6 +542,60 @@ def bench_ours(args):
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_extensions(lbm, args, stream, time_steps):
+    """The cost of the model extensions on grids larger than L2, timed like the variants: the bulk
+    block of Eq. (4-27) on the benchmark workload; the single-speed rD3Q27 Taylor-Green flow on
+    the same grid with the delta4 term of M2G (a density read at the 2d neighbours and one written
+    per cell); the config-2 lattice (rD2Q13 NCDE) on a 4096 x 3072 grid, moment variant and the
+    per-cell-rate variant with the mixed-derivative and cross-diffusion terms (phi and psi
+    fields)."""
+    import numpy as np
+    import torch
+    from paper_2512_16230_gb300 import inputs as I
+    from paper_2512_16230_gb300 import workloads as W
+    peak, _ = _peaks()
+    out = {}
+
+    def run(key, wl, setup, bytes_per_cell, note):
+        spec = wl.lattice
+        lat = lbm.Lattice(spec.kind, spec.c, spec.cs2, spec.free_w)
+        m = lbm.Model(lat, wl.eq, wl.n, store=wl.store, stream=stream.cuda_stream)
+        m.set_relaxation(wl.s, wl.s_high)
+        if wl.force is not None:
+            m.set_force(*wl.force)
+        if wl.u_const is not None:
+            m.set_ncde(wl.u_const, wl.nonlin)
+        rho, u = wl.fields()
+        m.init_fields(rho, None if u is None else np.ascontiguousarray(u))
+        setup(m)
+        ms = time_steps(m)
+        m.close()
+        torch.cuda.empty_cache()
+        out[key] = {"workload": note, "ms_per_step": ms, "mlups": wl.ncells / ms / 1e3,
+                    "algorithmic_bytes_per_cell": bytes_per_cell,
+                    "hbm_frac": bytes_per_cell * wl.ncells / (ms / 1e3) / 1e9 / peak}
+
+    grid = tuple(args.grid)
+    wl = W.taylor_green_3d(n=grid)
+    run("bulk_viscosity", wl, lambda m: m.set_bulk(0.9), 2 * 53 * 4,
+        f"rD3Q53 Taylor-Green {grid[0]}x{grid[1]}x{grid[2]} FP32, s_b = 0.9")
+    wl = W.taylor_green_3d(n=grid, lattice="rD3Q27", re=100.0, ma=0.1)
+    run("single_speed_m2g_delta4", wl, lambda m: m.set_m2g_anisotropy(1), 2 * 27 * 4 + 8,
+        f"rD3Q27 Taylor-Green {grid[0]}x{grid[1]}x{grid[2]} FP32 with the delta4 term of M2G")
+    nc = (4096, 3072)
+    wl = W.ncde_hill(n=nc, sigma=80.0)
+    run("ncde_moment", wl, lambda m: None, 2 * 13 * 4 + 8,
+        f"rD2Q13 nonlinear CDE {nc[0]}x{nc[1]} FP32, moment variant")
+    psi = I.random_scalar(nc, seed=1)
+
+    def rate_cross(m):
+        m.set_ncde_variant("rate", -0.2)
+        m.set_ncde_cross_diffusion(0.02, psi)
+    run("ncde_rate_mixed_cross", wl, rate_cross, 2 * 13 * 4 + 8 + 4,
+        f"rD2Q13 nonlinear CDE {nc[0]}x{nc[1]} FP32, per-cell rates, a1 = -0.2, cross diffusion a2 = 0.02")
+    return out
 
 
 def run_other_configs(lbm, W_stream, barrier):
