@@ -156,7 +156,9 @@ lbm_status lbm_model_workspace_bytes(const lbm_lattice* lat, lbm_eq eq, const in
                                      lbm_dtype store, size_t* bytes);
 
 /* Create a model on grid n[d] (host memory). Every n[a] must be at least the largest velocity
- * component of the lattice (2 or 3) and the cell count below 2^31.
+ * component of the lattice (2 or 3) and the cell count at most 2^31 - 2^21 = 2,145,386,496 (cell
+ * indices are 32-bit in the kernels; the margin keeps every index a launch forms below 2^31).
+ * lbm_model_workspace_bytes applies the same checks (LBM_ERR_ARG) without allocating anything.
  * store/compute: (F64, F64), (F32, F32), (BF16_DEV or F16_DEV, F32).
  * stream    : cudaStream_t on which every kernel of the model runs (NULL: legacy default).
  * workspace : device buffer of at least lbm_model_workspace_bytes(), 256-byte aligned, owned by
@@ -208,7 +210,9 @@ lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_o
  * called: the tensor cores with distinct higher-order rates (there they are the faster kernel),
  * the CUDA cores otherwise.
  * Device-side waits are bounded; a timeout is latched in the model's status word and returned as
- * LBM_ERR_TIMEOUT by the next lbm_model_synchronize / read / get / sums call.
+ * LBM_ERR_TIMEOUT by the next lbm_model_synchronize / read / get / sums call. After a timeout the
+ * populations (and the NCDE / density history fields) are undefined: re-initialise the model
+ * (lbm_model_init_fields or lbm_model_set_populations) before stepping it again.
  * enable = 2 is a test hook for that path: the kernel issues no matrix product, every wait runs
  * out after a short limit, the CTAs free their tensor memory and return, and the populations
  * are left undefined.
@@ -306,8 +310,9 @@ lbm_status lbm_model_read_fields(lbm_model* m, double* rho_or_phi, double* u, in
  * Synchronous. Returns LBM_ERR_NONFINITE (with the sums still written) if any is NaN/inf. */
 lbm_status lbm_model_conserved_sums(lbm_model* m, double* out_host);
 
-/* The same sums for callers that may not allocate device memory (graph capture, fixed-budget or
- * pool-managed device memory, out-of-memory diagnostics). The paper has no counterpart: this is
+/* The same sums for callers that may not allocate device memory (hosts whose device memory is
+ * managed by their own pool allocator or capped by a fixed budget, diagnostics after an
+ * out-of-memory error). The paper has no counterpart: this is
  * an interface variant of lbm_model_conserved_sums. Allocates nothing and synchronizes nothing:
  * the reduction scratch is a static device array of 608 x 4 doubles (19,456 bytes) resident on
  * every GPU that loads the library, the result goes to out_dev[4] (device memory, caller-owned,
@@ -316,7 +321,9 @@ lbm_status lbm_model_conserved_sums(lbm_model* m, double* out_host);
  * make it before any stream capture. All calls share the array and every call rewrites the slots
  * it reads, so no clearing is needed, but calls whose kernels overlap on the GPU race on it.
  * The reduction never needs more than the 608 slots; a build whose reduction grid exceeds the
- * array is rejected with LBM_ERR_ARG. Non-finite sums are not detected (no host read). */
+ * array is rejected with LBM_ERR_ARG, and so is an out_dev that is not device or managed memory
+ * of the model's GPU. Non-finite sums are not detected (no host read). The cached address is
+ * valid for the device's context: after cudaDeviceReset, reload the library. */
 lbm_status lbm_model_conserved_sums_noalloc(lbm_model* m, double* out_dev);
 
 /* Completed time steps since the last init/set; kernels launched by this model so far. */

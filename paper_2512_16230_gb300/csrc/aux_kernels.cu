@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(256) k_sums_partial(const GenParams p, const G
                                                       const ST* __restrict__ A, double* __restrict__ partials) {
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const size_t N = size_t(p.ncells);
-  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < p.ncells;
-       cell += gridDim.x * blockDim.x) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t cell = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; cell < p.ncells; cell += stride) {
     CT m = CT(0), j[3] = {CT(0), CT(0), CT(0)};
     for (int i = 0; i < p.Q; ++i) {
       const CT f = Codec<ST>::template dec<CT>(A[size_t(i) * N + cell], t.wref[i]);

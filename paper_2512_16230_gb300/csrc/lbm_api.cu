@@ -265,7 +265,8 @@ lbm_status check_grid(const lbm_lattice* L, const int64_t* n) {
                                         " (the largest velocity component)");
     if (n[a] > (int64_t(1) << 30)) return set_error(LBM_ERR_ARG, "grid extent too large");
     ncells *= n[a];
-    if (ncells >= (int64_t(1) << 31)) return set_error(LBM_ERR_ARG, "cell count must be below 2^31");
+    if (ncells > kMaxCells)
+      return set_error(LBM_ERR_ARG, "cell count must be at most 2^31 - 2^21 (" + std::to_string(kMaxCells) + ")");
   }
   return LBM_OK;
 }

@@ -87,6 +87,11 @@ namespace lbm {
 #endif
 constexpr int kBlock = LBM_K1_BLOCK;  // threads per block of the cell kernels
 constexpr int kRedBlocks = 608;      // blocks of the conservation-sum reduction (4 x 152 SMs)
+// Largest accepted cell count. Cell indices are 32-bit in the kernels; the margin below 2^31 keeps
+// every index a launch or a grid-stride loop can form (cell + one block, cell + the reduction
+// grid's stride of kRedBlocks x 256 threads, a tile start + the tile) below 2^31.
+constexpr int64_t kMaxCells = (int64_t(1) << 31) - (int64_t(1) << 21);
+static_assert(int64_t(kRedBlocks) * 256 < (int64_t(1) << 21), "reduction stride within the index margin");
 
 // Kernel parameters of the time step, passed by value (they live in the constant bank, so
 // every table read below is an operand of the arithmetic instruction, not a memory load).

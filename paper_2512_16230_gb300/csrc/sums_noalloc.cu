@@ -1,10 +1,10 @@
 // Conservation sums without any device allocation.
 //
-// Some callers cannot call cudaMalloc when they need the sums: code that records work into a
-// CUDA graph (allocation calls are not legal during stream capture), hosts that hand all device
-// memory to their own pool allocator or run under a fixed memory budget, and diagnostics that
-// must still work after the device has run out of memory. lbm_model_conserved_sums_noalloc
-// serves them: its reduction scratch is the file-scope device array below, compiled into the
+// Some callers cannot call cudaMalloc when they need the sums: hosts that hand all device memory
+// to their own pool allocator (a cudaMalloc behind the pool's back would fragment or exceed what
+// it manages), runtimes that run under a fixed device-memory budget, and diagnostics that must
+// still work after the device has run out of memory. lbm_model_conserved_sums_noalloc serves
+// them: its reduction scratch is the file-scope device array below, compiled into the
 // library and resident on every GPU that loads it until the process exits, and its result goes
 // to a buffer the caller already owns.
 //
@@ -17,7 +17,8 @@
 // Host code cannot use the array's name as a device address (in host code it names a host-side
 // stand-in), so the first call on each device looks the address up with cudaGetSymbolAddress,
 // with that device current, and caches it. That first call may also load the library's device
-// code for this file; make it before any stream capture begins.
+// code for this file; make it before any stream capture begins. The cached address belongs to
+// the device's current context: after cudaDeviceReset the library must be reloaded.
 #include <mutex>
 #include <string>
 
@@ -52,6 +53,16 @@ extern "C" lbm_status lbm_model_conserved_sums_noalloc(lbm_model* m, double* out
   if (!m || !out_dev) return lbm::set_error(LBM_ERR_ARG, "NULL argument");
   if (reinterpret_cast<uintptr_t>(out_dev) % alignof(double) != 0)
     return lbm::set_error(LBM_ERR_ARG, "out_dev must be 8-byte aligned device memory");
+  // the result is written by a kernel on the model's GPU: out_dev must be memory of that GPU
+  // (a host pointer or a peer GPU's buffer would fault there)
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, out_dev) != cudaSuccess) {
+    cudaGetLastError();
+    return lbm::set_error(LBM_ERR_ARG, "out_dev is not a device pointer");
+  }
+  if (!((attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) && attr.device == m->device))
+    return lbm::set_error(LBM_ERR_ARG, "out_dev must be device or managed memory of the model's GPU (device " +
+                                           std::to_string(m->device) + ")");
   if (lbm::kRedBlocks > kNoAllocSlots)
     return lbm::set_error(LBM_ERR_ARG, "the reduction needs " + std::to_string(lbm::kRedBlocks) +
                                            " scratch slots, the static array holds " + std::to_string(kNoAllocSlots));

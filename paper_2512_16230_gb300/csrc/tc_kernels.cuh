@@ -14,8 +14,9 @@
 // operands, y_r = sum_i H_r(c_i) d_i in the forward product and sum_r H_r(c_i) z_r (z_r = a_r y_r,
 // a_r = -(s_r - s_h) / N_r) in the back projection, which is the full Q x Q collision.
 // Operands sit in shared memory in the K-major, non-swizzled canonical layout (core matrices of
-// 8 rows x 16 bytes). Every mbarrier wait is bounded: on timeout the CTA records an error in the
-// model's status word, frees its tensor memory and returns.
+// 8 rows x 16 bytes). Every mbarrier wait is bounded: on timeout the CTA issues no further
+// product, waits (bounded again) for the one in flight, records an error in the model's status
+// word, frees its tensor memory and returns.
 #pragma once
 
 #include "tcgen05.cuh"
@@ -335,7 +336,12 @@ __global__ void __launch_bounds__(128, TcShape<L, HI>::CTAS)
     __syncthreads();
     if (next < tp.ntiles) stage(nraw);
   }
-  if (failed && tid == 0) atomicExch(tp.status, 1);
+  if (failed) {
+    // the product whose wait ran out may still be writing this CTA's TMEM columns: give its
+    // commit one more bounded wait before the columns are released (and issue nothing more)
+    if (!tp.no_issue) tc::mbar_wait_bounded(&sm.mbar, phase ^ 1u, tp.wait_limit);
+    if (tid == 0) atomicExch(tp.status, 1);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -577,7 +583,10 @@ __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<floa
     tc::fence_before_sync();
     __syncthreads();
   }
-  if (failed && tid == 0) atomicExch(tp.status, 1);
+  if (failed) {
+    if (!tp.no_issue) tc::mbar_wait_bounded(&sm.mbar, phase ^ 1u, tp.wait_limit);  // as in k_step_tc
+    if (tid == 0) atomicExch(tp.status, 1);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();

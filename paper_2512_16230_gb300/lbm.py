@@ -224,8 +224,11 @@ class Model:
         self.workspace_bytes = nbytes.value
         self._ws = workspace
         self.stream = stream
+        self.device_index = None
         try:
             import torch
+            if torch.cuda.is_available():
+                self.device_index = torch.cuda.current_device()
             if stream is None and torch.cuda.is_available():
                 self.stream = torch.cuda.current_stream().cuda_stream
             if workspace is None and torch.cuda.is_available():
@@ -357,6 +360,8 @@ class Model:
         p, dev, _ = _ptr(out)
         if not dev or out.numel() < 4:
             raise ValueError("out must be a torch CUDA float64 tensor with 4 elements")
+        if self.device_index is not None and out.device.index != self.device_index:
+            raise ValueError(f"out must live on the model's GPU (cuda:{self.device_index})")
         _check(load().lbm_model_conserved_sums_noalloc(self.handle, c_void_p(p)), "lbm_model_conserved_sums_noalloc")
         return out
 

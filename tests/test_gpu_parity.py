@@ -209,6 +209,11 @@ def test_invalid_arguments_are_rejected():
         lbm.Model(lat, "nse", (1, 8, 8))
     with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):        # 2^31 cells: rejected before any allocation
         lbm.Model(lat, "nse", (2048, 2048, 512))
+    # the largest accepted cell count is 2^31 - 2^21 (checked without allocating: workspace_bytes)
+    assert 1024 * 1024 * 2046 == 2 ** 31 - 2 ** 21
+    assert lbm.workspace_bytes(lat, "nse", (1024, 1024, 2046), "f16_dev") > 0
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+        lbm.workspace_bytes(lat, "nse", (1024, 1024, 2047), "f16_dev")
     with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
         lbm.Lattice("rD3Q53", spec.c, spec.cs2, ())
     with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):

@@ -1,9 +1,9 @@
 """The allocation-free conservation sums (lbm_model_conserved_sums_noalloc) agree with
 lbm_model_conserved_sums.
 
-The entry point serves callers that cannot call cudaMalloc when they need the sums: code recording
-into a CUDA graph, hosts whose device memory belongs to a pool allocator or a fixed budget, and
-diagnostics after an out-of-memory error. Its reduction scratch is a static device array that
+The entry point serves callers that cannot call cudaMalloc when they need the sums: hosts whose
+device memory belongs to their own pool allocator or to a fixed budget, and diagnostics after an
+out-of-memory error. Its reduction scratch is a static device array that
 every call reuses, so the test calls it twice in a row, with a time step in between, and checks
 that the second result is not contaminated by the first. This file is collected last and must
 pass both alone in a fresh process and after the other GPU tests.
@@ -49,3 +49,6 @@ def test_noalloc_rejects_bad_output(lbm_lib):
     lat, m = _model(lbm_lib)
     assert lbm.load().lbm_model_conserved_sums_noalloc(m.handle, None) == 1    # LBM_ERR_ARG
     assert lbm.load().lbm_model_conserved_sums_noalloc(None, None) == 1
+    host = np.zeros(4)                                                          # host memory: rejected
+    assert lbm.load().lbm_model_conserved_sums_noalloc(m.handle, host.ctypes.data) == 1
+    assert np.all(host == 0.0)
