@@ -88,6 +88,13 @@ typedef enum {
   LBM_NCDE_CDE = 2     /* diffusion-based CDE, App. A special case (3)                        */
 } lbm_ncde_variant;
 
+/* How the CUDA-core collide-stream kernel of 16-bit storage gathers the pull sources. */
+typedef enum {
+  LBM_GATHER_AUTO = 0,    /* rows when they apply (default), threads otherwise                 */
+  LBM_GATHER_THREADS = 1, /* every thread loads its Q sources from global memory               */
+  LBM_GATHER_ROWS = 2     /* bulk copies of whole source x-rows into shared memory             */
+} lbm_gather;
+
 int lbm_abi_version(void);
 
 /* Thread-local description of the last error returned on this thread ("" if none). */
@@ -218,6 +225,17 @@ lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_o
  * are left undefined.
  * Errors: LBM_ERR_ARG (FP64 storage, enable not in {0, 1, 2}). */
 lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable);
+
+/* Gather of the pull streaming (Eq. (2-2b)) for 16-bit deviation storage on the CUDA cores
+ * (the reduced-form collision and lbm_model_stream_only). ROWS: a CTA works on whole x-rows; the
+ * source x-row (y - e_y, z - e_z) of each population comes into shared memory by one bulk copy
+ * (n_x * 2 bytes) and every thread reads its sources there at (x - e_x) mod n_x. It applies when
+ * n_x is a multiple of 8 (16-byte rows) and at most 256 (3D) or 1024 (2D) cells. THREADS: every
+ * thread loads its own sources from global memory. Both give bitwise the same populations.
+ * AUTO (default) takes ROWS where it applies. Errors: LBM_ERR_ARG for an unknown mode, or ROWS
+ * on a model it does not apply to; a step with ROWS forced and per-order rates or the tensor
+ * cores (which have no row-staged kernel) returns LBM_ERR_NOT_IMPLEMENTED. */
+lbm_status lbm_model_set_gather(lbm_model* m, lbm_gather mode);
 
 /* Equation of state p = rho * cs2_eq (NSE, Eq. (M-NSEs-6-1)) or the prefactor of the diffusion
  * moment M2 = cs2_eq D(phi) I (NCDE, Eq. (M-NCDE-6)). */

@@ -575,6 +575,27 @@ lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable) {
   return LBM_OK;
 }
 
+lbm_status lbm_model_set_gather(lbm_model* m, lbm_gather mode) {
+  if (!m) return set_error(LBM_ERR_ARG, "NULL model");
+  if (mode != LBM_GATHER_AUTO && mode != LBM_GATHER_THREADS && mode != LBM_GATHER_ROWS)
+    return set_error(LBM_ERR_ARG, "gather must be LBM_GATHER_AUTO, _THREADS or _ROWS");
+  if (mode == LBM_GATHER_ROWS) {
+    RowPlan plan;
+    DeviceGuard guard(m->device);
+    bool ok = false;
+    lbm_status st = dispatch_kind(m->lat->kind, [&](auto kind) -> lbm_status {
+      ok = RowLaunch<decltype(kind)::value>::plan(m, &plan);
+      return LBM_OK;
+    });
+    if (st != LBM_OK) return st;
+    if (!ok)
+      return set_error(LBM_ERR_ARG, "the row-staged gather needs 16-bit deviation storage and n_x a multiple of 8, "
+                                    "at most 256 (3D) or 1024 (2D) cells");
+  }
+  m->gather = int(mode);
+  return LBM_OK;
+}
+
 lbm_status lbm_model_set_eos(lbm_model* m, double cs2_eq) {
   if (!m) return set_error(LBM_ERR_ARG, "NULL model");
   if (!(cs2_eq > 0.0) || !std::isfinite(cs2_eq)) return set_error(LBM_ERR_ARG, "cs2_eq must be positive");

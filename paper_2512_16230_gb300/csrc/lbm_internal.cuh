@@ -72,6 +72,7 @@ struct lbm_model {
   bool tensor_cores; // 16-bit storage: contractions on tcgen05 (k_step_tc)
   bool tc_auto;      // no explicit choice yet: tcgen05 with per-order rates (FP32 or 16-bit storage)
   bool tc_no_issue;  // test hook: k_step_tc issues no matrix product, so its waits run out
+  int gather;        // lbm_gather: how the CUDA-core kernel of 16-bit storage gathers (auto, threads, rows)
   int* status;       // device status word: non-zero after a device-side wait ran out
   int64_t steps, launches;
   int device;
@@ -158,6 +159,37 @@ struct TcParams {
   int* status;
   unsigned wait_limit;  // mbarrier polls before a wait is declared lost
   int no_issue;         // test hook: issue no matrix product (every wait then runs out)
+};
+
+// Row-staged collide-stream kernel (16-bit storage, row_kernels.cuh): row buffers of kRowPitch3 (3D)
+// or kRowPitch2 (2D) cells per population, kRowThreads threads per CTA, up to kRowMaxStages
+// buffers behind kRowBarBytes of mbarriers.
+constexpr int kRowPitch3 = 256, kRowPitch2 = 1024;
+constexpr int kRowThreads = 256;
+constexpr int kRowMaxStages = 8;
+constexpr int kRowBarBytes = 2 * kRowMaxStages * 8;
+struct RowParams {
+  int8_t ey[kMaxQ], ez[kMaxQ];  // y and z velocity components (pull source rows)
+  int nrows;                    // n_y n_z
+  int stages;                   // row buffers per CTA
+  uint32_t stage_bytes;         // Q * pitch * 2
+  uint32_t row_bytes;           // n_x * 2: one bulk copy
+  int* status;
+  unsigned wait_limit;          // mbarrier polls before a wait is declared lost
+};
+struct RowPlan {
+  int grid;
+  size_t smem;
+  RowParams rp;
+};
+template <int KIND>
+struct RowLaunch {
+  // false when the kernel does not apply (storage not 16-bit, n_x not a multiple of 8 or above the
+  // pitch, or the shared memory cannot hold two row buffers)
+  static bool plan(const lbm_model* m, RowPlan* out);
+  static lbm_status configure(const lbm_model* m, const RowPlan& plan, bool collide);
+  static lbm_status launch(const lbm_model* m, const RowPlan& plan, const StepParams<float>& p, const void* fin,
+                           void* fout, float* phi, bool collide);
 };
 
 // Multiply-high division by a runtime divisor 2 <= d < 2^31, exact for numerators below 2^31:

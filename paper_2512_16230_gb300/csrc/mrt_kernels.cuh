@@ -1026,6 +1026,22 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
       tgrid = tc_grid(m, tp.ntiles, k, 3, tsmem);
     }
   }
+  // 16-bit storage on the CUDA cores: the row-staged gather where it applies (or is forced)
+  [[maybe_unused]] RowPlan rplan;
+  bool rows = false;
+  if constexpr (is_deviation_storage<ST>()) {
+    if (m->gather == LBM_GATHER_ROWS && (tensor || high))
+      return set_error(LBM_ERR_NOT_IMPLEMENTED,
+                       "the row-staged gather has no kernel for per-order rates or the tensor cores");
+    if (m->gather != LBM_GATHER_THREADS && !tensor && !high) {
+      rows = RowLaunch<L::KIND>::plan(m, &rplan);
+      if (!rows && m->gather == LBM_GATHER_ROWS) return set_error(LBM_ERR_ARG, "the row-staged gather does not apply");
+      if (rows && nsteps > 0) {
+        const lbm_status st = RowLaunch<L::KIND>::configure(m, rplan, collide_on);
+        if (st != LBM_OK) return st;
+      }
+    }
+  }
   const bool hist = collide_on && m->m2g_aniso;
   p.grad_on = collide_on && p.grad_on;
   for (int64_t s = 0; s < nsteps; ++s) {
@@ -1037,7 +1053,11 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
     }
     bool done = false;
     if constexpr (is_deviation_storage<ST>()) {
-      if (tensor) {
+      if (rows) {
+        const lbm_status st = RowLaunch<L::KIND>::launch(m, rplan, p, fin, fout, phi, collide_on);
+        if (st != LBM_OK) return st;
+        done = true;
+      } else if (tensor) {
         if (high) {
           if (m->eq == LBM_NSE)
             k_step_tc<L, ST, LBM_NSE, true><<<tgrid, 128, tsmem, m->stream>>>(p, tp, fin, fout, phi);

@@ -33,6 +33,7 @@ _P = c_void_p
 _PD = POINTER(c_double)
 _PI64 = POINTER(c_int64)
 NCDE_VARIANTS = {"moment": 0, "rate": 1, "cde": 2}
+GATHERS = {"auto": 0, "threads": 1, "rows": 2}
 SIGNATURES = {
     "lbm_abi_version": (c_int, []),
     "lbm_last_error": (c_char_p, []),
@@ -53,6 +54,7 @@ SIGNATURES = {
     "lbm_model_set_m2g_anisotropy": (c_int, [_P, c_int]),
     "lbm_model_set_ncde_cross_diffusion": (c_int, [_P, c_double, _P, c_int]),
     "lbm_model_set_tensor_cores": (c_int, [_P, c_int]),
+    "lbm_model_set_gather": (c_int, [_P, c_int]),
     "lbm_model_init_fields": (c_int, [_P, _P, _P, c_int]),
     "lbm_model_set_populations": (c_int, [_P, _P, c_int]),
     "lbm_model_get_populations": (c_int, [_P, _P, c_int]),
@@ -274,6 +276,11 @@ class Model:
         """16-bit storage: run the collision's contractions on tcgen05 (0 = CUDA cores; 2 = the
         test hook whose waits run out)."""
         _check(load().lbm_model_set_tensor_cores(self.handle, int(enable)), "lbm_model_set_tensor_cores")
+
+    def set_gather(self, mode="auto"):
+        """16-bit storage on the CUDA cores: "rows" (source x-rows staged in shared memory by bulk
+        copies), "threads" (per-thread loads from global memory) or "auto" (rows where they apply)."""
+        _check(load().lbm_model_set_gather(self.handle, GATHERS[mode]), "lbm_model_set_gather")
 
     def set_ncde_variant(self, variant="moment", a1=0.0):
         """App. A variants: "moment" (default), "rate" (per-cell S1(phi)) or "cde" (diffusion-based

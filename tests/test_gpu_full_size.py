@@ -106,6 +106,29 @@ def test_config4_full_size_first_step_sampled(store, unit):
     assert rel_l2(got - w, want - w) <= 4 * unit
 
 
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+def test_config4_full_size_row_gather_is_bitwise_thread_gather(store):
+    """The benchmark workload in 16-bit storage, two steps, with the launch the benchmark times (the
+    row-staged gather, chosen automatically for n_x = 256) and with the per-thread gather: the
+    whole population arrays are bitwise equal (compared on the device)."""
+    import torch
+    wl = W.taylor_green_3d(store=store)
+    rho, u = wl.fields()
+    out = {}
+    for mode in ("auto", "threads"):
+        gm = gpu_model(wl.lattice, wl.eq, wl.n, wl.s, wl.s_high, store=store)
+        gm.set_gather(mode)
+        gm.init_fields(rho, np.ascontiguousarray(u))
+        gm.step(2)
+        out[mode] = torch.empty((gm.Q,) + tuple(reversed(wl.n)), dtype=torch.float64, device="cuda")
+        gm.get_populations(out[mode])
+        gm.synchronize()
+        gm.close()
+    assert torch.equal(out["auto"], out["threads"])
+    del out
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("store", ["f32", "f64"])
 def test_config2_full_size_first_step_sampled(store):
     """rD2Q13 nonlinear CDE hill, 1024 x 768, FP32 and FP64: one step from the seeded fields at

@@ -1,0 +1,156 @@
+"""The row-staged gather of 16-bit deviation storage (lbm_model_set_gather "rows"): each CTA
+moves the source x-rows of its row's populations into shared memory with bulk copies and reads
+the pull sources (Eq. (2-2b)) there.
+
+Checks: propagation alone is bit-exact against the oracle's periodic shift (pure data movement,
+every wrap in x, y and z, row lengths from 8 cells to the 256 / 1024-cell pitch); a collide-stream
+step gives bitwise the populations of the per-thread gather (same collision code, same inputs),
+and one step stays within the 16-bit bounds of the FP64 oracle; the model extensions that read
+neighbour fields (the M2G density gradient, the NCDE cross diffusion) agree bitwise too.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_16230_gb300 import inputs as I
+from paper_2512_16230_gb300 import workloads as W
+
+from _harness import gpu_model, oracle_lattice, oracle_model, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+# n_x a multiple of 8 (16-byte rows); the smallest extents make every pull wrap, the largest n_x
+# fill the row buffers (256 cells in 3D, 1024 in 2D)
+ROW_GRIDS = {2: [(8, 3), (48, 13), (1024, 4)], 3: [(8, 2, 2), (24, 7, 5), (256, 3, 2)]}
+LATTICES = ["rD2Q13", "rD2Q17", "rD2Q21", "rD2Q25", "rD2Q9", "rD3Q27", "rD3Q33", "rD3Q45", "rD3Q53"]
+UNIT = {"bf16_dev": 2.0 ** -8, "f16_dev": 2.0 ** -11}
+
+
+@pytest.fixture(autouse=True)
+def _lib(lbm_lib):
+    return lbm_lib
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+@pytest.mark.parametrize("name", LATTICES)
+def test_row_gather_stream_only_is_bit_exact(name, store):
+    """Eq. (2-2b) alone through the row buffers: the same bits as the oracle's periodic shift of the
+    stored state, on every grid of ROW_GRIDS."""
+    spec = W.LATTICES[name]
+    for n in ROW_GRIDS[spec.d]:
+        gm = gpu_model(spec, "nse", n, np.ones(spec.R), store=store)
+        gm.set_gather("rows")
+        gm.set_populations(I.random_populations(n, gm.Q, seed=7))
+        g0 = gm.get_populations()          # the stored (16-bit) state, decoded
+        om = oracle_model(spec, "nse", n, np.ones(spec.R))
+        om.set_populations(g0)
+        gm.stream_only(3)
+        om.stream_only(3)
+        assert np.array_equal(gm.get_populations(), om.f), n
+        gm.close()
+
+
+def _step_kwargs(eq, d):
+    if eq == "nse":
+        return dict(s_high=1.3, cs2_eq=0.55, force=(0, d - 1, 3e-3, 1, 0.4))
+    return dict(s_high=1.3, cs2_eq=0.55, u_const=tuple(np.linspace(0.03, 0.06, d)), nonlin=1.0)
+
+
+def _near_equilibrium(w, n, Q, seed, eq):
+    r = np.random.default_rng(seed).uniform(-0.1, 0.1, size=(Q,) + tuple(reversed(n)))
+    base = 1.0 if eq == "nse" else 0.7
+    return w.reshape((-1,) + (1,) * len(n)) * base * (1.0 + r)
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+@pytest.mark.parametrize("eq", ["nse", "ncde"])
+@pytest.mark.parametrize("name", LATTICES)
+def test_row_gather_step_matches_thread_gather(name, eq, store):
+    """Three collide-stream steps (NSE with a body force through M1F and M2G; NCDE with M1G and the
+    nonlinear D(phi)) with random rates: the row-staged and the per-thread gather give bitwise the
+    same populations; after the first step both are within the 16-bit bound of the FP64 oracle
+    started from the same stored state (the input and output roundings, each <= one unit of the
+    format relative to the deviation, times the O(1) gain of the collision)."""
+    spec = W.LATTICES[name]
+    d = spec.d
+    n = ROW_GRIDS[d][1]
+    s = np.random.default_rng(3).uniform(0.6, 1.9, spec.R)
+    kw = _step_kwargs(eq, d)
+    om = oracle_model(spec, eq, n, s, **kw)
+    w = om.lat.w
+    f0 = _near_equilibrium(w, n, om.lat.Q, 5, eq)
+    out = {}
+    for mode in ("rows", "threads"):
+        gm = gpu_model(spec, eq, n, s, store=store, **kw)
+        gm.set_gather(mode)
+        gm.set_populations(f0)
+        if mode == "rows":
+            om.set_populations(gm.get_populations())     # the value the GPU holds
+            om.step(1)
+        gm.step(1)
+        out[mode, 1] = gm.get_populations()
+        gm.step(2)
+        out[mode, 3] = gm.get_populations()
+        gm.close()
+    assert np.array_equal(out["rows", 1], out["threads", 1])
+    assert np.array_equal(out["rows", 3], out["threads", 3])
+    ref = w.reshape((-1,) + (1,) * d) * (1.0 if eq == "nse" else 0.0)
+    err = rel_l2(out["rows", 1] - ref, om.f - ref)
+    assert err <= 4 * UNIT[store], err
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+def test_row_gather_with_gradient_terms(store):
+    """The extensions that read neighbour cells besides the populations: the delta4 term of M2G on
+    rD3Q27 (previous-step density at the 2d neighbours) and, on rD2Q13, the per-cell-rate NCDE with
+    the mixed-derivative and cross-diffusion terms (psi at the neighbours): bitwise the same with
+    both gathers over four steps."""
+    cases = []
+    spec = W.LATTICES["rD3Q27"]
+    n = (24, 7, 5)
+    cases.append((spec, "nse", n, dict(force=(0, 2, 2e-3, 1, 0.1)), lambda m: m.set_m2g_anisotropy(1)))
+    spec2 = W.LATTICES["rD2Q13"]
+    n2 = (48, 13)
+    psi = I.random_scalar(n2, seed=2)
+
+    def rate_cross(m):
+        m.set_ncde_variant("rate", -0.2)
+        m.set_ncde_cross_diffusion(0.02, psi)
+    cases.append((spec2, "ncde", n2, dict(u_const=(0.03, 0.02), nonlin=1.0), rate_cross))
+    for spec, eq, n, kw, extra in cases:
+        s = np.random.default_rng(4).uniform(0.7, 1.8, spec.R)
+        w = oracle_lattice(spec).w
+        f0 = _near_equilibrium(w, n, len(w), 9, eq)
+        res = {}
+        for mode in ("rows", "threads"):
+            gm = gpu_model(spec, eq, n, s, store=store, **kw)
+            extra(gm)
+            gm.set_gather(mode)
+            gm.set_populations(f0)
+            gm.step(4)
+            res[mode] = gm.get_populations()
+            gm.close()
+        assert np.array_equal(res["rows"], res["threads"]), spec.kind
+
+
+def test_row_gather_errors():
+    """ROWS is refused where it does not apply (n_x not a multiple of 8, above the pitch, FP32
+    storage) and a forced ROWS step with a kernel that has no row-staged form reports
+    LBM_ERR_NOT_IMPLEMENTED; nothing runs in either case."""
+    from paper_2512_16230_gb300 import lbm
+    spec = W.LATTICES["rD3Q53"]
+    for n, store in (((37, 8, 8), "f16_dev"), ((264, 4, 4), "f16_dev"), ((16, 8, 8), "f32")):
+        gm = gpu_model(spec, "nse", n, np.ones(spec.R), store=store)
+        with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
+            gm.set_gather("rows")
+        gm.close()
+    gm = gpu_model(spec, "nse", (16, 8, 8), np.ones(spec.R), store="f16_dev")
+    gm.set_gather("rows")
+    gm.set_tensor_cores(1)
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_NOT_IMPLEMENTED"):
+        gm.step(1)
+    gm.set_tensor_cores(0)
+    gm.set_high_rates([0.9, 1.2])
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_NOT_IMPLEMENTED"):
+        gm.step(1)
+    assert gm.counters() == (0, 0)
+    assert lbm.load().lbm_model_set_gather(gm.handle, 7) == 1    # unknown mode: LBM_ERR_ARG

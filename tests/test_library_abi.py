@@ -60,4 +60,5 @@ def test_binding_enums_match_the_header():
     assert {"LBM_" + k.upper(): v for k, v in lbm.DTYPES.items()} == dtypes
     assert {"LBM_" + k.upper(): v for k, v in lbm.EQS.items()} == _header_enum("lbm_eq")
     assert {"LBM_NCDE_" + k.upper(): v for k, v in lbm.NCDE_VARIANTS.items()} == _header_enum("lbm_ncde_variant")
+    assert {"LBM_GATHER_" + k.upper(): v for k, v in lbm.GATHERS.items()} == _header_enum("lbm_gather")
     assert {v: k for k, v in _header_enum("lbm_status").items()} == lbm.STATUS
