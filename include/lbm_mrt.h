@@ -229,9 +229,10 @@ lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable);
 /* Gather of the pull streaming (Eq. (2-2b)) for 16-bit deviation storage on the CUDA cores
  * (the reduced-form collision and lbm_model_stream_only). ROWS: a CTA works on whole x-rows; the
  * source x-row (y - e_y, z - e_z) of each population comes into shared memory by one bulk copy
- * (n_x * 2 bytes) and every thread reads its sources there at (x - e_x) mod n_x. It applies when
- * n_x is a multiple of 8 (16-byte rows) and at most 256 (3D) or 1024 (2D) cells. THREADS: every
- * thread loads its own sources from global memory. Both give bitwise the same populations.
+ * (n_x * 2 bytes), every thread reads its sources there at (x - e_x) mod n_x, and the collided row
+ * goes back to memory by one bulk copy per population. It applies when n_x is a multiple of 8
+ * (16-byte rows) and at most 256 cells. THREADS: every thread loads and stores its own cell's
+ * populations in global memory. Both give bitwise the same populations.
  * AUTO (default) takes ROWS where it applies. Errors: LBM_ERR_ARG for an unknown mode, or ROWS
  * on a model it does not apply to; a step with ROWS forced and per-order rates or the tensor
  * cores (which have no row-staged kernel) returns LBM_ERR_NOT_IMPLEMENTED. */

@@ -590,7 +590,7 @@ lbm_status lbm_model_set_gather(lbm_model* m, lbm_gather mode) {
     if (st != LBM_OK) return st;
     if (!ok)
       return set_error(LBM_ERR_ARG, "the row-staged gather needs 16-bit deviation storage and n_x a multiple of 8, "
-                                    "at most 256 (3D) or 1024 (2D) cells");
+                                    "at most 256 cells");
   }
   m->gather = int(mode);
   return LBM_OK;

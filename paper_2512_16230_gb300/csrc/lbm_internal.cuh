@@ -161,19 +161,21 @@ struct TcParams {
   int no_issue;         // test hook: issue no matrix product (every wait then runs out)
 };
 
-// Row-staged collide-stream kernel (16-bit storage, row_kernels.cuh): row buffers of kRowPitch3 (3D)
-// or kRowPitch2 (2D) cells per population, kRowThreads threads per CTA, up to kRowMaxStages
-// buffers behind kRowBarBytes of mbarriers.
-constexpr int kRowPitch3 = 256, kRowPitch2 = 1024;
-constexpr int kRowThreads = 256;
+// Row-staged collide-stream kernel (16-bit storage, row_kernels.cuh): row buffers of kRowPitch
+// cells per population (the largest n_x; one cell per thread of a kRowThreads CTA), up to
+// kRowMaxStages buffers behind kRowBarBytes of mbarriers and counters.
+constexpr int kRowPitch = 256;
+constexpr int kRowThreads = kRowPitch;
 constexpr int kRowMaxStages = 8;
-constexpr int kRowBarBytes = 2 * kRowMaxStages * 8;
+constexpr int kRowBarBytes = 256;
 struct RowParams {
-  int8_t ey[kMaxQ], ez[kMaxQ];  // y and z velocity components (pull source rows)
+  // byte offset from the start of row r of the population arrays to the pull-source row of
+  // population i, 2 (i N - (e_iy + e_iz n_y) n_x), valid for rows away from the y and z faces
+  int64_t src_off[kMaxQ];
+  int8_t ey[kMaxQ], ez[kMaxQ];  // y and z velocity components (source rows next to a face)
   int nrows;                    // n_y n_z
   int stages;                   // row buffers per CTA
   uint32_t stage_bytes;         // Q * pitch * 2
-  uint32_t row_bytes;           // n_x * 2: one bulk copy
   int* status;
   unsigned wait_limit;          // mbarrier polls before a wait is declared lost
 };

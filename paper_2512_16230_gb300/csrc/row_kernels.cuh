@@ -1,20 +1,23 @@
 // Row-staged collide-stream kernel for 16-bit deviation storage (FP16 or BF16 deviations
 // f_i - w_i rho_ref, collision arithmetic in FP32).
 //
-// The per-thread pull gather of k_step moves 64 bytes per warp access when a population takes
-// 2 bytes, too little per memory request to keep HBM busy. Here a CTA works on whole x-rows of
-// the grid instead. For the row (y, z) the pull sources of population i (Eq. (2-2b)) are the
-// cells (x - e_ix, y - e_iy, z - e_iz): the x-row (y - e_iy, z - e_iz) of array i, read with a
-// periodic shift along x. Warp 0 brings these Q source rows into shared memory with one bulk
-// copy each (n_x * 2 bytes, 16-byte aligned, completing on the stage's mbarrier), the periodic
-// wraps in y and z being the choice of source row. Every thread then reads its cell's
-// populations at (x - e_ix) mod n_x, so the wrap in x is an index wrap. A ring of row buffers
-// keeps the next rows in flight while the current one is collided; a buffer is refilled once
-// every warp has arrived on its `empty` mbarrier. The collision and the aligned per-cell stores
-// are those of k_step (same code, same inputs), so the results are bitwise the same.
+// The per-thread pull gather and store of k_step move 64 bytes per warp access when a population
+// takes 2 bytes, too little per memory request to keep HBM busy. Here a CTA works on whole x-rows
+// of the grid, one cell per thread, and moves memory in 512-byte warp accesses. For the row (y, z)
+// the pull sources of population i (Eq. (2-2b)) are the cells (x - e_ix, y - e_iy, z - e_iz): the
+// x-row (y - e_iy, z - e_iz) of array i, read with a periodic shift along x. The warps copy these
+// Q source rows into a shared-memory row buffer with 16-byte cp.async copies (one warp instruction
+// per population row, completing on the buffer's mbarrier); the periodic wraps in y and z are the
+// choice of source row, the wrap in x an index wrap: every thread reads its sources at
+// (x - e_ix) mod n_x. After a CTA barrier (every source read) the threads write their
+// post-collision populations back into the buffer at their own x, and after a second barrier the
+// warps store the Q rows with 16-byte stores. A ring of row buffers keeps the following rows in
+// flight while the current one is collided. The collision is the code of k_step on the same
+// inputs, so the results are bitwise the same.
 //
-// Every mbarrier wait is bounded: on timeout the CTA records an error in the model's status word,
-// waits (bounded again) for the copies it still has in flight and returns.
+// The wait for a row's copies is bounded: on timeout (decided for the whole CTA at the next
+// barrier) the CTA records an error in the model's status word, waits for its own copies and
+// returns.
 #pragma once
 
 #include <algorithm>
@@ -23,150 +26,156 @@
 
 namespace lbm {
 
-template <class L>
-struct RowShape {
-  static constexpr int PITCH = L::D == 3 ? kRowPitch3 : kRowPitch2;  // largest n_x (cells per row buffer)
-  static constexpr int THREADS = kRowThreads;
-  static constexpr int WARPS = THREADS / 32;
-};
-
 template <class L, class ST, int EQ, bool COLLIDE>
 __global__ void __launch_bounds__(kRowThreads, 2)
     k_step_rows(const StepParams<float> p, const RowParams rp, const ST* __restrict__ fin, ST* __restrict__ fout,
                 float* __restrict__ phi) {
-  using S = RowShape<L>;
-  constexpr int Q = L::Q, RM = L::RMAX, PITCH = S::PITCH;
+  constexpr int Q = L::Q, RM = L::RMAX, PITCH = kRowPitch, WARPS = kRowThreads / 32;
+  constexpr uint32_t ROWB = PITCH * sizeof(ST);  // bytes of one population's row in a buffer
+  static_assert(ROWB == 32 * 16, "a row of the buffer is one 16-byte chunk per lane");
   extern __shared__ __align__(128) uint8_t row_smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(row_smem);
-  uint64_t* empty = full + kRowMaxStages;
-  const ST* rows = reinterpret_cast<const ST*>(row_smem + kRowBarBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(row_smem);  // every thread's copies of the row landed
+  ST* rows = reinterpret_cast<ST*>(row_smem + kRowBarBytes);
   const uint32_t rows_s = tc::smem_addr(row_smem + kRowBarBytes);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nx = p.n[0], ny = p.n[1];
+  const int nx = p.n[0], ny = p.n[1], nz = L::D == 3 ? p.n[2] : 1;
   const int G = int(gridDim.x);
   const int K = (rp.nrows - int(blockIdx.x) + G - 1) / G;  // rows of this CTA (the grid is <= nrows)
   const int NS = rp.stages;
   const uint32_t stage_elems = rp.stage_bytes / uint32_t(sizeof(ST));
   const size_t N = size_t(p.ncells);
-  if (tid == 0) {
-    for (int s = 0; s < NS; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], S::WARPS);
+  const size_t pop_bytes = N * sizeof(ST);
+  const int x = tid;
+  const bool live = x < nx;
+  const bool lane_chunk = lane * 8 < nx;  // this lane's 16-byte chunk (8 cells) of a row exists
+  // rows of this CTA are r = blockIdx.x + k G: (y, z) advance by (G mod n_y, G div n_y) with a carry
+  const int gy = G % ny, gz = G / ny;
+  auto advance = [&](int& y, int& z) {
+    y += gy;
+    z += gz;
+    if (y >= ny) {
+      y -= ny;
+      z += 1;
     }
+  };
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) tc::mbar_init(&full[s], kRowThreads);
     tc::mbar_fence_init();
   }
   __syncthreads();
 
-  // warp 0: the Q source rows of local row j into stage j % NS
-  auto issue = [&](int j) {
-    const int r = int(blockIdx.x) + j * G;
-    const int y = r % ny, z = r / ny;
-    const int s = j % NS;
-    if (lane == 0) bulk::arrive_expect_tx(&full[s], uint32_t(Q) * rp.row_bytes);
-    __syncwarp();
-    for (int i = lane; i < Q; i += 32) {
-      int ys = y - rp.ey[i];
-      ys += ys < 0 ? ny : 0;
-      ys -= ys >= ny ? ny : 0;
-      int zs = 0;
-      if constexpr (L::D == 3) {
-        zs = z - rp.ez[i];
-        zs += zs < 0 ? p.n[2] : 0;
-        zs -= zs >= p.n[2] ? p.n[2] : 0;
+  // every thread: its chunks of the Q source rows of row (y, z) into buffer s (warp w takes the
+  // populations w, w + 8, ...), then one arrival on the buffer's mbarrier when they have landed
+  auto load_row = [&](int y, int z, int s) {
+    if (lane_chunk) {
+      const size_t r = size_t(z) * ny + y;
+      const uint8_t* base = reinterpret_cast<const uint8_t*>(fin) + (r * nx + lane * 8) * sizeof(ST);
+      const uint32_t dst = rows_s + uint32_t(s) * rp.stage_bytes + uint32_t(lane * 16);
+      const bool inner = y >= RM && y < ny - RM && (L::D == 2 || (z >= RM && z < nz - RM));
+      if (inner) {
+        for (int i = warp; i < Q; i += WARPS) bulk::cp_async16(dst + uint32_t(i) * ROWB, base + rp.src_off[i]);
+      } else {
+        const uint8_t* b0 = reinterpret_cast<const uint8_t*>(fin) + size_t(lane * 8) * sizeof(ST);
+        for (int i = warp; i < Q; i += WARPS) {
+          int ys = y - rp.ey[i];
+          ys += ys < 0 ? ny : 0;
+          ys -= ys >= ny ? ny : 0;
+          int zs = 0;
+          if constexpr (L::D == 3) {
+            zs = z - rp.ez[i];
+            zs += zs < 0 ? nz : 0;
+            zs -= zs >= nz ? nz : 0;
+          }
+          bulk::cp_async16(dst + uint32_t(i) * ROWB,
+                           b0 + size_t(i) * pop_bytes + (size_t(zs) * ny + ys) * nx * sizeof(ST));
+        }
       }
-      const ST* src = fin + size_t(i) * N + (size_t(zs) * size_t(ny) + size_t(ys)) * size_t(nx);
-      bulk::copy_g2s(rows_s + uint32_t(s) * rp.stage_bytes + uint32_t(i * PITCH * int(sizeof(ST))), src,
-                     rp.row_bytes, &full[s]);
     }
+    bulk::cp_async_arrive(&full[s]);
   };
 
-  int issued = 0;  // warp 0: local rows whose copies have been issued
+  int ly = int(blockIdx.x) % ny, lz = int(blockIdx.x) / ny;  // next row to load
+  int y = ly, z = lz;                                          // row being collided
+  for (int j = 0; j < K && j < NS - 1; ++j) {
+    load_row(ly, lz, j);
+    advance(ly, lz);
+  }
   bool failed = false;
-  if (warp == 0)
-    for (; issued < K && issued < NS; ++issued) issue(issued);
-  int k = 0;
-  for (; k < K; ++k) {
+  for (int k = 0; k < K; ++k) {
     const int s = k % NS;
-    // warp 0 refills the buffer of the previous row once every warp has read it
-    if (warp == 0 && k >= 1 && issued < K) {
-      const int sp = (k - 1) % NS;
-      bool ok = true;
-      if (lane == 0) ok = tc::mbar_wait_bounded(&empty[sp], uint32_t((k - 1) / NS) & 1u, rp.wait_limit);
-      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
-        failed = true;
-        break;
-      }
-      issue(issued++);
-    }
     const bool landed = tc::mbar_wait_bounded(&full[s], uint32_t(k / NS) & 1u, rp.wait_limit);
-    if (!__all_sync(0xffffffffu, landed)) {
+    const int r = z * ny + y;
+    ST* st = rows + size_t(s) * stage_elems;
+    float f[Q];
+    if (live && landed) {
+      int xo[2 * RM + 1];  // (x - sh) mod n_x for the x-shifts sh = -RM..RM
+#pragma unroll
+      for (int sh = -RM; sh <= RM; ++sh) {
+        int v = x - sh;
+        if (sh > 0) v += v < 0 ? nx : 0;
+        if (sh < 0) v -= v >= nx ? nx : 0;
+        xo[sh + RM] = v;
+      }
+      static_for<Q>([&](auto i) {
+        constexpr int I = decltype(i)::value;
+        f[I] = RawCodec<ST>::dec(st[I * PITCH + xo[RM + L::e(I).x]]);
+      });
+    }
+    // every source of the row read, and row k - 1 stored: its buffer takes row k + NS - 1
+    if (__syncthreads_or(!landed)) {
       failed = true;
       break;
     }
-    const int r = int(blockIdx.x) + k * G;
-    const int y = r % ny, z = r / ny;  // z = 0 in 2D
-    const ST* st = rows + size_t(s) * stage_elems;
-    for (int x0 = 0; x0 < nx; x0 += S::THREADS) {
-      const int x = x0 + tid;
-      const bool live = x < nx;
-      float f[Q];
-      if (live) {
-        int xo[2 * RM + 1];  // (x - sh) mod n_x for the x-shifts sh = -RM..RM
-#pragma unroll
-        for (int sh = -RM; sh <= RM; ++sh) {
-          int v = x - sh;
-          if (sh > 0) v += v < 0 ? nx : 0;
-          if (sh < 0) v -= v >= nx ? nx : 0;
-          xo[sh + RM] = v;
-        }
-        static_for<Q>([&](auto i) {
-          constexpr int I = decltype(i)::value;
-          f[I] = RawCodec<ST>::dec(st[I * PITCH + xo[RM + L::e(I).x]]);
-        });
-      }
-      if (x0 + S::THREADS >= nx) {  // this warp's last read of the buffer
-        __syncwarp();
-        if (lane == 0) bulk::arrive(&empty[s]);
-      }
-      if (live) {
+    if (k + NS - 1 < K) {
+      load_row(ly, lz, (k + NS - 1) % NS);
+      advance(ly, lz);
+    }
+    if (live) {
+      if constexpr (COLLIDE) {
         const int cell = r * nx + x;
-        if constexpr (COLLIDE) {
-          float F[3];
-          body_force(p.force_a, p.force_b, p.force_tab, x, y, z, F);
-          float phi_prev = 0.f, phi_now = 0.f;
-          if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
-          constexpr bool AG = GradTerm<L, EQ>::kOn;
-          float gr[3];
-          if constexpr (AG) cell_field_gradient<L>(p, cell, x, y, z, gr);
-          collide<L, float, EQ, true>(f, p, F, phi_prev, phi_now, static_cast<NoHigh*>(nullptr), AG ? gr : nullptr);
-          if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
-          if constexpr (AG && EQ == LBM_NSE) {
-            if (p.grad_on) p.rho_out[cell] = phi_now;
-          }
+        float F[3];
+        body_force(p.force_a, p.force_b, p.force_tab, x, y, z, F);
+        float phi_prev = 0.f, phi_now = 0.f;
+        if constexpr (EQ == LBM_NCDE) phi_prev = phi[cell];
+        constexpr bool AG = GradTerm<L, EQ>::kOn;
+        float gr[3];
+        if constexpr (AG) cell_field_gradient<L>(p, cell, x, y, z, gr);
+        collide<L, float, EQ, true>(f, p, F, phi_prev, phi_now, static_cast<NoHigh*>(nullptr), AG ? gr : nullptr);
+        if constexpr (EQ == LBM_NCDE) phi[cell] = phi_now;
+        if constexpr (AG && EQ == LBM_NSE) {
+          if (p.grad_on) p.rho_out[cell] = phi_now;
         }
-        static_for<Q>([&](auto i) {
-          constexpr int I = decltype(i)::value;
-          k1_store(fout + size_t(I) * N + cell, RawCodec<ST>::enc(f[I]));
-        });
+      }
+      static_for<Q>([&](auto i) {
+        constexpr int I = decltype(i)::value;
+        st[I * PITCH + x] = RawCodec<ST>::enc(f[I]);
+      });
+    }
+    __syncthreads();  // the collided row is complete in the buffer
+    if (lane_chunk) {
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(st) + warp * ROWB + lane * 16;
+      uint8_t* dst = reinterpret_cast<uint8_t*>(fout) + (size_t(r) * nx + lane * 8) * sizeof(ST) + warp * pop_bytes;
+      for (int i = warp; i < Q; i += WARPS) {
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+        src += WARPS * ROWB;
+        dst += WARPS * pop_bytes;
       }
     }
+    advance(y, z);
   }
-  if (failed && lane == 0) atomicExch(rp.status, 1);
-  // copies still in flight into this CTA's shared memory land before it exits
-  if (warp == 0 && lane == 0)
-    for (int j = k; j < issued; ++j) tc::mbar_wait_bounded(&full[j % NS], uint32_t(j / NS) & 1u, rp.wait_limit);
+  if (failed && tid == 0) atomicExch(rp.status, 1);
+  bulk::cp_async_wait_all();  // no copy of this thread is still writing the CTA's shared memory
 }
 
 // Launch plan: the kernel applies to 16-bit storage with n_x a multiple of 8 (16-byte rows) and
-// at most the row pitch. Two CTAs per SM when two row buffers each fit, otherwise one; as many
+// at most the row pitch (256 cells). Two CTAs per SM when two row buffers each fit, otherwise one; as many
 // buffers (up to kRowMaxStages) as the shared memory of a CTA holds.
 template <int KIND>
 bool RowLaunch<KIND>::plan(const lbm_model* m, RowPlan* out) {
   using L = Lat<KIND>;
-  using S = RowShape<L>;
   if (m->store != LBM_F16_DEV && m->store != LBM_BF16_DEV) return false;
   const int64_t nx = m->n[0];
-  if (nx % 8 != 0 || nx > S::PITCH) return false;
+  if (nx % 8 != 0 || nx > kRowPitch) return false;
   int sms = 0, per_sm = 0, per_block = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device) != cudaSuccess ||
@@ -174,7 +183,7 @@ bool RowLaunch<KIND>::plan(const lbm_model* m, RowPlan* out) {
     cudaGetLastError();
     return false;
   }
-  const size_t stage_bytes = size_t(L::Q) * S::PITCH * 2;
+  const size_t stage_bytes = size_t(L::Q) * kRowPitch * 2;
   RowPlan p{};
   int ctas = 0, stages = 0;
   for (int c = 2; c >= 1 && ctas == 0; --c) {
@@ -190,12 +199,13 @@ bool RowLaunch<KIND>::plan(const lbm_model* m, RowPlan* out) {
   p.rp.nrows = int(nrows);
   p.rp.stages = stages;
   p.rp.stage_bytes = uint32_t(stage_bytes);
-  p.rp.row_bytes = uint32_t(nx * 2);
   p.rp.status = m->status;
   p.rp.wait_limit = 1u << 22;
+  const int64_t N = m->n[0] * m->n[1] * m->n[2];
   for (int i = 0; i < L::Q; ++i) {
     p.rp.ey[i] = int8_t(L::e(i).y);
     p.rp.ez[i] = int8_t(L::e(i).z);
+    p.rp.src_off[i] = 2 * (int64_t(i) * N - (int64_t(L::e(i).y) + int64_t(L::e(i).z) * m->n[1]) * nx);
   }
   p.grid = int(std::min<int64_t>(nrows, int64_t(sms) * ctas));
   p.smem = kRowBarBytes + size_t(stages) * stage_bytes;

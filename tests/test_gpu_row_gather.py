@@ -1,9 +1,9 @@
 """The row-staged gather of 16-bit deviation storage (lbm_model_set_gather "rows"): each CTA
-moves the source x-rows of its row's populations into shared memory with bulk copies and reads
-the pull sources (Eq. (2-2b)) there.
+moves the source x-rows of its row's populations into shared memory with bulk copies, reads the
+pull sources (Eq. (2-2b)) there, and sends the collided row back with bulk copies.
 
 Checks: propagation alone is bit-exact against the oracle's periodic shift (pure data movement,
-every wrap in x, y and z, row lengths from 8 cells to the 256 / 1024-cell pitch); a collide-stream
+every wrap in x, y and z, row lengths from 8 cells to the 256-cell pitch); a collide-stream
 step gives bitwise the populations of the per-thread gather (same collision code, same inputs),
 and one step stays within the 16-bit bounds of the FP64 oracle; the model extensions that read
 neighbour fields (the M2G density gradient, the NCDE cross diffusion) agree bitwise too.
@@ -18,9 +18,9 @@ from _harness import gpu_model, oracle_lattice, oracle_model, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-# n_x a multiple of 8 (16-byte rows); the smallest extents make every pull wrap, the largest n_x
-# fill the row buffers (256 cells in 3D, 1024 in 2D)
-ROW_GRIDS = {2: [(8, 3), (48, 13), (1024, 4)], 3: [(8, 2, 2), (24, 7, 5), (256, 3, 2)]}
+# n_x a multiple of 8 (16-byte rows); the smallest extents make every pull wrap, n_x = 256 fills
+# the row buffers
+ROW_GRIDS = {2: [(8, 3), (48, 13), (256, 5)], 3: [(8, 2, 2), (24, 7, 5), (256, 3, 2)]}
 LATTICES = ["rD2Q13", "rD2Q17", "rD2Q21", "rD2Q25", "rD2Q9", "rD3Q27", "rD3Q33", "rD3Q45", "rD3Q53"]
 UNIT = {"bf16_dev": 2.0 ** -8, "f16_dev": 2.0 ** -11}
 
