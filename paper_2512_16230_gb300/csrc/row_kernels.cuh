@@ -10,9 +10,9 @@
 // per population row, completing on the buffer's mbarrier); the periodic wraps in y and z are the
 // choice of source row, the wrap in x an index wrap: every thread reads its sources at
 // (x - e_ix) mod n_x. After a CTA barrier (every source read) the threads write their
-// post-collision populations back into the buffer at their own x, and after a second barrier the
-// warps store the Q rows with 16-byte stores. A ring of row buffers keeps the following rows in
-// flight while the current one is collided. The collision is the code of k_step on the same
+// post-collision populations back into the buffer at their own x; after the next row's barrier
+// the warps store the Q rows with 16-byte stores. A ring of row buffers keeps the following rows
+// in flight while the current one is collided. The collision is the code of k_step on the same
 // inputs, so the results are bitwise the same.
 //
 // The wait for a row's copies is bounded: on timeout (decided for the whole CTA at the next
@@ -26,7 +26,32 @@
 
 namespace lbm {
 
-template <class L, class ST, int EQ, bool COLLIDE>
+// 16-bit shared-memory accesses at a register address plus a compile-time byte offset, and the
+// conversions of one value between the storage format and FP32.
+template <int OFF>
+__device__ __forceinline__ uint16_t lds16(uint32_t addr) {
+  uint16_t v;
+  asm volatile("ld.shared.b16 %0, [%1+%2];" : "=h"(v) : "r"(addr), "n"(OFF));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sts16(uint32_t addr, uint16_t v) {
+  asm volatile("st.shared.b16 [%0+%1], %2;" ::"r"(addr), "n"(OFF), "h"(v) : "memory");
+}
+template <class ST>
+__device__ __forceinline__ float dec16(uint16_t b) {
+  if constexpr (std::is_same<ST, __half>::value) return __half2float(__ushort_as_half(b));
+  else return __uint_as_float(uint32_t(b) << 16);
+}
+template <class ST>
+__device__ __forceinline__ uint16_t enc16(float v) {
+  uint16_t b;
+  if constexpr (std::is_same<ST, __half>::value) asm("cvt.rn.f16.f32 %0, %1;" : "=h"(b) : "f"(v));
+  else asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(b) : "f"(v));
+  return b;
+}
+
+template <class L, class ST, int EQ, bool COLLIDE, bool FULL>
 __global__ void __launch_bounds__(kRowThreads, 2)
     k_step_rows(const StepParams<float> p, const RowParams rp, const ST* __restrict__ fin, ST* __restrict__ fout,
                 float* __restrict__ phi) {
@@ -46,8 +71,9 @@ __global__ void __launch_bounds__(kRowThreads, 2)
   const size_t N = size_t(p.ncells);
   const size_t pop_bytes = N * sizeof(ST);
   const int x = tid;
-  const bool live = x < nx;
-  const bool lane_chunk = lane * 8 < nx;  // this lane's 16-byte chunk (8 cells) of a row exists
+  // FULL: n_x equals the pitch, every thread has a cell and every lane a 16-byte chunk of a row
+  const bool live = FULL || x < nx;
+  const bool lane_chunk = FULL || lane * 8 < nx;
   // rows of this CTA are r = blockIdx.x + k G: (y, z) advance by (G mod n_y, G div n_y) with a carry
   const int gy = G % ny, gz = G / ny;
   auto advance = [&](int& y, int& z) {
@@ -73,7 +99,10 @@ __global__ void __launch_bounds__(kRowThreads, 2)
       const uint32_t dst = rows_s + uint32_t(s) * rp.stage_bytes + uint32_t(lane * 16);
       const bool inner = y >= RM && y < ny - RM && (L::D == 2 || (z >= RM && z < nz - RM));
       if (inner) {
-        for (int i = warp; i < Q; i += WARPS) bulk::cp_async16(dst + uint32_t(i) * ROWB, base + rp.src_off[i]);
+        static_for<(Q + WARPS - 1) / WARPS>([&](auto m) {
+          const int i = warp + WARPS * decltype(m)::value;
+          if (i < Q) bulk::cp_async16(dst + uint32_t(i) * ROWB, base + rp.src_off[i]);
+        });
       } else {
         const uint8_t* b0 = reinterpret_cast<const uint8_t*>(fin) + size_t(lane * 8) * sizeof(ST);
         for (int i = warp; i < Q; i += WARPS) {
@@ -96,38 +125,57 @@ __global__ void __launch_bounds__(kRowThreads, 2)
 
   int ly = int(blockIdx.x) % ny, lz = int(blockIdx.x) / ny;  // next row to load
   int y = ly, z = lz;                                          // row being collided
-  for (int j = 0; j < K && j < NS - 1; ++j) {
+  // one warp-wide 16-byte store per population row of buffer sb to row (sy, sz) of the output
+  auto store_row = [&](int sy, int sz, int sb) {
+    if (lane_chunk) {
+      const size_t sr = size_t(sz) * ny + sy;
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(rows + size_t(sb) * stage_elems) + warp * ROWB + lane * 16;
+      uint8_t* dst = reinterpret_cast<uint8_t*>(fout) + (sr * nx + lane * 8) * sizeof(ST) + warp * pop_bytes;
+      static_for<(Q + WARPS - 1) / WARPS>([&](auto m) {
+        constexpr int M = decltype(m)::value;
+        if (warp + WARPS * M < Q)
+          *reinterpret_cast<uint4*>(dst + M * WARPS * pop_bytes) = *reinterpret_cast<const uint4*>(src + M * WARPS * ROWB);
+      });
+    }
+  };
+
+  // Ring of NS buffers: while row k is collided (in its buffer), row k - 1 is stored from its
+  // buffer and rows k + 1 .. k + NS - 2 are in flight; one CTA barrier per row separates the reads
+  // of row k from the in-place writes, and the writes of row k - 1 from its store.
+  for (int j = 0; j < K && j < NS - 2; ++j) {
     load_row(ly, lz, j);
     advance(ly, lz);
   }
   bool failed = false;
+  int py = y, pz = z;  // row k - 1
   for (int k = 0; k < K; ++k) {
     const int s = k % NS;
     const bool landed = tc::mbar_wait_bounded(&full[s], uint32_t(k / NS) & 1u, rp.wait_limit);
     const int r = z * ny + y;
-    ST* st = rows + size_t(s) * stage_elems;
+    const uint32_t st_s = rows_s + uint32_t(s) * rp.stage_bytes;
     float f[Q];
     if (live && landed) {
-      int xo[2 * RM + 1];  // (x - sh) mod n_x for the x-shifts sh = -RM..RM
+      uint32_t xa[2 * RM + 1];  // address of (x - sh) mod n_x in row 0 of the buffer, sh = -RM..RM
 #pragma unroll
       for (int sh = -RM; sh <= RM; ++sh) {
         int v = x - sh;
         if (sh > 0) v += v < 0 ? nx : 0;
         if (sh < 0) v -= v >= nx ? nx : 0;
-        xo[sh + RM] = v;
+        xa[sh + RM] = st_s + uint32_t(v) * uint32_t(sizeof(ST));
       }
       static_for<Q>([&](auto i) {
         constexpr int I = decltype(i)::value;
-        f[I] = RawCodec<ST>::dec(st[I * PITCH + xo[RM + L::e(I).x]]);
+        f[I] = dec16<ST>(lds16<I * int(ROWB)>(xa[RM + L::e(I).x]));
       });
     }
-    // every source of the row read, and row k - 1 stored: its buffer takes row k + NS - 1
+    // every source of row k read, row k - 1 collided into its buffer, row k - 2 stored
     if (__syncthreads_or(!landed)) {
       failed = true;
       break;
     }
-    if (k + NS - 1 < K) {
-      load_row(ly, lz, (k + NS - 1) % NS);
+    if (k >= 1) store_row(py, pz, (k - 1) % NS);
+    if (k + NS - 2 < K) {  // into the buffer of row k - 2
+      load_row(ly, lz, (k + NS - 2) % NS);
       advance(ly, lz);
     }
     if (live) {
@@ -146,30 +194,27 @@ __global__ void __launch_bounds__(kRowThreads, 2)
           if (p.grad_on) p.rho_out[cell] = phi_now;
         }
       }
+      const uint32_t xs = st_s + uint32_t(x) * uint32_t(sizeof(ST));
       static_for<Q>([&](auto i) {
         constexpr int I = decltype(i)::value;
-        st[I * PITCH + x] = RawCodec<ST>::enc(f[I]);
+        sts16<I * int(ROWB)>(xs, enc16<ST>(f[I]));
       });
     }
-    __syncthreads();  // the collided row is complete in the buffer
-    if (lane_chunk) {
-      const uint8_t* src = reinterpret_cast<const uint8_t*>(st) + warp * ROWB + lane * 16;
-      uint8_t* dst = reinterpret_cast<uint8_t*>(fout) + (size_t(r) * nx + lane * 8) * sizeof(ST) + warp * pop_bytes;
-      for (int i = warp; i < Q; i += WARPS) {
-        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
-        src += WARPS * ROWB;
-        dst += WARPS * pop_bytes;
-      }
-    }
+    py = y;
+    pz = z;
     advance(y, z);
+  }
+  if (!failed && K > 0) {
+    __syncthreads();  // the last row is complete in its buffer
+    store_row(py, pz, (K - 1) % NS);
   }
   if (failed && tid == 0) atomicExch(rp.status, 1);
   bulk::cp_async_wait_all();  // no copy of this thread is still writing the CTA's shared memory
 }
 
 // Launch plan: the kernel applies to 16-bit storage with n_x a multiple of 8 (16-byte rows) and
-// at most the row pitch (256 cells). Two CTAs per SM when two row buffers each fit, otherwise one; as many
-// buffers (up to kRowMaxStages) as the shared memory of a CTA holds.
+// at most the row pitch (256 cells). Two CTAs per SM when three row buffers each fit, otherwise
+// one; as many buffers (up to kRowMaxStages) as the shared memory of a CTA holds.
 template <int KIND>
 bool RowLaunch<KIND>::plan(const lbm_model* m, RowPlan* out) {
   using L = Lat<KIND>;
@@ -189,7 +234,7 @@ bool RowLaunch<KIND>::plan(const lbm_model* m, RowPlan* out) {
   for (int c = 2; c >= 1 && ctas == 0; --c) {
     const size_t avail = std::min<size_t>(size_t(per_block), size_t(per_sm) / c - 1024);  // 1 KB reserved per CTA
     const int ns = int(std::min<size_t>(kRowMaxStages, (avail - kRowBarBytes) / stage_bytes));
-    if (ns >= 2) {
+    if (ns >= 3) {  // the row being collided, the row being stored, at least one in flight
       ctas = c;
       stages = ns;
     }
@@ -214,11 +259,16 @@ bool RowLaunch<KIND>::plan(const lbm_model* m, RowPlan* out) {
 }
 
 // The kernel of a model: storage type, equation, collision on / off (stream only).
+template <class L, class ST, bool FULL, class F>
+lbm_status row_kernel_full(int eq, bool collide, F&& fn) {
+  if (!collide) return fn(k_step_rows<L, ST, LBM_NSE, false, FULL>);
+  if (eq == LBM_NSE) return fn(k_step_rows<L, ST, LBM_NSE, true, FULL>);
+  return fn(k_step_rows<L, ST, LBM_NCDE, true, FULL>);
+}
 template <class L, class ST, class F>
-lbm_status row_kernel(int eq, bool collide, F&& fn) {
-  if (!collide) return fn(k_step_rows<L, ST, LBM_NSE, false>);
-  if (eq == LBM_NSE) return fn(k_step_rows<L, ST, LBM_NSE, true>);
-  return fn(k_step_rows<L, ST, LBM_NCDE, true>);
+lbm_status row_kernel(int eq, bool collide, bool full, F&& fn) {
+  if (full) return row_kernel_full<L, ST, true>(eq, collide, fn);
+  return row_kernel_full<L, ST, false>(eq, collide, fn);
 }
 
 template <int KIND>
@@ -231,8 +281,9 @@ lbm_status RowLaunch<KIND>::configure(const lbm_model* m, const RowPlan& plan, b
       return cuda_error(cudaGetLastError(), "row-staged kernel attributes");
     return LBM_OK;
   };
-  if (m->store == LBM_F16_DEV) return row_kernel<L, __half>(m->eq, collide, set);
-  return row_kernel<L, __nv_bfloat16>(m->eq, collide, set);
+  const bool full = m->n[0] == kRowPitch;
+  if (m->store == LBM_F16_DEV) return row_kernel<L, __half>(m->eq, collide, full, set);
+  return row_kernel<L, __nv_bfloat16>(m->eq, collide, full, set);
 }
 
 template <int KIND>
@@ -246,9 +297,11 @@ lbm_status RowLaunch<KIND>::launch(const lbm_model* m, const RowPlan& plan, cons
     cudaError_t err = cudaGetLastError();
     return err == cudaSuccess ? LBM_OK : cuda_error(err, "row-staged collide-stream launch");
   };
+  const bool full = m->n[0] == kRowPitch;
   if (m->store == LBM_F16_DEV)
-    return row_kernel<L, __half>(m->eq, collide, [&](auto kernel) { return go(kernel, __half()); });
-  return row_kernel<L, __nv_bfloat16>(m->eq, collide, [&](auto kernel) { return go(kernel, __nv_bfloat16()); });
+    return row_kernel<L, __half>(m->eq, collide, full, [&](auto kernel) { return go(kernel, __half()); });
+  return row_kernel<L, __nv_bfloat16>(m->eq, collide, full,
+                                      [&](auto kernel) { return go(kernel, __nv_bfloat16()); });
 }
 
 }  // namespace lbm
