@@ -24,9 +24,40 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from . import inputs as I
 from . import workloads as W
 
-STORE_OF = {"f32": "f32", "16bit": "f16_dev"}
+
+# The flow classes of the serving mix, and for each the longest run that FP16-deviation storage
+# serves within the 1e-3 relative L2 bound on u (or phi) against the FP64 oracle, on the smallest
+# and on the largest served grids (0: never). The rounding error of 16-bit storage grows with the
+# run (a random walk of the rounded momentum in the vortices) and with the grid (on fine grids the
+# per-step change of a population -- the forcing of the Kolmogorov flow, the diffusion of the hill
+# -- falls below a unit of the stored deviation and is rounded away), so only short vortex runs
+# qualify; every other request is served in FP32. The serving-precision tests check each threshold.
+SERVING_CLASSES = ([(flow, lat) for flow in ("tgv2d", "ncde") for lat in I.SERVING_2D]
+                   + [("kolmogorov", lat) for lat in I.SERVING_3D])
+F16_MAX_STEPS = {
+    ("tgv2d", "rD2Q17"): 200, ("tgv2d", "rD2Q21"): 200, ("tgv2d", "rD2Q25"): 200,
+    ("ncde", "rD2Q17"): 0, ("ncde", "rD2Q21"): 0, ("ncde", "rD2Q25"): 0,
+    ("kolmogorov", "rD3Q33"): 0, ("kolmogorov", "rD3Q45"): 0, ("kolmogorov", "rD3Q53-cubic"): 0,
+}
+
+
+def served_in_f16(flow, lattice, steps):
+    return steps <= F16_MAX_STEPS.get((flow, lattice), 0)
+
+
+def store_for(req, policy):
+    """Storage of a request under a serving policy: "as_requested" (FP32 requests in FP32, 16-bit
+    ones as FP16 deviations), "f16_dev" (every request as FP16 deviations: the reduced-precision
+    path) -- in both, FP16 only where the class and run length keep the error within the bound
+    (F16_MAX_STEPS), FP32 otherwise -- or a storage name applied to every request."""
+    if policy in ("as_requested", "f16_dev"):
+        if policy == "as_requested" and req["store"] == "f32":
+            return "f32"
+        return "f16_dev" if served_in_f16(req["flow"], req["lattice"], req["steps"]) else "f32"
+    return policy
 
 
 @dataclass
@@ -149,10 +180,8 @@ class Running:
 
 def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=64, clock=time.perf_counter,
                   store_policy="as_requested"):
-    """Continuous batching over ``requests`` (sorted by arrival). ``store_policy``: "as_requested"
-    (FP32 requests in FP32, 16-bit ones as FP16 deviations) or a storage name applied to every
-    request (e.g. "f16_dev": the reduced-precision serving path). Returns the records and the
-    elapsed wall time."""
+    """Continuous batching over ``requests`` (sorted by arrival); ``store_policy`` as in
+    ``store_for``. Returns the records and the elapsed wall time."""
     pending = collections.deque(sorted(requests, key=lambda r: r["arrival"]))
     running = []
     records = []
@@ -163,7 +192,7 @@ def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=6
         now = clock() - t0
         while pending and pending[0]["arrival"] <= now and len(running) < max_resident:
             req = pending[0]
-            store = STORE_OF[req["store"]] if store_policy == "as_requested" else store_policy
+            store = store_for(req, store_policy)
             if used + engine.nbytes(req, store) > budget_bytes and running:
                 break          # does not fit yet: admit after a retirement frees memory
             pending.popleft()

@@ -65,3 +65,19 @@ def test_sequential_loop_and_summary():
     assert s["solves_per_s"] == 12 / elapsed
     cells = sum(np.prod(r["grid"]) * r["steps"] for r in reqs)
     assert abs(s["mlups"] - cells / elapsed / 1e6) < 1e-9 * s["mlups"]
+
+
+def test_storage_policy():
+    """The serving policies: FP32 requests stay FP32 under "as_requested"; under both policies a
+    16-bit request is stored as FP16 deviations only while its run is no longer than its class's
+    FP16 threshold (F16_MAX_STEPS), FP32 otherwise; any other policy is a storage name."""
+    assert len(S.SERVING_CLASSES) == 9 and set(S.F16_MAX_STEPS) == set(S.SERVING_CLASSES)
+    for flow, lat in S.SERVING_CLASSES:
+        top = S.F16_MAX_STEPS[flow, lat]
+        for steps in (max(top, 1), top + 1):
+            for store in ("f32", "16bit"):
+                req = dict(flow=flow, lattice=lat, store=store, steps=steps)
+                f16 = "f16_dev" if steps <= top else "f32"
+                assert S.store_for(req, "as_requested") == ("f32" if store == "f32" else f16)
+                assert S.store_for(req, "f16_dev") == f16
+                assert S.store_for(req, "bf16_dev") == "bf16_dev"
