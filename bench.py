@@ -507,12 +507,17 @@ def bench_ours(args):
             "hbm_frac": 2 * Q * 2 * cells / (high16_ms / 1e3) / 1e9 / peak}
     # the same workload with 16-bit deviation storage (the reduced-precision configuration): FP16
     # and BF16 on the CUDA cores, FP16 with the contractions on tcgen05
-    for key, store, tc, kern in (("f16_deviations", "f16_dev", 0, "k_step<rD3Q53, f16_dev, NSE>"),
-                                 ("bf16_deviations", "bf16_dev", 0, "k_step<rD3Q53, bf16_dev, NSE>"),
-                                 ("f16_deviations_tensor_cores", "f16_dev", 1, "k_step_tc<rD3Q53, f16_dev, NSE>")):
+    for key, store, tc, gather, kern in (
+            ("f16_deviations", "f16_dev", 0, "auto",
+             "k_step_rows<rD3Q53, f16_dev, NSE> (source x-rows staged in shared memory by cp.async)"),
+            ("bf16_deviations", "bf16_dev", 0, "auto", "k_step_rows<rD3Q53, bf16_dev, NSE>"),
+            ("f16_deviations_thread_gather", "f16_dev", 0, "threads",
+             "k_step<rD3Q53, f16_dev, NSE> (per-thread gather from global memory)"),
+            ("f16_deviations_tensor_cores", "f16_dev", 1, "auto", "k_step_tc<rD3Q53, f16_dev, NSE>")):
         mr = lbm.Model(lat, "nse", wl.n, store=store, stream=stream.cuda_stream)
         mr.set_relaxation(wl.s, wl.s_high)
         mr.set_tensor_cores(tc)
+        mr.set_gather(gather)
         mr.init_fields(rho_d, u_d)
         r_ms = time_steps(mr)
         mr.close()
@@ -533,11 +538,12 @@ def bench_ours(args):
                 other["taylor_green_rD2Q25_64x48_f64"]["oracle"] = oc["taylor_green_rD2Q25_64x48_f64"]
                 other["ncde_hill_rD2Q13_1024x768_f64"]["oracle"] = oc["ncde_hill_rD2Q13_1024x768"]
             line["other_configs"] = other
-    if args.serving_requests > 0:
-        serving = run_serving(args.serving_requests)
-        if rank == 0:
-            line["serving"] = serving
+    if args.serving_requests > 0 and ws == 1:   # the serving leg (config 5) runs at N = 1 only
+        line["serving"] = run_serving(args.serving_requests)
     if rank == 0:
+        for key in ("extensions", "other_configs", "variants", "serving"):   # the long extras last
+            if key in line:
+                line[key] = line.pop(key)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -641,28 +647,92 @@ def run_other_configs(lbm, W_stream, barrier):
     return out
 
 
-def run_serving(n_requests, rate_per_s=20.0, seed=0):
-    """Config 5 on a prefix of the seeded request stream: continuous batching (16-bit requests in
-    FP16 deviation storage, tiles from the autotuner) against the plain FP32 one-solve-at-a-time
-    path, same requests and arrival times."""
+SERVING_PRECISION_GRID = {"tgv2d": (256, 192), "ncde": (256, 192), "kolmogorov": (64, 64, 64)}
+SERVING_PRECISION_STEPS = 1000
+
+
+def serving_precision(lbm, S):
+    """Per served class, the relative L2 error of u (or phi) after 1000 steps in FP32 and in FP16
+    deviation storage against the library's FP64 path (pinned to the FP64 oracle at 1e-12 by the
+    parity tests), on a mid-size grid of the class, with the class's FP16 threshold."""
+    import numpy as np
+    import torch
+    from paper_2512_16230_gb300 import workloads as W
+    out = {}
+    for flow, lat in S.SERVING_CLASSES:
+        req = dict(rid=0, flow=flow, lattice=lat, grid=SERVING_PRECISION_GRID[flow], steps=SERVING_PRECISION_STEPS,
+                   seed=7, store="16bit")
+        fields = {}
+        for store in ("f64", "f32", "f16_dev"):
+            wl = W.serving_workload(req, store)
+            spec = wl.lattice
+            m = lbm.Model(lbm.Lattice(spec.kind, spec.c, spec.cs2, spec.free_w), wl.eq, wl.n, store=store)
+            m.set_relaxation(wl.s, wl.s_high)
+            if wl.force is not None:
+                m.set_force(*wl.force)
+            if wl.u_const is not None:
+                m.set_ncde(wl.u_const, wl.nonlin)
+            rho, u = wl.fields()
+            m.init_fields(rho, None if u is None else np.ascontiguousarray(u))
+            m.step(wl.steps)
+            r, v = m.read_fields()
+            fields[store] = v if wl.eq == "nse" else r
+            m.close()
+        torch.cuda.empty_cache()
+        ref = fields["f64"]
+
+        def err(a):
+            return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+        out[f"{flow}|{lat}"] = {"grid": list(req["grid"]), "steps": SERVING_PRECISION_STEPS,
+                                "quantity": "u" if flow != "ncde" else "phi",
+                                "f32": err(fields["f32"]), "f16_dev": err(fields["f16_dev"]),
+                                "f16_max_steps": S.F16_MAX_STEPS[flow, lat]}
+    return out
+
+
+def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300):
+    """Config 5: the seeded request stream at its stated size, served by continuous batching
+    (policy "f16_dev": FP16 deviations only where the class and run length keep the error within
+    1e-3, FP32 otherwise; tiles from the autotuner) and by the plain FP32 one-solve-at-a-time path,
+    same requests and arrival times (20 arrivals/s, more than either path serves: solves/s is the
+    capacity). Then both paths on a shorter stream arriving at 0.8 x the smaller capacity, where
+    p50/p99 measure service rather than queueing. Also the per-class errors."""
     from paper_2512_16230_gb300 import autotune
     from paper_2512_16230_gb300 import inputs as I
+    from paper_2512_16230_gb300 import lbm
     from paper_2512_16230_gb300 import serve as S
+
+    def both(reqs, tiles):
+        eng = S.GpuEngine(tiles=tiles)
+        rec_b, t_b = S.serve_batched(reqs, eng, budget_bytes=150e9, max_resident=512, tick=64,
+                                     store_policy="f16_dev")
+        launches = eng.batch.counters()["launches"]
+        eng.close()
+        b = dict(S.summarize(rec_b, t_b), batched_launches=launches, hbm_budget_gb=150,
+                 peak_resident_gb=S.serve_batched.peak_bytes / 1e9,
+                 f16_requests=sum(r.store == "f16_dev" for r in rec_b))
+        seq = S.GpuEngine()
+        rec_s, t_s = S.serve_sequential(reqs, seq, store="f32")
+        seq.close()
+        return b, S.summarize(rec_s, t_s)
+
     reqs = I.serving_requests(n_requests, seed=seed, rate_per_s=rate_per_s)
     tiles = autotune.autotune()
-    eng = S.GpuEngine(tiles=tiles)
-    rec_b, t_b = S.serve_batched(reqs, eng, budget_bytes=150e9, max_resident=512, tick=64, store_policy="f16_dev")
-    launches_b = eng.batch.counters()["launches"]
-    eng.batch.close()
-    rec_s, t_s = S.serve_sequential(reqs, S.GpuEngine(), store="f32")
+    b, q = both(reqs, tiles)
+    rate2 = 0.8 * min(b["solves_per_s"], q["solves_per_s"])
+    reqs2 = I.serving_requests(sustained_requests, seed=seed + 1, rate_per_s=rate2)
+    b2, q2 = both(reqs2, tiles)
     return {
         "requests": n_requests, "arrival_rate_per_s": rate_per_s, "seed": seed,
         "mix": "2D rD2Q17/21/25 Taylor-Green + NCDE (32..1024 x 32..768), 3D rD3Q33/45/53 Kolmogorov "
                "(32^3..160^3), 200..5000 steps, Poisson arrivals",
-        "batched_f16": dict(S.summarize(rec_b, t_b), storage="FP16 deviations (u error <= 5.2e-4 vs FP64 oracle)",
-                            batched_launches=launches_b, hbm_budget_gb=150,
-                            peak_resident_gb=S.serve_batched.peak_bytes / 1e9),
-        "sequential_fp32": S.summarize(rec_s, t_s),
+        "batched": dict(b, storage="policy f16_dev: FP16 deviations where the class and run length keep the "
+                                   "u (phi) error <= 1e-3, FP32 otherwise"),
+        "sequential_fp32": q,
+        "speedup_solves_per_s": b["solves_per_s"] / q["solves_per_s"],
+        "sustained": {"requests": sustained_requests, "seed": seed + 1, "arrival_rate_per_s": rate2,
+                      "batched": b2, "sequential_fp32": q2},
+        "errors_vs_fp64": serving_precision(lbm, S),
         "tiles": {"|".join(k): v for k, v in tiles.items()},
     }
 
@@ -674,7 +744,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=160,
+    ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests of the seeded serving mix (config 5) served after the step benchmark; 0 skips")
     ap.add_argument("--no-other-configs", action="store_true",
                     help="skip the full-size runs of the smaller configurations (profiling commands)")

@@ -373,7 +373,9 @@ lbm_status lbm_batch_create(void* stream, int max_solves, lbm_batch** out);
  * cells, on the CUDA cores). FP64 storage is not batched (LBM_ERR_NOT_IMPLEMENTED). */
 lbm_status lbm_batch_add(lbm_batch* b, lbm_model* m);
 
-/* Remove a model (synchronizes the batch's stream; the model returns to its own stream). */
+/* Remove a model. It returns to its own stream, which is made to wait (on the device, through an
+ * event) for the batch's steps queued so far: no host synchronization, and any later call on the
+ * model sees its state after those steps. The next lbm_batch_step rebuilds the work-lists. */
 lbm_status lbm_batch_remove(lbm_batch* b, lbm_model* m);
 
 /* Tile size (cells per thread block) of the batched kernel for one group type: 64, 128 or 256.

@@ -50,6 +50,9 @@ struct lbm_batch {
   bool dirty = true;
   bool stable = false;  // no change since the last step call: capture a graph
   cudaGraphExec_t graph = nullptr;
+  // replaced graphs whose launches may still run, each with an event recorded after them on the
+  // batch stream: destroyed once the event has completed (no host synchronisation)
+  std::vector<std::pair<cudaGraphExec_t, cudaEvent_t>> old_graphs;
   // work-list buffers by group key, kept across rebuilds and grown geometrically
   std::map<std::tuple<const lbm_lattice*, int, int, int>, DeviceBuffers> buffers;
   int64_t steps = 0, launches = 0, rebuilds = 0, captures = 0;
@@ -79,9 +82,34 @@ lbm_status dispatch_batch_kind(int kind, F&& f) {
   return set_error(LBM_ERR_ARG, "unknown lattice kind");
 }
 
+// Destroy the replaced graphs whose launches have completed (all of them when `all`, after the
+// caller has synchronised the batch stream).
+void reap_graphs(lbm_batch* b, bool all) {
+  std::vector<std::pair<cudaGraphExec_t, cudaEvent_t>> keep;
+  for (auto& ge : b->old_graphs) {
+    if (all || cudaEventQuery(ge.second) == cudaSuccess) {
+      cudaGraphExecDestroy(ge.first);
+      cudaEventDestroy(ge.second);
+    } else {
+      keep.push_back(ge);
+    }
+  }
+  cudaGetLastError();  // clear the not-ready status of the queries
+  b->old_graphs.swap(keep);
+}
+
 void drop_graph(lbm_batch* b) {
+  reap_graphs(b, false);
   if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventRecord(ev, b->stream) == cudaSuccess) {
+      b->old_graphs.emplace_back(b->graph, ev);
+    } else {  // no event: wait for the launches before destroying the graph
+      if (ev) cudaEventDestroy(ev);
+      cudaStreamSynchronize(b->stream);
+      cudaGraphExecDestroy(b->graph);
+    }
     b->graph = nullptr;
   }
 }
@@ -220,9 +248,11 @@ lbm_status rebuild(lbm_batch* b) {
     }
     gh.g.nsolves = int(gh.members.size());
     gh.g.ntiles = int(tiles.size());
+    // The previous work-list may still be read by launches queued on the batch stream: the new one
+    // is uploaded on that stream, so it lands after them (a buffer that must grow is freed by
+    // cudaFree, which waits for the device); the host vectors are staged by the copy call itself.
     DeviceBuffers& buf = b->buffers[std::make_tuple(gh.g.lat, gh.g.store, gh.g.eq, gh.g.high)];
-    cudaError_t err = cudaStreamSynchronize(b->stream);   // the previous work-list may still be read
-    if (err == cudaSuccess) err = ensure(&buf.desc, &buf.desc_cap, gh.desc.size() * sizeof(SolveDesc<float>));
+    cudaError_t err = ensure(&buf.desc, &buf.desc_cap, gh.desc.size() * sizeof(SolveDesc<float>));
     if (err == cudaSuccess) err = ensure(&buf.tiles, &buf.tiles_cap, tiles.size() * sizeof(Tile));
     if (err == cudaSuccess && gh.g.high)
       err = ensure(&buf.high, &buf.high_cap, gh.high.size() * sizeof(HighParams<float>));
@@ -235,7 +265,6 @@ lbm_status rebuild(lbm_batch* b) {
     if (err == cudaSuccess && gh.g.high)
       err = cudaMemcpyAsync(gh.g.d_high, gh.high.data(), gh.high.size() * sizeof(HighParams<float>),
                             cudaMemcpyHostToDevice, b->stream);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(b->stream);
     if (err != cudaSuccess) return cuda_error(err, "batch work-list allocation");
     lbm_status st = upload_desc(b, gh);
     if (st != LBM_OK) return st;
@@ -341,8 +370,14 @@ lbm_status lbm_batch_remove(lbm_batch* b, lbm_model* m) {
   auto it = std::find(b->members.begin(), b->members.end(), m);
   if (it == b->members.end() || m->batch != b) return set_error(LBM_ERR_ARG, "model is not in this batch");
   DeviceScope scope(b->device);
-  cudaError_t err = cudaStreamSynchronize(b->stream);
-  if (err != cudaSuccess) return cuda_error(err, "batch stream");
+  // hand the model back to its own stream after the batch's queued steps, without waiting on the
+  // host: the model's stream waits for an event recorded on the batch stream
+  cudaEvent_t ev = nullptr;
+  cudaError_t err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (err == cudaSuccess) err = cudaEventRecord(ev, b->stream);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(m->own_stream, ev, 0);
+  if (ev) cudaEventDestroy(ev);
+  if (err != cudaSuccess) return cuda_error(err, "batch stream hand-over");
   b->members.erase(it);
   m->stream = m->own_stream;
   m->batch = nullptr;
@@ -442,6 +477,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
     m->batch = nullptr;
   }
   free_groups(b);
+  reap_graphs(b, true);
   free_buffers(b);
   if (b->owns_stream) cudaStreamDestroy(b->stream);
   delete b;

@@ -6,27 +6,31 @@ Two request loops over the same seeded request stream (``inputs.serving_requests
   they have arrived and their device workspace fits the HBM budget and a slot is free; every
   admitted solve stays resident and joins one ``lbm.Batch``, which advances all resident solves
   together (one persistent launch per group of solves per step, steps replayed from a CUDA graph).
-  The loop advances the batch by ticks of at most ``tick`` steps, never past the earliest
-  completion, retires finished solves (their fields are read back to host memory), frees their
-  memory, and admits new arrivals between ticks. 16-bit requests are stored as FP16 deviations.
+  The loop enqueues the batch in ticks of at most ``tick`` steps, never past the earliest
+  completion, and keeps one tick queued ahead of the one running, so that the host work between
+  ticks overlaps the device: the initial fields of arrived requests are generated on worker
+  threads, a new solve is initialised on its own stream while the batch runs, and a finished
+  solve leaves the batch without a host wait -- its fields are computed on the device and copied
+  into pinned host memory behind an event, and its memory is released once that event is done.
 * ``serve_sequential`` -- the plain path: one solve at a time in arrival order, FP32, each step one
-  launch of the single-solve kernel.
+  launch of the single-solve kernel, fields read back synchronously.
 
-Both record arrival, admission and completion times per request; ``summarize`` turns them into
-solves/s, latency percentiles and cell updates per second. The host logic (admission, ticks,
-retirement, accounting) is independent of the GPU: ``FakeEngine`` drives it on the CPU in tests.
+Both record arrival, admission and completion times per request (a batched completion is the
+device time of its read-back event, on the host clock); ``summarize`` turns them into solves/s,
+latency percentiles and cell updates per second. The host logic (admission, ticks, retirement,
+accounting) is independent of the GPU: ``FakeEngine`` drives it on the CPU in tests.
 """
 from __future__ import annotations
 
 import collections
+import concurrent.futures as cf
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
 from . import inputs as I
 from . import workloads as W
-
 
 # The flow classes of the serving mix, and for each the longest run that FP16-deviation storage
 # serves within the 1e-3 relative L2 bound on u (or phi) against the FP64 oracle, on the smallest
@@ -74,15 +78,26 @@ class Record:
 
 
 class GpuEngine:
-    """Creates, batches and retires models through the CUDA library."""
+    """Creates, batches and retires models through the CUDA library.
 
-    def __init__(self, max_solves=4096, tiles=None, keep_results=False):
+    Protocol of the batched loop: ``prepare`` (host fields of an arrived request, on a worker
+    thread), ``create`` + ``add`` (initialise on the model's own stream, join the batch), ``step``
+    (enqueue a tick, return its event), ``wait`` (a tick's event), ``finish`` (leave the batch and
+    start the read-back, return a handle), ``done`` / ``finish_time`` / ``release`` (poll the
+    read-back, its completion time on the host clock, free the model)."""
+
+    def __init__(self, max_solves=4096, tiles=None, keep_results=False, workers=4):
+        import torch
         from . import lbm
+        self.torch = torch
         self.lbm = lbm
         self.batch = lbm.Batch(max_solves)
+        self.stream = torch.cuda.ExternalStream(self.batch.stream)
         self._lattices = {}
         self.keep_results = keep_results
         self.results = {}
+        self.pool = cf.ThreadPoolExecutor(max_workers=workers)
+        self.ref = None
         for key, cells in (tiles or {}).items():
             self.batch.set_tile(*key, cells)
 
@@ -96,7 +111,23 @@ class GpuEngine:
         wl = W.serving_workload(req, store)
         return self.lbm.workspace_bytes(self.lattice(req["lattice"]), wl.eq, wl.n, store)
 
-    def create(self, req, store, stream=None):
+    def start_clock(self, t0):
+        """A device timestamp paired with the host clock value t0 (completion times of read-backs
+        are measured from it)."""
+        ev = self.torch.cuda.Event(enable_timing=True)
+        ev.record(self.torch.cuda.current_stream())
+        ev.synchronize()
+        self.ref = (ev, t0)
+
+    @staticmethod
+    def _fields(req, store):
+        rho, u = W.serving_workload(req, store).fields()
+        return rho, None if u is None else np.ascontiguousarray(u)
+
+    def prepare(self, req, store):
+        return self.pool.submit(self._fields, req, store)
+
+    def create(self, req, store, prepared=None, stream=None):
         wl = W.serving_workload(req, store)
         lat = self.lattice(req["lattice"])
         m = self.lbm.Model(lat, wl.eq, wl.n, store=store, stream=stream)
@@ -106,7 +137,7 @@ class GpuEngine:
             m.set_force(*wl.force)
         if wl.u_const is not None:
             m.set_ncde(wl.u_const, wl.nonlin)
-        rho, u = wl.fields()
+        rho, u = prepared.result() if prepared is not None else self._fields(req, store)
         m.init_fields(rho, u)
         return m, m.workspace_bytes, lat.Q
 
@@ -115,13 +146,42 @@ class GpuEngine:
 
     def step(self, k):
         self.batch.step(k)
-        self.batch.synchronize()
+        ev = self.torch.cuda.Event()
+        ev.record(self.stream)
+        return ev
+
+    def wait(self, token):
+        token.synchronize()
 
     def finish(self, m):
-        self.batch.remove(m)
-        out = m.read_fields()
+        torch = self.torch
+        self.batch.remove(m)          # the model's stream now waits for the batch's queued steps
+        shape = tuple(reversed(m.n))
+        rho_d = torch.empty(shape, dtype=torch.float64, device="cuda")
+        u_d = torch.empty((m.d,) + shape, dtype=torch.float64, device="cuda") if m.eq == "nse" else None
+        m.read_fields(rho_d, u_d)     # on the model's stream (the current one)
+        rho_h = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        rho_h.copy_(rho_d, non_blocking=True)
+        u_h = None
+        if u_d is not None:
+            u_h = torch.empty(u_d.shape, dtype=torch.float64, pin_memory=True)
+            u_h.copy_(u_d, non_blocking=True)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(torch.cuda.current_stream())
+        return (m, ev, rho_h, u_h, rho_d, u_d)
+
+    def done(self, h):
+        return h[1].query()
+
+    def finish_time(self, h):
+        ev0, t0 = self.ref
+        return t0 + ev0.elapsed_time(h[1]) / 1e3
+
+    def release(self, h):
+        m, ev, rho_h, u_h = h[0], h[1], h[2], h[3]
+        ev.synchronize()
         if self.keep_results:
-            self.results[m.rid] = out
+            self.results[m.rid] = (rho_h.numpy().copy(), None if u_h is None else u_h.numpy().copy())
         m.close()
 
     def run_alone(self, m, steps):
@@ -131,14 +191,19 @@ class GpuEngine:
             self.results[m.rid] = out
         m.close()
 
+    def close(self):
+        self.pool.shutdown(wait=True)
+        self.batch.close()
+
 
 class FakeEngine:
-    """CPU stand-in with the same interface: a step of the batch costs time proportional to the
+    """CPU stand-in with the same interface: a tick of the batch costs time proportional to the
     resident cells (tests of the host logic)."""
 
-    def __init__(self, seconds_per_cell_step=1e-12, bytes_per_cell=400):
+    def __init__(self, seconds_per_cell_step=1e-12, bytes_per_cell=400, clock=time.perf_counter):
         self.spc = seconds_per_cell_step
         self.bpc = bytes_per_cell
+        self.clock = clock
         self.resident = {}
         self.serial = 0
         self.steps_taken = collections.Counter()
@@ -146,7 +211,13 @@ class FakeEngine:
     def nbytes(self, req, store):
         return int(np.prod(req["grid"])) * self.bpc
 
-    def create(self, req, store, stream=None):
+    def start_clock(self, t0):
+        pass
+
+    def prepare(self, req, store):
+        return None
+
+    def create(self, req, store, prepared=None, stream=None):
         self.serial += 1
         m = self.serial
         cells = int(np.prod(req["grid"]))
@@ -160,13 +231,29 @@ class FakeEngine:
         for key in self.resident:
             self.steps_taken[key] += k
         time.sleep(self.spc * k * sum(self.resident.values()))
+        return None
+
+    def wait(self, token):
+        pass
 
     def finish(self, m):
-        self.resident.pop(m)
+        return (m, self.clock())
+
+    def done(self, h):
+        return True
+
+    def finish_time(self, h):
+        return h[1]
+
+    def release(self, h):
+        self.resident.pop(h[0])
 
     def run_alone(self, m, steps):
         self.steps_taken[m] += steps
         time.sleep(self.spc * steps * self.resident.pop(m))
+
+    def close(self):
+        pass
 
 
 @dataclass
@@ -176,51 +263,79 @@ class Running:
     nbytes: int
     record: Record
     done: int = 0
+    handle: object = None
 
 
 def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=64, clock=time.perf_counter,
-                  store_policy="as_requested"):
+                  store_policy="as_requested", ahead=1, prepare_depth=16):
     """Continuous batching over ``requests`` (sorted by arrival); ``store_policy`` as in
-    ``store_for``. Returns the records and the elapsed wall time."""
+    ``store_for``; ``ahead`` ticks stay queued beyond the one the device runs; the host fields of
+    up to ``prepare_depth`` arrived requests are generated ahead of their admission. Returns the
+    records and the elapsed wall time."""
     pending = collections.deque(sorted(requests, key=lambda r: r["arrival"]))
-    running = []
-    records = []
+    prepared = {}
+    running, retiring, records = [], [], []
+    queued = collections.deque()
     used = 0
     peak_used = [0]
     t0 = clock()
-    while pending or running:
+    engine.start_clock(t0)
+    while pending or running or retiring:
         now = clock() - t0
+        # host fields of arrived requests, on worker threads
+        for req in list(pending)[:prepare_depth]:
+            if req["arrival"] > now:
+                break
+            if req["rid"] not in prepared:
+                prepared[req["rid"]] = engine.prepare(req, store_for(req, store_policy))
+        # admission in arrival order while memory and slots allow
         while pending and pending[0]["arrival"] <= now and len(running) < max_resident:
             req = pending[0]
             store = store_for(req, store_policy)
-            if used + engine.nbytes(req, store) > budget_bytes and running:
+            if used + engine.nbytes(req, store) > budget_bytes and (running or retiring):
                 break          # does not fit yet: admit after a retirement frees memory
             pending.popleft()
-            m, nbytes, q = engine.create(req, store)
+            m, nbytes, q = engine.create(req, store, prepared.pop(req["rid"], None))
             engine.add(m)
             used += nbytes
             rec = Record(req["rid"], req["arrival"], admitted=clock() - t0, steps=req["steps"],
                          cells=int(np.prod(req["grid"])), lattice=req["lattice"], store=store, q=q)
             running.append(Running(req, m, nbytes, rec))
             peak_used[0] = max(peak_used[0], used)
-        if not running:
-            if pending:
-                time.sleep(max(0.0, pending[0]["arrival"] - (clock() - t0)))
-            continue
-        k = min(tick, min(r.req["steps"] - r.done for r in running))
-        engine.step(k)
-        for r in running:
-            r.done += k
+        # read-backs that have completed: the result is on the host, the memory is free
         still = []
-        for r in running:
-            if r.done >= r.req["steps"]:
-                engine.finish(r.model)
+        for r in retiring:
+            if engine.done(r.handle):
+                r.record.finished = engine.finish_time(r.handle) - t0
+                engine.release(r.handle)
                 used -= r.nbytes
-                r.record.finished = clock() - t0
                 records.append(r.record)
             else:
                 still.append(r)
-        running = still
+        retiring = still
+        if running:
+            k = min(tick, min(r.req["steps"] - r.done for r in running))
+            queued.append(engine.step(k))
+            for r in running:
+                r.done += k
+            still = []
+            for r in running:
+                if r.done >= r.req["steps"]:
+                    r.handle = engine.finish(r.model)
+                    retiring.append(r)
+                else:
+                    still.append(r)
+            running = still
+            while len(queued) > ahead:
+                engine.wait(queued.popleft())
+        elif retiring:
+            while queued:
+                engine.wait(queued.popleft())
+            time.sleep(1e-4)
+        elif pending:
+            time.sleep(max(0.0, min(pending[0]["arrival"] - (clock() - t0), 0.01)))
+    while queued:
+        engine.wait(queued.popleft())
     serve_batched.peak_bytes = peak_used[0]
     return records, clock() - t0
 
