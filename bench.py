@@ -690,7 +690,10 @@ def serving_precision(lbm, S):
     return out
 
 
-def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300):
+SERVING_STEP_BYTES = 4e9   # bound on the resident solves' work per batch step (serve_batched)
+
+
+def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300, max_step_bytes=SERVING_STEP_BYTES):
     """Config 5: the seeded request stream at its stated size, served by continuous batching
     (policy "f16_dev": FP16 deviations only where the class and run length keep the error within
     1e-3, FP32 otherwise; tiles from the autotuner) and by the plain FP32 one-solve-at-a-time path,
@@ -705,7 +708,7 @@ def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300):
     def both(reqs, tiles):
         eng = S.GpuEngine(tiles=tiles)
         rec_b, t_b = S.serve_batched(reqs, eng, budget_bytes=150e9, max_resident=512, tick=64,
-                                     store_policy="f16_dev")
+                                     store_policy="f16_dev", max_step_bytes=max_step_bytes)
         launches = eng.batch.counters()["launches"]
         eng.close()
         b = dict(S.summarize(rec_b, t_b), batched_launches=launches, hbm_budget_gb=150,
@@ -727,7 +730,7 @@ def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300):
         "mix": "2D rD2Q17/21/25 Taylor-Green + NCDE (32..1024 x 32..768), 3D rD3Q33/45/53 Kolmogorov "
                "(32^3..160^3), 200..5000 steps, Poisson arrivals",
         "batched": dict(b, storage="policy f16_dev: FP16 deviations where the class and run length keep the "
-                                   "u (phi) error <= 1e-3, FP32 otherwise"),
+                                   "u (phi) error <= 1e-3, FP32 otherwise", max_step_bytes=max_step_bytes),
         "sequential_fp32": q,
         "speedup_solves_per_s": b["solves_per_s"] / q["solves_per_s"],
         "sustained": {"requests": sustained_requests, "seed": seed + 1, "arrival_rate_per_s": rate2,

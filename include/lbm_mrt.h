@@ -383,6 +383,13 @@ lbm_status lbm_batch_remove(lbm_batch* b, lbm_model* m);
 lbm_status lbm_batch_set_tile(lbm_batch* b, lbm_kind kind, lbm_dtype store, lbm_eq eq,
                               int cells_per_tile);
 
+/* Members of at least `cells` cells (default 2^19) run on the single-solve kernels of
+ * lbm_model_step (one launch per step each, on the batch's stream) instead of the work-list
+ * kernel: a grid that large fills the GPU alone, and the single-solve kernels reach a larger share
+ * of HBM bandwidth. The results are bitwise the same either way. 0 keeps every member in the
+ * work-lists. Errors: LBM_ERR_ARG for a negative threshold. */
+lbm_status lbm_batch_set_solo_threshold(lbm_batch* b, int64_t cells);
+
 /* Advance every member by nsteps time steps, asynchronously on the batch's stream. Each step is
  * one persistent launch per group over a tile work-list that covers every cell of every solve of
  * the group (the same per-cell collide-stream arithmetic as lbm_model_step); groups of 8 steps are

@@ -46,6 +46,11 @@ struct lbm_batch {
   int num_sms = 0;
   std::vector<lbm_model*> members;
   std::vector<GroupHost> groups;
+  // members of at least solo_cells cells run on the single-solve kernels (one launch per step
+  // each, outside the work-lists): large grids fill the GPU alone and the single-solve kernels
+  // reach a larger share of HBM bandwidth than the work-list kernel
+  std::vector<lbm_model*> solos;
+  int64_t solo_cells = int64_t(1) << 19;
   std::map<std::tuple<int, int, int>, int> tile;  // (kind, store, eq) -> cells per tile
   bool dirty = true;
   bool stable = false;  // no change since the last step call: capture a graph
@@ -206,8 +211,13 @@ lbm_status upload_desc(lbm_batch* b, GroupHost& gh) {
 
 lbm_status rebuild(lbm_batch* b) {
   free_groups(b);
+  b->solos.clear();
   std::map<std::tuple<const lbm_lattice*, int, int, int>, size_t> index;
   for (lbm_model* m : b->members) {
+    if (b->solo_cells > 0 && m->ncells >= b->solo_cells) {
+      b->solos.push_back(m);
+      continue;
+    }
     const int high = has_high_rates(m) ? 1 : 0;
     auto key = std::make_tuple(m->lat, m->store, m->eq, high);
     auto it = index.find(key);
@@ -394,6 +404,14 @@ lbm_status lbm_batch_set_tile(lbm_batch* b, lbm_kind kind, lbm_dtype store, lbm_
   return LBM_OK;
 }
 
+lbm_status lbm_batch_set_solo_threshold(lbm_batch* b, int64_t cells) {
+  if (!b) return set_error(LBM_ERR_ARG, "NULL batch");
+  if (cells < 0) return set_error(LBM_ERR_ARG, "the threshold must be non-negative");
+  b->solo_cells = cells;
+  b->dirty = true;
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
   if (!b) return set_error(LBM_ERR_ARG, "NULL batch");
   if (nsteps < 0) return set_error(LBM_ERR_ARG, "nsteps must be non-negative");
@@ -419,6 +437,12 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
       lbm_status st = launch_group(gh, s & 1, b->stream);
       if (st != LBM_OK) return st;
     }
+  for (lbm_model* m : b->solos) {  // on the batch's stream, like the work-list launches
+    lbm_status st = dispatch_batch_kind(m->lat->kind, [&](auto kc) {
+      return Launch<decltype(kc)::value>::step(m, nsteps, true);
+    });
+    if (st != LBM_OK) return st;
+  }
   if (rem & 1) {
     // every model's current buffer flipped: swap the descriptors' buffers (the graph reads them)
     for (auto& gh : b->groups) {
@@ -436,12 +460,13 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
       if (st != LBM_OK) return st;
     }
   }
-  for (lbm_model* m : b->members) {
-    m->steps += nsteps;
-    m->launches += nsteps;
-  }
+  for (auto& gh : b->groups)  // (the single-solve launcher counts the solos' steps itself)
+    for (lbm_model* m : gh.members) {
+      m->steps += nsteps;
+      m->launches += nsteps;
+    }
   b->steps += nsteps;
-  b->launches += nsteps * int64_t(b->groups.size());
+  b->launches += nsteps * int64_t(b->groups.size() + b->solos.size());
   b->stable = true;
   return LBM_OK;
 }

@@ -266,17 +266,27 @@ class Running:
     handle: object = None
 
 
+def step_bytes(req, store):
+    """Algorithmic bytes one time step of a request moves: every population read and written once."""
+    q = int(req["lattice"].split("Q")[1].split("-")[0])
+    return int(np.prod(req["grid"])) * 2 * q * (4 if store == "f32" else 2)
+
+
 def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=64, clock=time.perf_counter,
-                  store_policy="as_requested", ahead=1, prepare_depth=16):
+                  store_policy="as_requested", ahead=1, prepare_depth=16, max_step_bytes=None):
     """Continuous batching over ``requests`` (sorted by arrival); ``store_policy`` as in
     ``store_for``; ``ahead`` ticks stay queued beyond the one the device runs; the host fields of
-    up to ``prepare_depth`` arrived requests are generated ahead of their admission. Returns the
-    records and the elapsed wall time."""
+    up to ``prepare_depth`` arrived requests are generated ahead of their admission.
+    ``max_step_bytes`` bounds the work of the resident solves per batch step (a new arrival waits
+    while it would exceed the bound, unless nothing runs): enough to keep the device busy, few
+    enough that the solves ahead in the queue finish first instead of all sharing the device to
+    the end. Returns the records and the elapsed wall time."""
     pending = collections.deque(sorted(requests, key=lambda r: r["arrival"]))
     prepared = {}
     running, retiring, records = [], [], []
     queued = collections.deque()
     used = 0
+    work = 0          # step bytes of the running solves
     peak_used = [0]
     t0 = clock()
     engine.start_clock(t0)
@@ -294,7 +304,11 @@ def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=6
             store = store_for(req, store_policy)
             if used + engine.nbytes(req, store) > budget_bytes and (running or retiring):
                 break          # does not fit yet: admit after a retirement frees memory
+            sb = step_bytes(req, store)
+            if max_step_bytes is not None and running and work + sb > max_step_bytes:
+                break          # the device is busy enough: admit when a running solve finishes
             pending.popleft()
+            work += sb
             m, nbytes, q = engine.create(req, store, prepared.pop(req["rid"], None))
             engine.add(m)
             used += nbytes
@@ -323,6 +337,7 @@ def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=6
                 if r.done >= r.req["steps"]:
                     r.handle = engine.finish(r.model)
                     retiring.append(r)
+                    work -= step_bytes(r.req, r.record.store)
                 else:
                     still.append(r)
             running = still

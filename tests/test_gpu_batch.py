@@ -62,6 +62,30 @@ def _compare(a, b, store):
     return np.array_equal(ra, rb) and (ua is None or np.array_equal(ua, ub))
 
 
+def test_batch_solos_equal_single_solve_path():
+    """Members above the solo threshold run on the single-solve kernels inside the batch (here a
+    low threshold makes the larger half of the mix solos, 16-bit storage with n_x % 8 == 0 on the
+    row-staged kernel among them): every member is bitwise the same as the same solve alone, and
+    the step counters count each solo step once."""
+    from paper_2512_16230_gb300 import lbm
+    mix = MIX + [("rD3Q53", "nse", (16, 10, 9), "f16_dev"), ("rD2Q17", "ncde", (24, 20), "bf16_dev")]
+    cache = {}
+    alone = [_make(cache, *spec, seed=i) for i, spec in enumerate(mix)]
+    batched = [_make(cache, *spec, seed=i) for i, spec in enumerate(mix)]
+    b = lbm.Batch(64)
+    b.set_solo_threshold(1000)
+    for m in batched:
+        b.add(m)
+    b.step(13)
+    b.synchronize()
+    for m in alone:
+        m.step(13)
+    assert [m.counters()[0] for m in batched] == [13] * len(mix)
+    exact = [_compare(x, y, spec[3]) for x, y, spec in zip(alone, batched, mix)]
+    assert all(exact)
+    b.close()
+
+
 def test_batch_equals_single_solve_path():
     from paper_2512_16230_gb300 import lbm
     cache = {}

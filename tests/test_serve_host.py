@@ -81,3 +81,17 @@ def test_storage_policy():
                 assert S.store_for(req, "as_requested") == ("f32" if store == "f32" else f16)
                 assert S.store_for(req, "f16_dev") == f16
                 assert S.store_for(req, "bf16_dev") == "bf16_dev"
+
+
+def test_step_work_bound_admits_in_order():
+    """With a bound on the resident step work (a request waits while it would exceed the bound,
+    unless nothing runs), every request still completes and admission stays in arrival order."""
+    reqs = _requests(n=30, rate=1e4)
+    eng = S.FakeEngine(seconds_per_cell_step=1e-9)
+    bound = max(S.step_bytes(r, "f32") for r in reqs)
+    recs, _ = S.serve_batched(reqs, eng, budget_bytes=1e12, tick=5, store_policy="f32", max_step_bytes=bound)
+    assert sorted(r.rid for r in recs) == [r["rid"] for r in reqs]
+    adm = sorted(recs, key=lambda r: r.admitted)
+    assert [r.rid for r in adm] == sorted(r.rid for r in recs)
+    assert S.step_bytes(dict(lattice="rD3Q53-cubic", grid=(10, 10, 10)), "f32") == 1000 * 2 * 53 * 4
+    assert S.step_bytes(dict(lattice="rD2Q17", grid=(10, 20)), "f16_dev") == 200 * 2 * 17 * 2
