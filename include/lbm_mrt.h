@@ -233,9 +233,11 @@ lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable);
  * goes back to memory by one bulk copy per population. It applies when n_x is a multiple of 8
  * (16-byte rows) and at most 256 cells. THREADS: every thread loads and stores its own cell's
  * populations in global memory. Both give bitwise the same populations.
- * AUTO (default) takes ROWS where it applies. Errors: LBM_ERR_ARG for an unknown mode, or ROWS
- * on a model it does not apply to; a step with ROWS forced and per-order rates or the tensor
- * cores (which have no row-staged kernel) returns LBM_ERR_NOT_IMPLEMENTED. */
+ * With the tensor cores selected (lbm_model_set_tensor_cores), ROWS runs the two contractions
+ * on tcgen05 with the A operands written into tensor memory, also with per-order rates (bitwise
+ * the per-thread tcgen05 kernel). AUTO (default) takes ROWS where it applies. Errors: LBM_ERR_ARG
+ * for an unknown mode, or ROWS on a model it does not apply to; a step with ROWS forced and
+ * per-order rates on the CUDA cores (no row-staged kernel) returns LBM_ERR_NOT_IMPLEMENTED. */
 lbm_status lbm_model_set_gather(lbm_model* m, lbm_gather mode);
 
 /* Equation of state p = rho * cs2_eq (NSE, Eq. (M-NSEs-6-1)) or the prefactor of the diffusion

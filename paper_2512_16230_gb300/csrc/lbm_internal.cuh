@@ -183,12 +183,16 @@ struct RowPlan {
   int grid;
   size_t smem;
   RowParams rp;
+  bool tensor;  // the tensor-core kernel (k_step_rows_tc) for the collide steps
+  bool high;    // with the rows of order >= 4 at their own rates (tensor-core kernel only)
+  TcParams tp;
 };
 template <int KIND>
 struct RowLaunch {
   // false when the kernel does not apply (storage not 16-bit, n_x not a multiple of 8 or above the
-  // pitch, or the shared memory cannot hold two row buffers)
-  static bool plan(const lbm_model* m, RowPlan* out);
+  // pitch, or the shared memory cannot hold three row buffers); `tensor`: the tensor-core kernel,
+  // `high`: with one rate per order >= 4 (needs `tensor`)
+  static bool plan(const lbm_model* m, RowPlan* out, bool tensor = false, bool high = false);
   static lbm_status configure(const lbm_model* m, const RowPlan& plan, bool collide);
   static lbm_status launch(const lbm_model* m, const RowPlan& plan, const StepParams<float>& p, const void* fin,
                            void* fout, float* phi, bool collide);

@@ -1026,15 +1026,16 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
       tgrid = tc_grid(m, tp.ntiles, k, 3, tsmem);
     }
   }
-  // 16-bit storage on the CUDA cores: the row-staged gather where it applies (or is forced)
+  // 16-bit storage: the row-staged gather where it applies (or is forced), with the contractions
+  // on the CUDA cores or, when the tensor cores are selected, on tcgen05
   [[maybe_unused]] RowPlan rplan;
   bool rows = false;
   if constexpr (is_deviation_storage<ST>()) {
-    if (m->gather == LBM_GATHER_ROWS && (tensor || high))
+    if (m->gather == LBM_GATHER_ROWS && high && !tensor)
       return set_error(LBM_ERR_NOT_IMPLEMENTED,
-                       "the row-staged gather has no kernel for per-order rates or the tensor cores");
-    if (m->gather != LBM_GATHER_THREADS && !tensor && !high) {
-      rows = RowLaunch<L::KIND>::plan(m, &rplan);
+                       "the row-staged gather runs per-order rates on the tensor cores only");
+    if (m->gather != LBM_GATHER_THREADS && (!high || tensor)) {
+      rows = RowLaunch<L::KIND>::plan(m, &rplan, tensor, high);
       if (!rows && m->gather == LBM_GATHER_ROWS) return set_error(LBM_ERR_ARG, "the row-staged gather does not apply");
       if (rows && nsteps > 0) {
         const lbm_status st = RowLaunch<L::KIND>::configure(m, rplan, collide_on);

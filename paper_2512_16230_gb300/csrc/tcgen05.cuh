@@ -7,8 +7,9 @@
 //   * tcgen05.alloc / dealloc / relinquish_alloc_permit are warp-wide (.sync.aligned);
 //   * tcgen05.commit makes an mbarrier track the completion of every tcgen05 operation the
 //     issuing thread started before it;
-//   * with M = 128 and cta_group::1, row i of D is TMEM lane i, so the 32x32b load of warp w
-//     (w = warp index mod 4) returns rows 32w..32w+31, one row per thread.
+//   * with M = 128 and cta_group::1, row i of D (and of an A operand held in TMEM) is TMEM lane i,
+//     so the 32x32b load or store of warp w (w = warp index mod 4) covers rows 32w..32w+31, one
+//     row per thread.
 #pragma once
 
 #include <cstdint>
@@ -49,6 +50,18 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// The same product with A read from tensor memory (a_tmem: A's first column; row m of A is lane m,
+// two 16-bit elements per 32-bit column, so one K = 16 slice spans 8 columns).
+__device__ __forceinline__ void mma_f16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -95,6 +108,29 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
 }
 __device__ __forceinline__ void wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// 32 lanes x 32b, 16 consecutive columns: this thread's row, columns col..col+15 <- v.
+__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// Barrier over COUNT threads (a multiple of 32) with the named barrier ID (1..15; 0 is
+// __syncthreads), both compile-time so that the kernel reserves only the barriers it names.
+template <int ID, int COUNT>
+__device__ __forceinline__ void named_barrier() {
+  asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
 }
 
 // mbarrier with a bounded wait: returns false if the phase did not complete within `limit`

@@ -134,8 +134,8 @@ def test_row_gather_with_gradient_terms(store):
 
 def test_row_gather_errors():
     """ROWS is refused where it does not apply (n_x not a multiple of 8, above the pitch, FP32
-    storage) and a forced ROWS step with a kernel that has no row-staged form reports
-    LBM_ERR_NOT_IMPLEMENTED; nothing runs in either case."""
+    storage) and a forced ROWS step with a kernel that has no row-staged form (per-order rates on
+    the CUDA cores) reports LBM_ERR_NOT_IMPLEMENTED; nothing runs in either case."""
     from paper_2512_16230_gb300 import lbm
     spec = W.LATTICES["rD3Q53"]
     for n, store in (((37, 8, 8), "f16_dev"), ((264, 4, 4), "f16_dev"), ((16, 8, 8), "f32")):
@@ -145,12 +145,82 @@ def test_row_gather_errors():
         gm.close()
     gm = gpu_model(spec, "nse", (16, 8, 8), np.ones(spec.R), store="f16_dev")
     gm.set_gather("rows")
-    gm.set_tensor_cores(1)
-    with pytest.raises(lbm.LBMError, match="LBM_ERR_NOT_IMPLEMENTED"):
-        gm.step(1)
     gm.set_tensor_cores(0)
-    gm.set_high_rates([0.9, 1.2])
+    gm.set_high_rates([0.9, 1.2])       # per-order rates on the CUDA cores have no row-staged kernel
     with pytest.raises(lbm.LBMError, match="LBM_ERR_NOT_IMPLEMENTED"):
         gm.step(1)
     assert gm.counters() == (0, 0)
     assert lbm.load().lbm_model_set_gather(gm.handle, 7) == 1    # unknown mode: LBM_ERR_ARG
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+@pytest.mark.parametrize("eq", ["nse", "ncde"])
+@pytest.mark.parametrize("name", LATTICES)
+def test_row_gather_tensor_cores_step(name, eq, store):
+    """The row-staged kernel with the contractions on tcgen05 (A operands written into tensor memory
+    by the threads): one step within the 16-bit bound of the FP64 oracle from the same stored state;
+    after three steps bitwise the per-thread tcgen05 kernel (the same products on the same operands,
+    A from shared memory there) and within the 16-bit bound of the CUDA-core row kernel."""
+    spec = W.LATTICES[name]
+    d = spec.d
+    n = ROW_GRIDS[d][1]
+    s = np.random.default_rng(3).uniform(0.6, 1.9, spec.R)
+    kw = _step_kwargs(eq, d)
+    om = oracle_model(spec, eq, n, s, **kw)
+    w = om.lat.w
+    f0 = _near_equilibrium(w, n, om.lat.Q, 5, eq)
+    out = {}
+    for mode, tensor in (("rows", 1), ("rows", 0), ("threads", 1)):
+        gm = gpu_model(spec, eq, n, s, store=store, **kw)
+        gm.set_gather(mode)
+        gm.set_tensor_cores(tensor)
+        gm.set_populations(f0)
+        if mode == "rows" and tensor:
+            om.set_populations(gm.get_populations())
+            om.step(1)
+        gm.step(1)
+        out[mode, tensor, 1] = gm.get_populations()
+        gm.step(2)
+        out[mode, tensor, 3] = gm.get_populations()
+        gm.synchronize()
+        gm.close()
+    ref = w.reshape((-1,) + (1,) * d) * (1.0 if eq == "nse" else 0.0)
+    assert rel_l2(out["rows", 1, 1] - ref, om.f - ref) <= 4 * UNIT[store]
+    assert np.array_equal(out["rows", 1, 3], out["threads", 1, 3])
+    assert rel_l2(out["rows", 1, 3] - ref, out["rows", 0, 3] - ref) <= 4 * UNIT[store]
+
+
+HIGH_RATES = {4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25}
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+@pytest.mark.parametrize("name", ["rD2Q13", "rD2Q25", "rD3Q33", "rD3Q45", "rD3Q53", "rD2Q9", "rD3Q27"])
+def test_row_gather_tensor_cores_high_order_rates(name, store):
+    """The full Q x Q collision with one rate per order >= 4 in the row-staged tensor-core kernel
+    (the higher rows join both products): one step within the 16-bit bound of the FP64 oracle with
+    the same per-order rates, and three steps bitwise the per-thread tcgen05 kernel."""
+    spec = W.LATTICES[name]
+    d = spec.d
+    n = ROW_GRIDS[d][1]
+    s = np.random.default_rng(31).uniform(0.6, 1.9, spec.R)
+    kw = dict(s_high=1.2, force=(0, d - 1, 1e-3, 1, 0.2), s_orders=HIGH_RATES)
+    om = oracle_model(spec, "nse", n, s, **kw)
+    w = om.lat.w
+    f0 = _near_equilibrium(w, n, om.lat.Q, 6, "nse")
+    out = {}
+    for mode in ("rows", "threads"):
+        gm = gpu_model(spec, "nse", n, s, store=store, **kw)
+        gm.set_gather(mode)
+        gm.set_tensor_cores(1)
+        gm.set_populations(f0)
+        if mode == "rows":
+            om.set_populations(gm.get_populations())
+            om.step(1)
+        gm.step(1)
+        out[mode, 1] = gm.get_populations()
+        gm.step(2)
+        out[mode, 3] = gm.get_populations()
+        gm.close()
+    wr = w.reshape((-1,) + (1,) * d)
+    assert rel_l2(out["rows", 1] - wr, om.f - wr) <= 4 * UNIT[store]
+    assert np.array_equal(out["rows", 3], out["threads", 3])
