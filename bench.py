@@ -705,8 +705,8 @@ def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300, max
     from paper_2512_16230_gb300 import lbm
     from paper_2512_16230_gb300 import serve as S
 
-    def both(reqs, tiles):
-        eng = S.GpuEngine(tiles=tiles)
+    def both(reqs, tuning):
+        eng = S.GpuEngine(tuning=tuning)
         rec_b, t_b = S.serve_batched(reqs, eng, budget_bytes=150e9, max_resident=512, tick=64,
                                      store_policy="f16_dev", max_step_bytes=max_step_bytes)
         launches = eng.batch.counters()["launches"]
@@ -720,11 +720,17 @@ def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300, max
         return b, S.summarize(rec_s, t_s)
 
     reqs = I.serving_requests(n_requests, seed=seed, rate_per_s=rate_per_s)
-    tiles = autotune.autotune()
-    b, q = both(reqs, tiles)
+    tuning = autotune.autotune()
+    b, q = both(reqs, tuning)
     rate2 = 0.8 * min(b["solves_per_s"], q["solves_per_s"])
     reqs2 = I.serving_requests(sustained_requests, seed=seed + 1, rate_per_s=rate2)
-    b2, q2 = both(reqs2, tiles)
+    b2, q2 = both(reqs2, tuning)
+    groups = {}
+    for key, ms in tuning["ms_per_step"].items():
+        if "|tile=" in key:
+            g = key.split("|tile=")[0]
+            lo, hi = groups.get(g, (ms, ms))
+            groups[g] = (min(lo, ms), max(hi, ms))
     return {
         "requests": n_requests, "arrival_rate_per_s": rate_per_s, "seed": seed,
         "mix": "2D rD2Q17/21/25 Taylor-Green + NCDE (32..1024 x 32..768), 3D rD3Q33/45/53 Kolmogorov "
@@ -736,7 +742,9 @@ def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300, max
         "sustained": {"requests": sustained_requests, "seed": seed + 1, "arrival_rate_per_s": rate2,
                       "batched": b2, "sequential_fp32": q2},
         "errors_vs_fp64": serving_precision(lbm, S),
-        "tiles": {"|".join(k): v for k, v in tiles.items()},
+        "tuning": dict(autotune.summary(tuning),
+                       group_ms_best_worst={g: [round(v[0], 4), round(v[1], 4)] for g, v in groups.items()},
+                       solo_ms={k: round(v, 4) for k, v in tuning["ms_per_step"].items() if k.startswith("solo_cells=")}),
     }
 
 

@@ -385,6 +385,12 @@ lbm_status lbm_batch_remove(lbm_batch* b, lbm_model* m);
 lbm_status lbm_batch_set_tile(lbm_batch* b, lbm_kind kind, lbm_dtype store, lbm_eq eq,
                               int cells_per_tile);
 
+/* Persistent grid of a group's work-list launch: at most `blocks` resident blocks per SM (the
+ * grid is that times the SM count, capped by the tile count); 0 (default) takes the occupancy
+ * limit of the kernel. A launch-shape knob for autotuning; results do not depend on it.
+ * Errors: LBM_ERR_ARG for a negative count. */
+lbm_status lbm_batch_set_blocks_per_sm(lbm_batch* b, lbm_kind kind, lbm_dtype store, lbm_eq eq, int blocks);
+
 /* Members of at least `cells` cells (default 2^19) run on the single-solve kernels of
  * lbm_model_step (one launch per step each, on the batch's stream) instead of the work-list
  * kernel: a grid that large fills the GPU alone, and the single-solve kernels reach a larger share

@@ -52,6 +52,7 @@ struct lbm_batch {
   std::vector<lbm_model*> solos;
   int64_t solo_cells = int64_t(1) << 19;
   std::map<std::tuple<int, int, int>, int> tile;  // (kind, store, eq) -> cells per tile
+  std::map<std::tuple<int, int, int>, int> per_sm;  // (kind, store, eq) -> resident blocks per SM (cap)
   bool dirty = true;
   bool stable = false;  // no change since the last step call: capture a graph
   cudaGraphExec_t graph = nullptr;
@@ -283,6 +284,8 @@ lbm_status rebuild(lbm_batch* b) {
       return BatchLaunch<decltype(kc)::value>::occupancy(gh.g.store, gh.g.eq, gh.g.block, gh.g.high, &per_sm);
     });
     if (st != LBM_OK) return st;
+    auto cap = b->per_sm.find(std::make_tuple(gh.g.kind, gh.g.store, gh.g.eq));
+    if (cap != b->per_sm.end() && cap->second > 0) per_sm = std::min(std::max(1, per_sm), cap->second);
     gh.g.grid = std::max(1, std::min(gh.g.ntiles, std::max(1, per_sm) * b->num_sms));
   }
   b->dirty = false;
@@ -400,6 +403,14 @@ lbm_status lbm_batch_set_tile(lbm_batch* b, lbm_kind kind, lbm_dtype store, lbm_
   if (cells_per_tile != 64 && cells_per_tile != 128 && cells_per_tile != 256)
     return set_error(LBM_ERR_ARG, "cells per tile must be 64, 128 or 256");
   b->tile[std::make_tuple(int(kind), int(store), int(eq))] = cells_per_tile;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_blocks_per_sm(lbm_batch* b, lbm_kind kind, lbm_dtype store, lbm_eq eq, int blocks) {
+  if (!b) return set_error(LBM_ERR_ARG, "NULL batch");
+  if (blocks < 0) return set_error(LBM_ERR_ARG, "blocks per SM must be non-negative");
+  b->per_sm[std::make_tuple(int(kind), int(store), int(eq))] = blocks;
   b->dirty = true;
   return LBM_OK;
 }

@@ -71,6 +71,7 @@ SIGNATURES = {
     "lbm_batch_remove": (c_int, [_P, _P]),
     "lbm_batch_set_tile": (c_int, [_P, c_int, c_int, c_int, c_int]),
     "lbm_batch_set_solo_threshold": (c_int, [_P, c_int64]),
+    "lbm_batch_set_blocks_per_sm": (c_int, [_P, c_int, c_int, c_int, c_int]),
     "lbm_batch_step": (c_int, [_P, c_int64]),
     "lbm_batch_counters": (c_int, [_P, _PI64, _PI64, POINTER(c_int), _PI64]),
     "lbm_batch_stream": (c_void_p, [_P]),
@@ -419,6 +420,11 @@ class Batch:
     def set_tile(self, kind, store, eq, cells):
         _check(load().lbm_batch_set_tile(self.handle, KINDS[kind], DTYPES[store], EQS[eq], int(cells)),
                "lbm_batch_set_tile")
+
+    def set_blocks_per_sm(self, kind, store, eq, blocks):
+        """Resident blocks per SM of a group's persistent launch (0: the occupancy limit)."""
+        _check(load().lbm_batch_set_blocks_per_sm(self.handle, KINDS[kind], DTYPES[store], EQS[eq], int(blocks)),
+               "lbm_batch_set_blocks_per_sm")
 
     def set_solo_threshold(self, cells):
         """Members of at least ``cells`` cells run on the single-solve kernels (0: none)."""

@@ -86,8 +86,9 @@ class GpuEngine:
     start the read-back, return a handle), ``done`` / ``finish_time`` / ``release`` (poll the
     read-back, its completion time on the host clock, free the model)."""
 
-    def __init__(self, max_solves=4096, tiles=None, keep_results=False, workers=4):
+    def __init__(self, max_solves=4096, tuning=None, keep_results=False, workers=4):
         import torch
+        from . import autotune
         from . import lbm
         self.torch = torch
         self.lbm = lbm
@@ -98,8 +99,7 @@ class GpuEngine:
         self.results = {}
         self.pool = cf.ThreadPoolExecutor(max_workers=workers)
         self.ref = None
-        for key, cells in (tiles or {}).items():
-            self.batch.set_tile(*key, cells)
+        autotune.apply(self.batch, tuning)
 
     def lattice(self, name):
         if name not in self._lattices:
@@ -406,16 +406,18 @@ def main(argv=None):
                     help="comma-separated storage policies of the batched path")
     a = ap.parse_args(argv)
     reqs = I.serving_requests(a.requests, seed=a.seed, rate_per_s=a.rate)
-    tiles = autotune.autotune()
+    tuning = autotune.autotune()
     out = {"requests": a.requests, "rate_per_s": a.rate, "seed": a.seed}
     for policy in a.policies.split(","):
-        eng = GpuEngine(tiles=tiles)
+        eng = GpuEngine(tuning=tuning)
         rec_b, t_b = serve_batched(reqs, eng, budget_bytes=a.budget_gb * 1e9, tick=a.tick, store_policy=policy)
         out[f"batched_{policy}"] = dict(summarize(rec_b, t_b), peak_resident_gb=serve_batched.peak_bytes / 1e9,
                                         batched_launches=eng.batch.counters()["launches"])
-        eng.batch.close()
+        eng.close()
     if not a.skip_sequential:
-        rec_s, t_s = serve_sequential(reqs, GpuEngine(), store="f32")
+        seq = GpuEngine()
+        rec_s, t_s = serve_sequential(reqs, seq, store="f32")
+        seq.close()
         out["sequential_fp32"] = summarize(rec_s, t_s)
     print(json.dumps(out))
 
