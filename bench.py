@@ -36,7 +36,14 @@ METRIC = "rD3Q53 MLUPS"
 UNIT = "MLUPS"
 GRID = (256, 256, 192)
 Q = 53
-PROFILE = os.path.join(ROOT, "profiles", "k_step_rd3q53_f32_tgv3d_256x256x192.md")
+# DRAM traffic of the benchmark kernel per cell update, from an ncu capture of the same workload on
+# 256 x 256 x 96 cells (half the grid: 2.7 GB on the device), scaled to the benchmark grid by cells
+PROFILE = os.path.join(ROOT, "profiles", "k_step_rd3q53_f32_tgv3d_256x256x96.md")
+# the sources the benchmark kernel is compiled from (the traffic figure is void once one changes)
+KERNEL_SOURCES = ("include/lbm_mrt.h", "paper_2512_16230_gb300/csrc/lattices.cuh",
+                  "paper_2512_16230_gb300/csrc/lbm_internal.cuh", "paper_2512_16230_gb300/csrc/mrt_kernels.cuh",
+                  "paper_2512_16230_gb300/csrc/tc_kernels.cuh", "paper_2512_16230_gb300/csrc/tcgen05.cuh",
+                  "paper_2512_16230_gb300/csrc/k_rd3q53.cu")
 CPU_SAMPLE_GRID = (256, 256, 16)    # cpu_baseline: ~10-30 s of oracle work on the GPU machine
 CPU_SAMPLE_STEPS = 8
 REF_BUDGET_S = 150.0                  # --impl reference: wall-clock budget for W + K sample steps
@@ -72,9 +79,8 @@ def _config(extra=None, grid=GRID, store="f32"):
 
 def _source_sha():
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2512_16230_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
