@@ -98,6 +98,16 @@ def _profile_traffic(cells):
     return float(m.group(1)) * cells, s.group(1)
 
 
+def _kernel_name(args, grid):
+    """The collide-stream kernel the library runs for this storage and grid."""
+    rows = args.store != "f32" and grid[0] % 8 == 0 and grid[0] <= 256
+    if args.store == "f32":
+        return "k_step<rD3Q53, f32, NSE>"
+    base = ("k_step_rows_tc" if args.tensor_cores else "k_step_rows") if rows else \
+        ("k_step_tc" if args.tensor_cores else "k_step")
+    return f"{base}<rD3Q53, {args.store}, NSE>"
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -468,8 +478,7 @@ def bench_ours(args):
             "config": _config(grid=grid, store=args.store),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                         "kernel": ("k_step_tc<rD3Q53, " if args.tensor_cores else "k_step<rD3Q53, ")
-                                   + args.store + ", NSE> (fused pull-gather, collide, store)",
+                         "kernel": _kernel_name(args, grid) + " (fused pull-gather, collide, store)",
                          "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": launch_ms},
             "clocks": {k: csum[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes / args.steps,
@@ -507,7 +516,8 @@ def bench_ours(args):
     torch.cuda.empty_cache()
     if rank == 0:
         line["variants"]["high_order_rates_f16_tensor_cores"] = {
-            "kernel": "k_step_tc<rD3Q53, f16_dev, NSE, higher rows> (tcgen05 products with the dense higher rows)",
+            "kernel": "k_step_rows_tc<rD3Q53, f16_dev, NSE, higher rows> (row-staged, tcgen05 products with the "
+                      "dense higher rows)",
             "rates": {str(k): v for k, v in HIGH_RATES.items()}, "steps": vsteps,
             "ms_per_step": high16_ms, "mlups": cells / high16_ms / 1e3,
             "hbm_frac": 2 * Q * 2 * cells / (high16_ms / 1e3) / 1e9 / peak}
@@ -519,7 +529,10 @@ def bench_ours(args):
             ("bf16_deviations", "bf16_dev", 0, "auto", "k_step_rows<rD3Q53, bf16_dev, NSE>"),
             ("f16_deviations_thread_gather", "f16_dev", 0, "threads",
              "k_step<rD3Q53, f16_dev, NSE> (per-thread gather from global memory)"),
-            ("f16_deviations_tensor_cores", "f16_dev", 1, "auto", "k_step_tc<rD3Q53, f16_dev, NSE>")):
+            ("f16_deviations_tensor_cores", "f16_dev", 1, "auto",
+             "k_step_rows_tc<rD3Q53, f16_dev, NSE> (row-staged, contractions on tcgen05)"),
+            ("f16_deviations_tensor_cores_thread_gather", "f16_dev", 1, "threads",
+             "k_step_tc<rD3Q53, f16_dev, NSE> (per-thread gather, contractions on tcgen05)")):
         mr = lbm.Model(lat, "nse", wl.n, store=store, stream=stream.cuda_stream)
         mr.set_relaxation(wl.s, wl.s_high)
         mr.set_tensor_cores(tc)
