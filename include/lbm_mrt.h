@@ -237,7 +237,10 @@ lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable);
  * on tcgen05 with the A operands written into tensor memory, also with per-order rates (bitwise
  * the per-thread tcgen05 kernel). AUTO (default) takes ROWS where it applies. Errors: LBM_ERR_ARG
  * for an unknown mode, or ROWS on a model it does not apply to; a step with ROWS forced and
- * per-order rates on the CUDA cores (no row-staged kernel) returns LBM_ERR_NOT_IMPLEMENTED. */
+ * per-order rates on the CUDA cores (no row-staged kernel) returns LBM_ERR_NOT_IMPLEMENTED.
+ * mode = 3 is a test hook of the bounded waits: ROWS with no row copy issued, so every wait on a
+ * row buffer runs out after a short limit, the CTAs return, the next synchronizing call reports
+ * LBM_ERR_TIMEOUT and the populations are left undefined. */
 lbm_status lbm_model_set_gather(lbm_model* m, lbm_gather mode);
 
 /* Equation of state p = rho * cs2_eq (NSE, Eq. (M-NSEs-6-1)) or the prefactor of the diffusion

@@ -314,7 +314,8 @@ lbm_status take_status(lbm_model* m) {
   if (err == cudaSuccess) err = cudaStreamSynchronize(m->stream);
   if (err != cudaSuccess) return cuda_error(err, "status word");
   return set_error(LBM_ERR_TIMEOUT,
-                   "a tensor-core step gave up waiting for its matrix products; the populations are invalid");
+                   "a step gave up waiting on the device (tensor-core products or row copies); the populations "
+                   "are invalid");
 }
 
 template <class F>
@@ -577,8 +578,10 @@ lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable) {
 
 lbm_status lbm_model_set_gather(lbm_model* m, lbm_gather mode) {
   if (!m) return set_error(LBM_ERR_ARG, "NULL model");
-  if (mode != LBM_GATHER_AUTO && mode != LBM_GATHER_THREADS && mode != LBM_GATHER_ROWS)
+  const bool no_copy = int(mode) == 3;  // test hook: rows without copies (every wait runs out)
+  if (mode != LBM_GATHER_AUTO && mode != LBM_GATHER_THREADS && mode != LBM_GATHER_ROWS && !no_copy)
     return set_error(LBM_ERR_ARG, "gather must be LBM_GATHER_AUTO, _THREADS or _ROWS");
+  if (no_copy) mode = LBM_GATHER_ROWS;
   if (mode == LBM_GATHER_ROWS) {
     RowPlan plan;
     DeviceGuard guard(m->device);
@@ -593,6 +596,7 @@ lbm_status lbm_model_set_gather(lbm_model* m, lbm_gather mode) {
                                     "at most 256 cells");
   }
   m->gather = int(mode);
+  m->row_no_copy = no_copy;
   return LBM_OK;
 }
 

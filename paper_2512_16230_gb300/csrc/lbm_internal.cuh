@@ -73,6 +73,7 @@ struct lbm_model {
   bool tc_auto;      // no explicit choice yet: tcgen05 with per-order rates (FP32 or 16-bit storage)
   bool tc_no_issue;  // test hook: k_step_tc issues no matrix product, so its waits run out
   int gather;        // lbm_gather: how the CUDA-core kernel of 16-bit storage gathers (auto, threads, rows)
+  bool row_no_copy;  // test hook: the row-staged kernels issue no row copy, so their waits run out
   int* status;       // device status word: non-zero after a device-side wait ran out
   int64_t steps, launches;
   int device;
@@ -178,6 +179,7 @@ struct RowParams {
   uint32_t stage_bytes;         // Q * pitch * 2
   int* status;
   unsigned wait_limit;          // mbarrier polls before a wait is declared lost
+  int no_copy;                  // test hook: issue no row copy (every wait then runs out)
 };
 struct RowPlan {
   int grid;

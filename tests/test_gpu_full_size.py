@@ -60,11 +60,13 @@ def _oracle_first_step(wl, cells, rho, u):
     return np.array([[ft[i, s * Q + i] for s in range(len(cells))] for i in range(Q)])
 
 
-def _gpu_first_step(wl, cells, rho, u):
+def _gpu_first_step(wl, cells, rho, u, tensor=0):
     import torch
     spec = wl.lattice
     gm = gpu_model(spec, wl.eq, wl.n, wl.s, wl.s_high, force=wl.force, u_const=wl.u_const, nonlin=wl.nonlin,
                    store=wl.store)
+    if tensor:
+        gm.set_tensor_cores(1)
     gm.init_fields(rho, None if u is None else np.ascontiguousarray(u))
     gm.step(1)
     out = torch.empty((gm.Q,) + tuple(reversed(wl.n)), dtype=torch.float64, device="cuda")
@@ -91,16 +93,18 @@ def test_config3_full_size_first_step_sampled():
     assert np.abs(got - want).max() <= 10 * TOL["f32"] * np.abs(want).max()
 
 
+@pytest.mark.parametrize("tensor", [0, 1])
 @pytest.mark.parametrize("store,unit", [("f16_dev", 2.0 ** -11), ("bf16_dev", 2.0 ** -8)])
-def test_config4_full_size_first_step_sampled(store, unit):
+def test_config4_full_size_first_step_sampled(store, unit, tensor):
     """The reduced-precision configuration: the benchmark workload with 16-bit deviation storage
-    (f - w rho_ref stored, collision in FP32). One step at 72 sampled cells against the oracle's
-    per-cell collisions of the FP64 equilibrium: the deviations agree within the rounding of the
-    stored input and output (4 units of the 16-bit format)."""
+    (f - w rho_ref stored, collision in FP32), in the launch the benchmark times (the row-staged
+    kernel, with the contractions on the CUDA cores or on tcgen05). One step at 72 sampled cells
+    against the oracle's per-cell collisions of the FP64 equilibrium: the deviations agree within
+    the rounding of the stored input and output (4 units of the 16-bit format)."""
     wl = W.taylor_green_3d(store=store)
     rho, u = wl.fields()
     cells = _sample_cells(wl.n, 64, seed=7)
-    got = _gpu_first_step(wl, cells, rho, u)
+    got = _gpu_first_step(wl, cells, rho, u, tensor)
     want = _oracle_first_step(wl, cells, rho, u)
     w = oracle_lattice(wl.lattice).w[:, None]
     assert rel_l2(got - w, want - w) <= 4 * unit

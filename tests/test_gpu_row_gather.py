@@ -224,3 +224,26 @@ def test_row_gather_tensor_cores_high_order_rates(name, store):
     wr = w.reshape((-1,) + (1,) * d)
     assert rel_l2(out["rows", 1] - wr, om.f - wr) <= 4 * UNIT[store]
     assert np.array_equal(out["rows", 3], out["threads", 3])
+
+
+@pytest.mark.parametrize("tensor", [0, 1])
+def test_row_gather_timeout_is_reported(tensor):
+    """The bounded waits of the row-staged kernels: with the test hook no row copy is issued, every
+    CTA's wait on its first row buffer runs out, the status word reports LBM_ERR_TIMEOUT at the next
+    synchronisation, and the model (and the context) keep working afterwards."""
+    from paper_2512_16230_gb300 import lbm
+    spec = W.LATTICES["rD3Q53"]
+    n = (32, 12, 10)
+    gm = gpu_model(spec, "nse", n, np.ones(spec.R), store="f16_dev")
+    gm.init_fields(*I.rest_state(n, 3))
+    gm.set_tensor_cores(tensor)
+    assert lbm.load().lbm_model_set_gather(gm.handle, 3) == 0
+    gm.step(1)
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_TIMEOUT"):
+        gm.synchronize()
+    gm.synchronize()                      # the status word was cleared
+    gm.set_gather("rows")
+    gm.init_fields(*I.rest_state(n, 3))
+    gm.step(3)
+    rho, u = gm.read_fields()
+    assert np.allclose(rho, 1.0, atol=1e-3) and np.abs(u).max() < 1e-3
