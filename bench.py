@@ -709,13 +709,14 @@ def serving_precision(lbm, S):
     return out
 
 
-SERVING_STEP_BYTES = 4e9   # bound on the resident solves' work per batch step (serve_batched)
+SERVING_LARGE_STEP_BYTES = 5e8   # serve_batched: requests moving this much per step run one at a time
 
 
-def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300, max_step_bytes=SERVING_STEP_BYTES):
+def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300, large_step_bytes=SERVING_LARGE_STEP_BYTES):
     """Config 5: the seeded request stream at its stated size, served by continuous batching
     (policy "f16_dev": FP16 deviations only where the class and run length keep the error within
-    1e-3, FP32 otherwise; tiles from the autotuner) and by the plain FP32 one-solve-at-a-time path,
+    1e-3, FP32 otherwise; launch shapes from the autotuner; large requests one at a time with the
+    small ones admitted beside them) and by the plain FP32 one-solve-at-a-time path,
     same requests and arrival times (20 arrivals/s, more than either path serves: solves/s is the
     capacity). Then both paths on a shorter stream arriving at 0.8 x the smaller capacity, where
     p50/p99 measure service rather than queueing. Also the per-class errors."""
@@ -727,7 +728,7 @@ def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300, max
     def both(reqs, tuning):
         eng = S.GpuEngine(tuning=tuning)
         rec_b, t_b = S.serve_batched(reqs, eng, budget_bytes=150e9, max_resident=512, tick=64,
-                                     store_policy="f16_dev", max_step_bytes=max_step_bytes)
+                                     store_policy="f16_dev", large_step_bytes=large_step_bytes)
         launches = eng.batch.counters()["launches"]
         eng.close()
         b = dict(S.summarize(rec_b, t_b), batched_launches=launches, hbm_budget_gb=150,
@@ -755,7 +756,9 @@ def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300, max
         "mix": "2D rD2Q17/21/25 Taylor-Green + NCDE (32..1024 x 32..768), 3D rD3Q33/45/53 Kolmogorov "
                "(32^3..160^3), 200..5000 steps, Poisson arrivals",
         "batched": dict(b, storage="policy f16_dev: FP16 deviations where the class and run length keep the "
-                                   "u (phi) error <= 1e-3, FP32 otherwise", max_step_bytes=max_step_bytes),
+                                   "u (phi) error <= 1e-3, FP32 otherwise",
+                  admission="arrival order; requests moving >= large_step_bytes per step one at a time, smaller "
+                            "ones admitted past a waiting large one", large_step_bytes=large_step_bytes),
         "sequential_fp32": q,
         "speedup_solves_per_s": b["solves_per_s"] / q["solves_per_s"],
         "sustained": {"requests": sustained_requests, "seed": seed + 1, "arrival_rate_per_s": rate2,

@@ -273,14 +273,18 @@ def step_bytes(req, store):
 
 
 def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=64, clock=time.perf_counter,
-                  store_policy="as_requested", ahead=1, prepare_depth=16, max_step_bytes=None):
+                  store_policy="as_requested", ahead=1, prepare_depth=16, max_step_bytes=None,
+                  large_step_bytes=None):
     """Continuous batching over ``requests`` (sorted by arrival); ``store_policy`` as in
     ``store_for``; ``ahead`` ticks stay queued beyond the one the device runs; the host fields of
     up to ``prepare_depth`` arrived requests are generated ahead of their admission.
-    ``max_step_bytes`` bounds the work of the resident solves per batch step (a new arrival waits
-    while it would exceed the bound, unless nothing runs): enough to keep the device busy, few
-    enough that the solves ahead in the queue finish first instead of all sharing the device to
-    the end. Returns the records and the elapsed wall time."""
+    Admission is in arrival order. ``max_step_bytes`` bounds the work of the resident solves per
+    batch step (a new arrival waits while it would exceed the bound, unless nothing runs).
+    ``large_step_bytes``: a request moving at least that much per step is large; large requests run
+    one at a time, in arrival order, and the small ones behind a waiting large one are admitted
+    past it (they never delay its admission, which only waits for the running large one), so that
+    a large solve shares the device with small ones only and a small one never queues behind a
+    large one. Returns the records and the elapsed wall time."""
     pending = collections.deque(sorted(requests, key=lambda r: r["arrival"]))
     prepared = {}
     running, retiring, records = [], [], []
@@ -299,16 +303,24 @@ def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=6
             if req["rid"] not in prepared:
                 prepared[req["rid"]] = engine.prepare(req, store_for(req, store_policy))
         # admission in arrival order while memory and slots allow
+        large_running = large_step_bytes is not None and any(
+            step_bytes(r.req, r.record.store) >= large_step_bytes for r in running)
+        skipped = collections.deque()
         while pending and pending[0]["arrival"] <= now and len(running) < max_resident:
             req = pending[0]
             store = store_for(req, store_policy)
+            sb = step_bytes(req, store)
+            if large_step_bytes is not None and sb >= large_step_bytes and large_running:
+                skipped.append(pending.popleft())   # waits for the running large one; small ones pass
+                continue
             if used + engine.nbytes(req, store) > budget_bytes and (running or retiring):
                 break          # does not fit yet: admit after a retirement frees memory
-            sb = step_bytes(req, store)
             if max_step_bytes is not None and running and work + sb > max_step_bytes:
                 break          # the device is busy enough: admit when a running solve finishes
             pending.popleft()
             work += sb
+            if large_step_bytes is not None and sb >= large_step_bytes:
+                large_running = True
             m, nbytes, q = engine.create(req, store, prepared.pop(req["rid"], None))
             engine.add(m)
             used += nbytes
@@ -316,6 +328,7 @@ def serve_batched(requests, engine, budget_bytes=150e9, max_resident=512, tick=6
                          cells=int(np.prod(req["grid"])), lattice=req["lattice"], store=store, q=q)
             running.append(Running(req, m, nbytes, rec))
             peak_used[0] = max(peak_used[0], used)
+        pending.extendleft(reversed(skipped))        # the waiting large ones keep their places
         # read-backs that have completed: the result is on the host, the memory is free
         still = []
         for r in retiring:
@@ -401,6 +414,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--tick", type=int, default=64)
+    ap.add_argument("--large-step-bytes", type=float, default=5e8,
+                    help="requests moving at least this much per step run one at a time (0: no limit)")
     ap.add_argument("--skip-sequential", action="store_true")
     ap.add_argument("--policies", default="f16_dev,as_requested",
                     help="comma-separated storage policies of the batched path")
@@ -410,7 +425,8 @@ def main(argv=None):
     out = {"requests": a.requests, "rate_per_s": a.rate, "seed": a.seed}
     for policy in a.policies.split(","):
         eng = GpuEngine(tuning=tuning)
-        rec_b, t_b = serve_batched(reqs, eng, budget_bytes=a.budget_gb * 1e9, tick=a.tick, store_policy=policy)
+        rec_b, t_b = serve_batched(reqs, eng, budget_bytes=a.budget_gb * 1e9, tick=a.tick, store_policy=policy,
+                                   large_step_bytes=a.large_step_bytes or None)
         out[f"batched_{policy}"] = dict(summarize(rec_b, t_b), peak_resident_gb=serve_batched.peak_bytes / 1e9,
                                         batched_launches=eng.batch.counters()["launches"])
         eng.close()

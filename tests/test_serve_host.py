@@ -95,3 +95,34 @@ def test_step_work_bound_admits_in_order():
     assert [r.rid for r in adm] == sorted(r.rid for r in recs)
     assert S.step_bytes(dict(lattice="rD3Q53-cubic", grid=(10, 10, 10)), "f32") == 1000 * 2 * 53 * 4
     assert S.step_bytes(dict(lattice="rD2Q17", grid=(10, 20)), "f16_dev") == 200 * 2 * 17 * 2
+
+
+def test_large_requests_run_one_at_a_time():
+    """With a large-request threshold, at most one large request steps at a time, small requests
+    behind a waiting large one are admitted past it, every request completes, and the large ones
+    start in their arrival order."""
+    reqs = _requests(n=40, rate=1e4)
+    sizes = sorted(S.step_bytes(r, "f32") for r in reqs)
+    large = sizes[len(sizes) * 3 // 4]
+    eng = S.FakeEngine(seconds_per_cell_step=2e-9)
+    live, peak = [], [0]
+    by_model = {}
+    orig_create, orig_finish = eng.create, eng.finish
+
+    def create(req, store, prepared=None, stream=None):     # a solve starts stepping
+        m, nb, q = orig_create(req, store, prepared, stream)
+        by_model[m] = S.step_bytes(req, store) >= large
+        live.append(m)
+        peak[0] = max(peak[0], sum(by_model[x] for x in live))
+        return m, nb, q
+
+    def finish(m):                                           # ... and stops stepping
+        live.remove(m)
+        return orig_finish(m)
+    eng.create, eng.finish = create, finish
+    recs, _ = S.serve_batched(reqs, eng, budget_bytes=1e12, tick=5, store_policy="f32", large_step_bytes=large)
+    assert sorted(r.rid for r in recs) == [r["rid"] for r in reqs]
+    assert peak[0] == 1
+    big = [r for r in sorted(recs, key=lambda r: r.admitted) if S.step_bytes(
+        dict(lattice=r.lattice, grid=next(q["grid"] for q in reqs if q["rid"] == r.rid)), "f32") >= large]
+    assert [r.rid for r in big] == sorted(r.rid for r in big)
