@@ -1,5 +1,6 @@
 // The extern "C" entry points of include/lbm_mrt.h: argument validation, device memory layout,
 // parameter marshalling and dispatch to the kernels. No exception crosses the ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -202,6 +203,37 @@ void make_tc_params(const lbm_model* m, TcParams* tp) {
       for (int i = 0; i < L->Q; ++i) tp->hrow[r][i] = float(L->Hh[size_t(r) * L->Q + i]);
       tp->ah[r] = float(-(high_rate(m, L->h_order[r]) - m->s_high) / L->Nh[r]);
     }
+  tp->ntiles = (m->ncells + 127) / 128;
+  tp->status = m->status;
+  tp->no_issue = m->tc_no_issue ? 1 : 0;
+  tp->wait_limit = m->tc_no_issue ? (1u << 10) : (1u << 22);
+}
+
+void make_tc32_params(const lbm_model* m, Tc32Params* tp) {
+  const lbm_lattice* L = m->lat;
+  const int Q = L->Q;
+  std::memset(tp, 0, sizeof(*tp));
+  // G_ij = sum_r a_r H_r(c_i) H_r(c_j), a_r = -(s_r - s_high) / N_r, in FP64
+  std::vector<double> G(size_t(Q) * Q, 0.0);
+  if (has_high_rates(m))
+    for (int r = 0; r < L->nhigh; ++r) {
+      const double a = -(high_rate(m, L->h_order[r]) - m->s_high) / L->Nh[r];
+      if (a == 0.0) continue;
+      const double* h = L->Hh + size_t(r) * Q;
+      for (int i = 0; i < Q; ++i)
+        for (int j = 0; j < Q; ++j) G[size_t(i) * Q + j] += a * h[i] * h[j];
+    }
+  // row i scaled by the power of two 2^-k_i that brings its max |G_ij| into [1, 2) (the high/low
+  // split then keeps about 22 bits of each row's large entries), undone in wg_i = 2^k_i w_i
+  for (int i = 0; i < Q; ++i) {
+    double gmax = 0.0;
+    for (int j = 0; j < Q; ++j) gmax = std::max(gmax, std::fabs(G[size_t(i) * Q + j]));
+    int e = 1;
+    if (gmax > 0.0) std::frexp(gmax, &e);  // gmax = m 2^e, m in [0.5, 1)
+    const int k = e - 1;
+    for (int j = 0; j < Q; ++j) tp->g[i][j] = float(std::ldexp(G[size_t(i) * Q + j], -k));
+    tp->wg[i] = float(std::ldexp(L->w[i], k));
+  }
   tp->ntiles = (m->ncells + 127) / 128;
   tp->status = m->status;
   tp->no_issue = m->tc_no_issue ? 1 : 0;

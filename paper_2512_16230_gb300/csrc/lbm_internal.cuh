@@ -162,6 +162,20 @@ struct TcParams {
   int no_issue;         // test hook: issue no matrix product (every wait then runs out)
 };
 
+// FP32 storage with one rate per order >= 4 on tcgen05 (k_step_tc32_high): the correction of the
+// higher rows, w_i sum_r a_r H_r(c_i) sum_j H_r(c_j) f_j, as one dense Q x Q operator applied to
+// the pre-collision populations: Delta_i = wg_i sum_j g_ij f_j, with
+// g_ij = 2^-k_i sum_r a_r H_r(c_i) H_r(c_j) (k_i brings the row's max |g_ij| into [1, 2)) and
+// wg_i = 2^k_i w_i.
+struct Tc32Params {
+  float g[kMaxQ][kMaxQ];
+  float wg[kMaxQ];
+  int ntiles;
+  int* status;
+  unsigned wait_limit;  // mbarrier polls before a wait is declared lost
+  int no_issue;         // test hook: issue no matrix product (every wait then runs out)
+};
+
 // Row-staged collide-stream kernel (16-bit storage, row_kernels.cuh): row buffers of kRowPitch
 // cells per population (the largest n_x; one cell per thread of a kRowThreads CTA), up to
 // kRowMaxStages buffers behind kRowBarBytes of mbarriers and counters.
@@ -386,6 +400,7 @@ void make_high_params(const lbm_model* m, HighParams<CT>* hp);
 // true when some row of order >= 4 relaxes with a rate other than s_high
 bool has_high_rates(const lbm_model* m);
 void make_tc_params(const lbm_model* m, TcParams* tp);
+void make_tc32_params(const lbm_model* m, Tc32Params* tp);
 int tc_grid(const lbm_model* m, int ntiles, const void* kernel, int ctas_per_sm, size_t smem_bytes);
 
 }  // namespace lbm

@@ -993,6 +993,7 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
   [[maybe_unused]] const bool tensor = collide_on && (m->tensor_cores || (m->tc_auto && high));
   [[maybe_unused]] const bool tensor32 = std::is_same<ST, float>::value && tensor && high;
   TcParams tp;
+  [[maybe_unused]] Tc32Params tp32;
   int tgrid = 0;
   size_t tsmem = 0;
   [[maybe_unused]] auto tc_kernel = [&](auto hi_tag, auto eq_tag) {
@@ -1019,11 +1020,11 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
   }
   if constexpr (std::is_same<ST, float>::value) {
     if (tensor32) {
-      make_tc_params(m, &tp);
+      make_tc32_params(m, &tp32);
       tsmem = sizeof(Tc32Smem<L>);
       const void* k = m->eq == LBM_NSE ? reinterpret_cast<const void*>(k_step_tc32_high<L, LBM_NSE>)
                                        : reinterpret_cast<const void*>(k_step_tc32_high<L, LBM_NCDE>);
-      tgrid = tc_grid(m, tp.ntiles, k, 3, tsmem);
+      tgrid = tc_grid(m, tp32.ntiles, k, Tc32Shape<L>::CTAS, tsmem);
     }
   }
   // 16-bit storage: the row-staged gather where it applies (or is forced), with the contractions
@@ -1076,9 +1077,9 @@ lbm_status launch_step_typed(lbm_model* m, int64_t nsteps, bool collide_on) {
     if constexpr (std::is_same<ST, float>::value) {
       if (tensor32) {
         if (m->eq == LBM_NSE)
-          k_step_tc32_high<L, LBM_NSE><<<tgrid, 128, tsmem, m->stream>>>(p, tp, fin, fout, phi);
+          k_step_tc32_high<L, LBM_NSE><<<tgrid, 128, tsmem, m->stream>>>(p, tp32, fin, fout, phi);
         else
-          k_step_tc32_high<L, LBM_NCDE><<<tgrid, 128, tsmem, m->stream>>>(p, tp, fin, fout, phi);
+          k_step_tc32_high<L, LBM_NCDE><<<tgrid, 128, tsmem, m->stream>>>(p, tp32, fin, fout, phi);
         done = true;
       }
     }

@@ -350,42 +350,35 @@ __global__ void __launch_bounds__(128, TcShape<L, HI>::CTAS)
 
 
 // FP32 storage with one rate per order >= 4: the low-order collision runs on the CUDA cores (the
-// reduced form of collide, exact FP32), and only the dense higher rows go to tcgen05. Their
-// operands are FP32 values, so each is scaled per cell (or per row of the table) by a power of
-// two and split into an FP16 high and low part, and a product takes three kind::f16 chains
-// into one accumulator: hi.hi + hi.lo + lo.hi (about 22 bits, like the 16-bit kernel's h):
-//   y (128 x NH)  = f (128 x Q) . H^T (Q x NH)   on the pre-collision populations
-//   Delta (128 x Q) = z (128 x NH) . H (NH x Q)   with z_r = a_r y_r, then f*_i += w_i Delta_i.
-// The forward product runs while the CUDA cores collide the same cell's populations.
+// reduced form of collide, exact FP32), and only the correction of the higher rows goes to
+// tcgen05. That correction is linear in the pre-collision populations,
+//   Delta_i = w_i sum_r a_r H_r(c_i) y_r,  y_r = sum_j H_r(c_j) f_j,
+// so it is applied as one dense Q x Q operator G_ij = sum_r a_r H_r(c_i) H_r(c_j) (built in FP64
+// with the rates): Delta (128 x Q) = f (128 x Q) . G^T (Q x Q), one product per 128-cell tile,
+// issued before the CUDA cores collide the same cells and read back after. Both operands are
+// FP32 values, so each is scaled by a power of two (G row by row on the host, the populations per
+// cell) and split into an FP16 high and low part; the product takes three kind::f16 chains into
+// one accumulator,
+// hi.hi + hi.lo + lo.hi (about 22 bits). One CTA-wide barrier per tile orders the operand stores
+// before the product and the previous tile's tensor-memory reads before it is overwritten.
 template <class L>
 struct Tc32Shape {
-  static constexpr int QP = (L::Q + 15) / 16 * 16;
-  static constexpr int NH = L::Q - L::R;
-  static constexpr int NHP = (NH + 15) / 16 * 16;
+  static constexpr int QP = (L::Q + 15) / 16 * 16;  // K and N of the product
+  static constexpr int CTAS = 4;                    // resident CTAs per SM
 };
 
 template <class L>
 struct __align__(1024) Tc32Smem {
   using S = Tc32Shape<L>;
-  union {
-    struct {
-      uint8_t hi[128 * S::QP * 2];  // scaled pre-collision f, high parts: row = cell, k = population
-      uint8_t lo[128 * S::QP * 2];
-    } a;
-    struct {
-      uint8_t hi[128 * S::NHP * 2];  // scaled z, high parts: row = cell, k = higher row
-      uint8_t lo[128 * S::NHP * 2];
-    } a2;  // reuses a once the forward product has completed
-  } u;
-  uint8_t b1_hi[S::NHP * S::QP * 2];  // row = higher row r, column = population i: H_r(c_i)
-  uint8_t b1_lo[S::NHP * S::QP * 2];
-  uint8_t b2_hi[S::QP * S::NHP * 2];  // row = population i, column = higher row r
-  uint8_t b2_lo[S::QP * S::NHP * 2];
+  uint8_t a_hi[128 * S::QP * 2];  // scaled pre-collision f, high parts: row = cell, k = population j
+  uint8_t a_lo[128 * S::QP * 2];
+  uint8_t b_hi[S::QP * S::QP * 2];  // row = population i, column = population j: g_ij
+  uint8_t b_lo[S::QP * S::QP * 2];
   uint64_t mbar;
   uint32_t tmem;
 };
 
-constexpr int kTc32Cols = 64;  // TMEM columns per CTA: D1 in [0, NHP), then D2 in [0, QP)
+constexpr int kTc32Cols = 64;  // TMEM columns per CTA: Delta in [0, QP)
 
 // power of two that brings max |v| into [1, 2) (1 for zero or out-of-range values)
 __device__ __forceinline__ float pow2_scale(float vmax) {
@@ -399,29 +392,25 @@ __device__ __forceinline__ void split16(float v, uint16_t& hi, uint16_t& lo) {
   lo = __half_as_ushort(__float2half_rn(v - __half2float(h)));
 }
 
-
 template <class L, int EQ>
-__global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<float> p, const TcParams tp,
-                                                           const float* __restrict__ fin, float* __restrict__ fout,
-                                                           float* __restrict__ phi) {
+__global__ void __launch_bounds__(128, Tc32Shape<L>::CTAS)
+    k_step_tc32_high(const StepParams<float> p, const Tc32Params tp, const float* __restrict__ fin,
+                     float* __restrict__ fout, float* __restrict__ phi) {
   using S = Tc32Shape<L>;
-  constexpr int Q = L::Q, QP = S::QP, NH = S::NH, NHP = S::NHP;
-  static_assert(QP <= kTc32Cols && NHP <= kTc32Cols, "TMEM column plan");
-  static_assert(NH <= kMaxHigh, "higher-row table");
+  constexpr int Q = L::Q, QP = S::QP;
+  static_assert(QP <= kTc32Cols, "TMEM column plan");
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   Tc32Smem<L>& sm = *reinterpret_cast<Tc32Smem<L>*>(tc_smem_raw);
   const int tid = threadIdx.x;
 
-  // operand tables (the higher rows are scaled to unit max on the host side of the set-up)
-  for (int idx = tid; idx < NHP * QP; idx += 128) {
-    const int r = idx / QP, i = idx % QP;
-    const float v = (r < NH && i < Q) ? tp.hrow[r][i] : 0.f;
+  // the operator, once per CTA (each row of g is scaled to unit max on the host)
+  for (int idx = tid; idx < QP * QP; idx += 128) {
+    const int i = idx / QP, j = idx % QP;
+    const float v = (i < Q && j < Q) ? tp.g[i][j] : 0.f;
     uint16_t hi, lo;
     split16(v, hi, lo);
-    *reinterpret_cast<uint16_t*>(sm.b1_hi + kmajor_off(r, i, QP)) = hi;
-    *reinterpret_cast<uint16_t*>(sm.b1_lo + kmajor_off(r, i, QP)) = lo;
-    *reinterpret_cast<uint16_t*>(sm.b2_hi + kmajor_off(i, r, NHP)) = hi;
-    *reinterpret_cast<uint16_t*>(sm.b2_lo + kmajor_off(i, r, NHP)) = lo;
+    *reinterpret_cast<uint16_t*>(sm.b_hi + kmajor_off(i, j, QP)) = hi;
+    *reinterpret_cast<uint16_t*>(sm.b_lo + kmajor_off(i, j, QP)) = lo;
   }
   if (tid == 0) {
     tc::mbar_init(&sm.mbar, 1);
@@ -437,12 +426,9 @@ __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<floa
   tc::fence_after_sync();
   const uint32_t tmem = sm.tmem;
   const uint32_t row_lane = uint32_t(tid & ~31) << 16;
-  const uint32_t ah_s = tc::smem_addr(sm.u.a.hi), al_s = tc::smem_addr(sm.u.a.lo);
-  const uint32_t zh_s = tc::smem_addr(sm.u.a2.hi), zl_s = tc::smem_addr(sm.u.a2.lo);
-  const uint32_t b1h_s = tc::smem_addr(sm.b1_hi), b1l_s = tc::smem_addr(sm.b1_lo);
-  const uint32_t b2h_s = tc::smem_addr(sm.b2_hi), b2l_s = tc::smem_addr(sm.b2_lo);
-  constexpr uint32_t idesc1 = tc::idesc_f16<false>(128, NHP);
-  constexpr uint32_t idesc2 = tc::idesc_f16<false>(128, QP);
+  const uint32_t ah_s = tc::smem_addr(sm.a_hi), al_s = tc::smem_addr(sm.a_lo);
+  const uint32_t bh_s = tc::smem_addr(sm.b_hi), bl_s = tc::smem_addr(sm.b_lo);
+  constexpr uint32_t idesc = tc::idesc_f16<false>(128, QP);
   const size_t N = size_t(p.ncells);
   uint32_t phase = 0;
   bool failed = false;
@@ -464,31 +450,39 @@ __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<floa
     } else {
       static_for<Q>([&](auto i) { f[decltype(i)::value] = 0.f; });
     }
-    // A = scaled pre-collision populations, high and low parts
+    // A = scaled pre-collision populations, high and low parts. The previous tile's product has
+    // completed (this thread saw its barrier phase) unless a wait ran out, and then no thread
+    // stores: one that did see the phase knows the product is done.
     float fmax = 0.f;
     static_for<Q>([&](auto i) { fmax = fmaxf(fmax, fabsf(f[decltype(i)::value])); });
     const float sa = pow2_scale(fmax);
-    static_for<QP / 8>([&](auto c) {
-      constexpr int C = decltype(c)::value;
-      uint32_t wh[4], wl[4];
-      static_for<4>([&](auto j) {
-        constexpr int I0 = 8 * C + 2 * decltype(j)::value;
-        const float a = I0 < Q ? f[I0 < Q ? I0 : 0] * sa : 0.f;
-        const float b = I0 + 1 < Q ? f[I0 + 1 < Q ? I0 + 1 : 0] * sa : 0.f;
-        split16x2<__half>(a, b, wh[decltype(j)::value], wl[decltype(j)::value]);
+    if (!failed) {
+      static_for<QP / 8>([&](auto c) {
+        constexpr int C = decltype(c)::value;
+        uint32_t wh[4], wl[4];
+        static_for<4>([&](auto j) {
+          constexpr int I0 = 8 * C + 2 * decltype(j)::value;
+          const float a = I0 < Q ? f[I0 < Q ? I0 : 0] * sa : 0.f;
+          const float b = I0 + 1 < Q ? f[I0 + 1 < Q ? I0 + 1 : 0] * sa : 0.f;
+          split16x2<__half>(a, b, wh[decltype(j)::value], wl[decltype(j)::value]);
+        });
+        *reinterpret_cast<uint4*>(sm.a_hi + kmajor_off(tid, 8 * C, QP)) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        *reinterpret_cast<uint4*>(sm.a_lo + kmajor_off(tid, 8 * C, QP)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
       });
-      *reinterpret_cast<uint4*>(sm.u.a.hi + kmajor_off(tid, 8 * C, QP)) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-      *reinterpret_cast<uint4*>(sm.u.a.lo + kmajor_off(tid, 8 * C, QP)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-    });
+    }
     tc::fence_async_smem();
-    __syncthreads();
+    tc::fence_before_sync();  // this thread's reads of the previous tile's Delta are complete
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
     if (tid == 0 && !tp.no_issue) {
-      tc::fence_after_sync();
-      // y = A_hi B_hi + A_hi B_lo + A_lo B_hi
+      // Delta = A_hi G_hi + A_hi G_lo + A_lo G_hi
       static_for<3 * (QP / 16)>([&](auto q) {
         constexpr int Kc = decltype(q)::value % (QP / 16), part = decltype(q)::value / (QP / 16);
-        const uint32_t a = (part == 2 ? al_s : ah_s) + Kc * 256, b = (part == 1 ? b1l_s : b1h_s) + Kc * 256;
-        tc::mma_f16(tmem, tc::smem_desc(a, 128, QP * 16), tc::smem_desc(b, 128, QP * 16), idesc1,
+        const uint32_t a = (part == 2 ? al_s : ah_s) + Kc * 256, b = (part == 1 ? bl_s : bh_s) + Kc * 256;
+        tc::mma_f16(tmem, tc::smem_desc(a, 128, QP * 16), tc::smem_desc(b, 128, QP * 16), idesc,
                     decltype(q)::value > 0 ? 1u : 0u);
       });
       tc::commit(&sm.mbar);
@@ -510,64 +504,15 @@ __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<floa
     if constexpr (AG && EQ == LBM_NSE) {
       if (live && p.grad_on) p.rho_out[cell] = phi_now;
     }
-    bool ok = tc::mbar_wait_bounded(&sm.mbar, phase, tp.wait_limit);
+    const bool ok = tc::mbar_wait_bounded(&sm.mbar, phase, tp.wait_limit);
     phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
+    if (!ok) {
+      failed = true;  // the CTA stops at the next barrier; this tile's populations are not written
+      continue;
     }
     tc::fence_after_sync();
-    // z_r = a_r y_r, y = D1 / sa (sa a power of two, so the reciprocal is exact); then its own
-    // scale and split
-    const float inv_sa = 1.f / sa;
-    float zr[NH];
-    static_for<NHP / 16>([&](auto c) {
-      constexpr int C = decltype(c)::value;
-      float v[16];
-      tc::ld16(tmem + row_lane + 16 * C, v);
-      tc::wait_ld();
-      static_for<16>([&](auto j) {
-        constexpr int K = 16 * C + decltype(j)::value;
-        if constexpr (K < NH) zr[K] = tp.ah[K] * (v[decltype(j)::value] * inv_sa);
-      });
-    });
-    float zmax = 0.f;
-    static_for<NH>([&](auto k) { zmax = fmaxf(zmax, fabsf(zr[decltype(k)::value])); });
-    const float sz = live ? pow2_scale(zmax) : 1.f;
-    static_for<NHP / 8>([&](auto c) {
-      constexpr int C = decltype(c)::value;
-      uint32_t wh[4], wl[4];
-      static_for<4>([&](auto j) {
-        constexpr int K0 = 8 * C + 2 * decltype(j)::value;
-        const float a = (K0 < NH && live) ? zr[K0 < NH ? K0 : 0] * sz : 0.f;
-        const float b = (K0 + 1 < NH && live) ? zr[K0 + 1 < NH ? K0 + 1 : 0] * sz : 0.f;
-        split16x2<__half>(a, b, wh[decltype(j)::value], wl[decltype(j)::value]);
-      });
-      *reinterpret_cast<uint4*>(sm.u.a2.hi + kmajor_off(tid, 8 * C, NHP)) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-      *reinterpret_cast<uint4*>(sm.u.a2.lo + kmajor_off(tid, 8 * C, NHP)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-    });
-    tc::fence_before_sync();
-    tc::fence_async_smem();
-    __syncthreads();
-    if (tid == 0 && !tp.no_issue) {
-      tc::fence_after_sync();
-      // Delta = Z_hi Bt_hi + Z_hi Bt_lo + Z_lo Bt_hi
-      static_for<3 * (NHP / 16)>([&](auto q) {
-        constexpr int Kc = decltype(q)::value % (NHP / 16), part = decltype(q)::value / (NHP / 16);
-        const uint32_t a = (part == 2 ? zl_s : zh_s) + Kc * 256, b = (part == 1 ? b2l_s : b2h_s) + Kc * 256;
-        tc::mma_f16(tmem, tc::smem_desc(a, 128, NHP * 16), tc::smem_desc(b, 128, NHP * 16), idesc2,
-                    decltype(q)::value > 0 ? 1u : 0u);
-      });
-      tc::commit(&sm.mbar);
-    }
-    ok = tc::mbar_wait_bounded(&sm.mbar, phase, tp.wait_limit);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    tc::fence_after_sync();
-    const float inv = 1.f / sz;
+    // f*_i = collided f_i + w_i Delta_i, Delta = D / sa (sa a power of two: exact reciprocal)
+    const float inv = 1.f / sa;
     static_for<QP / 16>([&](auto c) {
       constexpr int C = decltype(c)::value;
       float v[16];
@@ -576,20 +521,21 @@ __global__ void __launch_bounds__(128, 3) k_step_tc32_high(const StepParams<floa
       static_for<16>([&](auto j) {
         constexpr int I = 16 * C + decltype(j)::value;
         if constexpr (I < Q) {
-          if (live) k1_store(fout + size_t(I) * N + cell, fmaf(p.w[I], v[decltype(j)::value] * inv, f[I]));
+          if (live) k1_store(fout + size_t(I) * N + cell, fmaf(tp.wg[I], v[decltype(j)::value] * inv, f[I]));
         }
       });
     });
-    tc::fence_before_sync();
-    __syncthreads();
   }
+  // a wait that ran out on the CTA's last tile: every thread learns of it here
+  tc::fence_before_sync();
+  failed = __syncthreads_or(failed);
+  tc::fence_after_sync();
   if (failed) {
-    if (!tp.no_issue) tc::mbar_wait_bounded(&sm.mbar, phase ^ 1u, tp.wait_limit);  // as in k_step_tc
+    // the product in flight, if any, completes before its tensor memory is freed (bounded again)
+    if (!tp.no_issue) tc::mbar_wait_bounded(&sm.mbar, phase ^ 1u, tp.wait_limit);
     if (tid == 0) atomicExch(tp.status, 1);
   }
-  tc::fence_before_sync();
   __syncthreads();
-  tc::fence_after_sync();
   if (tid < 32) tc::dealloc(tmem, kTc32Cols);
 }
 

@@ -98,6 +98,9 @@ def test_tensor_core_taylor_green_copy(store, bound, rho_bound):
     assert er <= rho_bound
 
 
+HIGH_RATES = {4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25}
+
+
 def test_tensor_core_timeout_is_reported():
     """The bounded waits: with the test hook no matrix product is issued, every CTA's wait runs
     out, the status word reports LBM_ERR_TIMEOUT at the next synchronisation, and the model (and
@@ -119,15 +122,33 @@ def test_tensor_core_timeout_is_reported():
     assert np.allclose(rho, 1.0, atol=1e-3) and np.abs(u).max() < 1e-3
 
 
+def test_tensor_core_timeout_is_reported_fp32_high_rates():
+    """The same hook on the FP32 kernel with per-order rates (the higher rows' operator on
+    tcgen05): every wait runs out, LBM_ERR_TIMEOUT is reported, and the model steps correctly
+    afterwards (rest state, per-order rates: a fixed point)."""
+    from paper_2512_16230_gb300 import lbm
+    spec = W.LATTICES["rD3Q33"]
+    n = (16, 12, 10)
+    gm = gpu_model(spec, "nse", n, np.ones(spec.R), s_high=1.2, store="f32", s_orders=HIGH_RATES)
+    gm.init_fields(*I.rest_state(n, 3))
+    gm.set_tensor_cores(2)
+    gm.step(1)
+    with pytest.raises(lbm.LBMError, match="LBM_ERR_TIMEOUT"):
+        gm.synchronize()
+    gm.synchronize()
+    gm.set_tensor_cores(1)
+    gm.init_fields(*I.rest_state(n, 3))
+    gm.step(3)
+    rho, u = gm.read_fields()
+    assert np.allclose(rho, 1.0, atol=1e-6) and np.abs(u).max() < 1e-6
+
+
 def test_tensor_cores_not_for_fp64():
     from paper_2512_16230_gb300 import lbm
     spec = W.LATTICES["rD2Q13"]
     gm = gpu_model(spec, "nse", (8, 8), np.ones(spec.R), store="f64")
     with pytest.raises(lbm.LBMError, match="LBM_ERR_ARG"):
         gm.set_tensor_cores(1)
-
-
-HIGH_RATES = {4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25}
 
 
 @pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
