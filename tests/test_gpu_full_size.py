@@ -133,6 +133,74 @@ def test_config4_full_size_row_gather_is_bitwise_thread_gather(store):
     torch.cuda.empty_cache()
 
 
+HIGH_RATES = {4: 0.8, 5: 1.35, 6: 1.6, 7: 0.9, 8: 1.25}
+
+
+def _wave_populations(n, w, seed, amp=0.05):
+    """Non-equilibrium populations on the whole grid, (Q, nz, ny, nx) float64:
+    f_i(x) = w_i (1 + amp sin(2 pi sum_a k_ia x_a / n_a + phase_i)) with seeded integer wave vectors
+    and phases per population, so that every moment order, the rows of order >= 4 included, is
+    excited and varies from cell to cell."""
+    rng = np.random.default_rng(seed)
+    Q = len(w)
+    k = rng.integers(-3, 4, size=(Q, 3))
+    ph = rng.uniform(0.0, 2.0 * np.pi, Q)
+    x = [2.0 * np.pi * np.arange(n[a]) / n[a] for a in range(3)]
+    f = np.empty((Q, n[2], n[1], n[0]))
+    for i in range(Q):
+        arg = (k[i, 0] * x[0][None, None, :] + k[i, 1] * x[1][None, :, None] + k[i, 2] * x[2][:, None, None]
+               + ph[i])
+        f[i] = w[i] * (1.0 + amp * np.sin(arg))
+    return f
+
+
+@pytest.mark.parametrize("store,tol", [("f32", 1e-5), ("f16_dev", 4 * 2.0 ** -11)])
+def test_config3_high_order_rates_full_size_sampled(store, tol):
+    """The per-order-rate variant of the benchmark solve at its full size (rD3Q53, 256 x 256 x 192),
+    in the launch the benchmark times (FP32: the CUDA-core reduced form with the higher rows'
+    operator on tcgen05; FP16 deviations: the row-staged tcgen05 kernel with the higher rows): one
+    step from seeded non-equilibrium populations (every order excited), all 53 populations at 72
+    sampled cells against the oracle's full Q x Q collision Lambda = H^-1 S H of the source cells
+    x - e_i, within the FP32 bound (FP32) or 4 units of FP16 on the deviations (FP16)."""
+    import torch
+    wl = W.taylor_green_3d(store=store)
+    spec = wl.lattice
+    lat = oracle_lattice(spec)
+    f0 = _wave_populations(wl.n, lat.w, seed=31)
+    w4 = lat.w[:, None, None, None]
+    if store == "f32":
+        f0 = f0.astype(np.float32).astype(np.float64)
+    else:
+        f0 = w4 + (f0 - w4).astype(np.float16).astype(np.float64)
+    cells = _sample_cells(wl.n, 64, seed=9)
+    gm = gpu_model(spec, wl.eq, wl.n, wl.s, wl.s_high, store=store, s_orders=HIGH_RATES)
+    gm.set_populations(f0)
+    gm.step(1)
+    out = torch.empty((gm.Q,) + tuple(reversed(wl.n)), dtype=torch.float64, device="cuda")
+    gm.get_populations(out)
+    gm.synchronize()
+    idx = tuple(torch.tensor([x[a] for x in cells], device="cuda") for a in (2, 1, 0))
+    got = out[(slice(None),) + idx].cpu().numpy()
+    del out
+    gm.close()
+    torch.cuda.empty_cache()
+    # the oracle: the full collision of every source cell x - e_i, on a one-dimensional list of cells
+    Q, n = lat.Q, wl.n
+    src = [tuple((x[a] - int(lat.e[i, a])) % n[a] for a in range(3)) for x in cells for i in range(Q)]
+    fs = f0[:, [c[2] for c in src], [c[1] for c in src], [c[0] for c in src]]
+    del f0
+    M = len(src)
+    om = oracle_model(spec, wl.eq, (M, 1, 1), wl.s, wl.s_high, s_orders=HIGH_RATES)
+    om.set_populations(fs.reshape(Q, 1, 1, M))
+    ft = om.collide().reshape(Q, M)
+    want = np.array([[ft[i, s * Q + i] for s in range(len(cells))] for i in range(Q)])
+    if store == "f32":
+        assert rel_l2(got, want) <= tol
+    else:
+        w = lat.w[:, None]
+        assert rel_l2(got - w, want - w) <= tol
+
+
 @pytest.mark.parametrize("store", ["f32", "f64"])
 def test_config2_full_size_first_step_sampled(store):
     """rD2Q13 nonlinear CDE hill, 1024 x 768, FP32 and FP64: one step from the seeded fields at
