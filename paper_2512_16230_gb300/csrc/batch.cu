@@ -51,6 +51,11 @@ struct lbm_batch {
   // reach a larger share of HBM bandwidth than the work-list kernel
   std::vector<lbm_model*> solos;
   int64_t solo_cells = int64_t(1) << 19;
+  // the solos' launches run on a second stream, forked from the batch stream before the
+  // work-list launches of a step call and joined back after them, so that a large solve's
+  // bandwidth-bound steps and the small solves' latency-bound ones share the SMs
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   std::map<std::tuple<int, int, int>, int> tile;  // (kind, store, eq) -> cells per tile
   std::map<std::tuple<int, int, int>, int> per_sm;  // (kind, store, eq) -> resident blocks per SM (cap)
   bool dirty = true;
@@ -439,21 +444,42 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
   const bool use_graph = b->graph != nullptr;
   const int64_t chunks = use_graph ? nsteps / kChunk : 0;
   const int rem = int(nsteps - chunks * kChunk);
-  for (int64_t c = 0; c < chunks; ++c) {
-    cudaError_t err = cudaGraphLaunch(b->graph, b->stream);
-    if (err != cudaSuccess) return cuda_error(err, "batch graph launch");
+  // the solos first, on the side stream (ordered after everything queued on the batch stream)
+  const bool forked = !b->solos.empty();
+  if (forked) {
+    cudaError_t err = cudaSuccess;
+    if (!b->side) err = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (err == cudaSuccess && !b->fork) err = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (err == cudaSuccess && !b->join) err = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventRecord(b->fork, b->stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(b->side, b->fork, 0);
+    if (err != cudaSuccess) return cuda_error(err, "batch side stream");
   }
-  for (int s = 0; s < rem; ++s)
-    for (auto& gh : b->groups) {
-      lbm_status st = launch_group(gh, s & 1, b->stream);
-      if (st != LBM_OK) return st;
-    }
-  for (lbm_model* m : b->solos) {  // on the batch's stream, like the work-list launches
-    lbm_status st = dispatch_batch_kind(m->lat->kind, [&](auto kc) {
+  lbm_status st = LBM_OK;
+  for (lbm_model* m : b->solos) {
+    const cudaStream_t own = m->stream;  // the batch stream while the model is a member
+    m->stream = b->side;
+    st = dispatch_batch_kind(m->lat->kind, [&](auto kc) {
       return Launch<decltype(kc)::value>::step(m, nsteps, true);
     });
-    if (st != LBM_OK) return st;
+    m->stream = own;
+    if (st != LBM_OK) break;
   }
+  for (int64_t c = 0; c < chunks && st == LBM_OK; ++c) {
+    cudaError_t err = cudaGraphLaunch(b->graph, b->stream);
+    if (err != cudaSuccess) st = cuda_error(err, "batch graph launch");
+  }
+  for (int s = 0; s < rem && st == LBM_OK; ++s)
+    for (auto& gh : b->groups) {
+      st = launch_group(gh, s & 1, b->stream);
+      if (st != LBM_OK) break;
+    }
+  if (forked) {  // join, also after a failed launch: nothing queued on the side stream is left behind
+    cudaError_t err = cudaEventRecord(b->join, b->side);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(b->stream, b->join, 0);
+    if (err != cudaSuccess && st == LBM_OK) st = cuda_error(err, "batch side stream");
+  }
+  if (st != LBM_OK) return st;
   if (rem & 1) {
     // every model's current buffer flipped: swap the descriptors' buffers (the graph reads them)
     for (auto& gh : b->groups) {
@@ -467,8 +493,8 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
           std::swap(gh.desc[j].rho_out[0], gh.desc[j].rho_out[1]);
         }
       }
-      lbm_status st = upload_desc(b, gh);
-      if (st != LBM_OK) return st;
+      const lbm_status su = upload_desc(b, gh);
+      if (su != LBM_OK) return su;
     }
   }
   for (auto& gh : b->groups)  // (the single-solve launcher counts the solos' steps itself)
@@ -512,9 +538,13 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
     m->stream = m->own_stream;
     m->batch = nullptr;
   }
+  if (b->side) cudaStreamSynchronize(b->side);
   free_groups(b);
   reap_graphs(b, true);
   free_buffers(b);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  if (b->side) cudaStreamDestroy(b->side);
   if (b->owns_stream) cudaStreamDestroy(b->stream);
   delete b;
   return LBM_OK;
