@@ -56,6 +56,13 @@ struct lbm_batch {
   // bandwidth-bound steps and the small solves' latency-bound ones share the SMs
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // one stream per group: a step call forks them from the batch stream, each runs its group's
+  // steps as a chain, and the batch stream joins them all, so that groups too small to fill the
+  // GPU (the 2D solves of a serving mix) overlap instead of queueing one launch after another.
+  // The events of a graph capture are separate from those of the launches outside one.
+  std::vector<cudaStream_t> lanes;
+  std::vector<cudaEvent_t> lane_join, cap_join;
+  cudaEvent_t lane_fork = nullptr, cap_fork = nullptr;
   std::map<std::tuple<int, int, int>, int> tile;  // (kind, store, eq) -> cells per tile
   std::map<std::tuple<int, int, int>, int> per_sm;  // (kind, store, eq) -> resident blocks per SM (cap)
   bool dirty = true;
@@ -209,6 +216,60 @@ lbm_status launch_group(const GroupHost& gh, int parity, cudaStream_t stream) {
   });
 }
 
+// streams and events for the group lanes (created once, grown with the group count)
+lbm_status ensure_lanes(lbm_batch* b) {
+  cudaError_t err = cudaSuccess;
+  if (!b->lane_fork) err = cudaEventCreateWithFlags(&b->lane_fork, cudaEventDisableTiming);
+  if (err == cudaSuccess && !b->cap_fork) err = cudaEventCreateWithFlags(&b->cap_fork, cudaEventDisableTiming);
+  while (err == cudaSuccess && b->lanes.size() < b->groups.size()) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e2, cudaEventDisableTiming);
+    if (err != cudaSuccess) {
+      if (st) cudaStreamDestroy(st);
+      if (e1) cudaEventDestroy(e1);
+      break;
+    }
+    b->lanes.push_back(st);
+    b->lane_join.push_back(e1);
+    b->cap_join.push_back(e2);
+  }
+  return err == cudaSuccess ? LBM_OK : cuda_error(err, "batch group streams");
+}
+
+// nsteps steps of every group, as one chain per group on its lane: forked from `main` and joined
+// back into it (inside a graph capture of `main` too, with the capture's own events). Step s of
+// the call reads the buffers of parity s & 1. One group runs on `main` itself.
+lbm_status launch_groups(lbm_batch* b, int nsteps, cudaStream_t main, bool capturing) {
+  if (b->groups.size() == 1) {
+    for (int s = 0; s < nsteps; ++s) {
+      lbm_status st = launch_group(b->groups[0], s & 1, main);
+      if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+  }
+  lbm_status st = ensure_lanes(b);
+  if (st != LBM_OK) return st;
+  cudaEvent_t fork = capturing ? b->cap_fork : b->lane_fork;
+  cudaError_t err = cudaEventRecord(fork, main);
+  if (err != cudaSuccess) return cuda_error(err, "batch group fork");
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    cudaStream_t lane = b->lanes[k];
+    err = cudaStreamWaitEvent(lane, fork, 0);
+    if (err != cudaSuccess) return cuda_error(err, "batch group fork");
+    for (int s = 0; s < nsteps && st == LBM_OK; ++s) st = launch_group(b->groups[k], s & 1, lane);
+    // joined even after a failed launch, so that nothing on the lane is left outside the batch stream
+    cudaEvent_t done = capturing ? b->cap_join[k] : b->lane_join[k];
+    err = cudaEventRecord(done, lane);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(main, done, 0);
+    if (err != cudaSuccess) return cuda_error(err, "batch group join");
+    if (st != LBM_OK) return st;
+  }
+  return LBM_OK;
+}
+
 lbm_status upload_desc(lbm_batch* b, GroupHost& gh) {
   cudaError_t err = cudaMemcpyAsync(gh.g.d_desc, gh.desc.data(), gh.desc.size() * sizeof(SolveDesc<float>),
                                     cudaMemcpyHostToDevice, b->stream);
@@ -302,13 +363,14 @@ lbm_status rebuild(lbm_batch* b) {
 lbm_status capture(lbm_batch* b) {
   drop_graph(b);
   if (!b->groups.empty()) {
+    if (b->groups.size() > 1) {  // streams and events are created before the capture begins
+      lbm_status st = ensure_lanes(b);
+      if (st != LBM_OK) return st;
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t err = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (err != cudaSuccess) return cuda_error(err, "graph capture (the batch needs a non-legacy stream)");
-    lbm_status st = LBM_OK;
-    for (int s = 0; s < kChunk && st == LBM_OK; ++s)
-      for (auto& gh : b->groups)
-        if (st == LBM_OK) st = launch_group(gh, s & 1, b->stream);
+    const lbm_status st = launch_groups(b, kChunk, b->stream, true);
     err = cudaStreamEndCapture(b->stream, &graph);
     if (st != LBM_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -469,11 +531,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     cudaError_t err = cudaGraphLaunch(b->graph, b->stream);
     if (err != cudaSuccess) st = cuda_error(err, "batch graph launch");
   }
-  for (int s = 0; s < rem && st == LBM_OK; ++s)
-    for (auto& gh : b->groups) {
-      st = launch_group(gh, s & 1, b->stream);
-      if (st != LBM_OK) break;
-    }
+  if (rem > 0 && st == LBM_OK && !b->groups.empty()) st = launch_groups(b, rem, b->stream, false);
   if (forked) {  // join, also after a failed launch: nothing queued on the side stream is left behind
     cudaError_t err = cudaEventRecord(b->join, b->side);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(b->stream, b->join, 0);
@@ -539,9 +597,17 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
     m->batch = nullptr;
   }
   if (b->side) cudaStreamSynchronize(b->side);
+  for (cudaStream_t lane : b->lanes) cudaStreamSynchronize(lane);
   free_groups(b);
   reap_graphs(b, true);
   free_buffers(b);
+  for (size_t k = 0; k < b->lanes.size(); ++k) {
+    cudaStreamDestroy(b->lanes[k]);
+    cudaEventDestroy(b->lane_join[k]);
+    cudaEventDestroy(b->cap_join[k]);
+  }
+  if (b->lane_fork) cudaEventDestroy(b->lane_fork);
+  if (b->cap_fork) cudaEventDestroy(b->cap_fork);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->join) cudaEventDestroy(b->join);
   if (b->side) cudaStreamDestroy(b->side);
