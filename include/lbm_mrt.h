@@ -395,17 +395,23 @@ lbm_status lbm_batch_set_tile(lbm_batch* b, lbm_kind kind, lbm_dtype store, lbm_
 lbm_status lbm_batch_set_blocks_per_sm(lbm_batch* b, lbm_kind kind, lbm_dtype store, lbm_eq eq, int blocks);
 
 /* Members of at least `cells` cells (default 2^19) run on the single-solve kernels of
- * lbm_model_step (one launch per step each, on the batch's stream) instead of the work-list
- * kernel: a grid that large fills the GPU alone, and the single-solve kernels reach a larger share
- * of HBM bandwidth. The results are bitwise the same either way. 0 keeps every member in the
- * work-lists. Errors: LBM_ERR_ARG for a negative threshold. */
+ * lbm_model_step (one launch per step each) instead of the work-list kernel: a grid that large
+ * fills the GPU alone, and the single-solve kernels reach a larger share of HBM bandwidth. The
+ * results are bitwise the same either way. 0 keeps every member in the work-lists. Errors:
+ * LBM_ERR_ARG for a negative threshold. */
 lbm_status lbm_batch_set_solo_threshold(lbm_batch* b, int64_t cells);
 
-/* Advance every member by nsteps time steps, asynchronously on the batch's stream. Each step is
- * one persistent launch per group over a tile work-list that covers every cell of every solve of
- * the group (the same per-cell collide-stream arithmetic as lbm_model_step); groups of 8 steps are
- * replayed from a captured CUDA graph. The first call after a membership or parameter change
- * rebuilds the work-lists and the graph (it allocates small device buffers and synchronizes). */
+/* Advance every member by nsteps time steps, asynchronously with respect to the host and in order
+ * on the batch's stream. Each step is one persistent launch per group over a tile work-list that
+ * covers every cell of every solve of the group (the same per-cell collide-stream arithmetic as
+ * lbm_model_step), and one single-solve launch per member above the solo threshold. The work of a
+ * call is forked from the batch's stream onto internal streams (one per group, one for the
+ * single-solve members), so that groups and large members overlap, and joined back into it before
+ * the call returns: anything enqueued on the batch's stream afterwards (an event, a copy, a
+ * removal) comes after every member's steps. Chunks of 8 steps are replayed from a captured CUDA
+ * graph (one branch per group) once membership has been stable for a whole call. The first call
+ * after a membership or parameter change rebuilds the work-lists (a work-list buffer that must grow
+ * is reallocated, and cudaFree waits for the device). */
 lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
 
 /* Steps taken, batched launches issued, current number of groups and of tiles. */
