@@ -758,7 +758,11 @@ def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300, lar
         "batched": dict(b, storage="policy f16_dev: FP16 deviations where the class and run length keep the "
                                    "u (phi) error <= 1e-3, FP32 otherwise",
                   admission="arrival order; requests moving >= large_step_bytes per step one at a time, smaller "
-                            "ones admitted past a waiting large one", large_step_bytes=large_step_bytes),
+                            "ones admitted past a waiting large one", large_step_bytes=large_step_bytes,
+                  engine="one persistent work-list launch per (lattice, storage, equation) group and step, each "
+                         "group on its own stream; solves of >= solo_cells cells on the single-solve kernels on "
+                         "another stream; all forked from and joined back into the batch stream per call; "
+                         "8-step chunks replayed from a CUDA graph"),
         "sequential_fp32": q,
         "speedup_solves_per_s": b["solves_per_s"] / q["solves_per_s"],
         "sustained": {"requests": sustained_requests, "seed": seed + 1, "arrival_rate_per_s": rate2,
