@@ -563,6 +563,7 @@ def bench_ours(args):
         for key in ("extensions", "other_configs", "variants", "serving"):   # the long extras last
             if key in line:
                 line[key] = line.pop(key)
+        line["summary"] = _summary(line)   # a compact digest of the extras, at the very end
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -772,6 +773,33 @@ def run_serving(n_requests, rate_per_s=20.0, seed=0, sustained_requests=300, lar
                        group_ms_best_worst={g: [round(v[0], 4), round(v[1], 4)] for g, v in groups.items()},
                        solo_ms={k: round(v, 4) for k, v in tuning["ms_per_step"].items() if k.startswith("solo_cells=")}),
     }
+
+
+def _summary(line):
+    """The figures of the long extras that matter most, rounded: the per-step time and HBM
+    fraction (algorithmic bytes over the measured copy bandwidth) of each kernel variant on the
+    benchmark solve, and the serving comparison (config 5)."""
+    var = {k: v for k, v in line.get("variants", {}).items() if isinstance(v, dict) and "ms_per_step" in v}
+    out = {"variants_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in var.items()},
+           "variants_hbm_frac": {k: round(v["hbm_frac"], 3) for k, v in var.items() if "hbm_frac" in v}}
+    sv = line.get("serving")
+    if sv and "batched" in sv:
+        b, q = sv["batched"], sv["sequential_fp32"]
+        out["serving"] = {
+            "requests": sv["requests"],
+            "solves_per_s": [round(b["solves_per_s"], 3), round(q["solves_per_s"], 3)],
+            "p50_s": [round(b["latency_p50_s"], 3), round(q["latency_p50_s"], 3)],
+            "p99_s": [round(b["latency_p99_s"], 3), round(q["latency_p99_s"], 3)],
+            "order": "batched (size-aware admission, f16_dev policy), plain FP32 one at a time",
+        }
+        st = sv.get("sustained")
+        if st:
+            out["serving"]["sustained"] = {
+                "arrival_rate_per_s": round(st["arrival_rate_per_s"], 3),
+                "p50_s": [round(st["batched"]["latency_p50_s"], 3), round(st["sequential_fp32"]["latency_p50_s"], 3)],
+                "p99_s": [round(st["batched"]["latency_p99_s"], 3), round(st["sequential_fp32"]["latency_p99_s"], 3)],
+            }
+    return out
 
 
 def main(argv=None):
