@@ -65,8 +65,9 @@ def _compare(a, b, store):
 def test_batch_solos_equal_single_solve_path():
     """Members above the solo threshold run on the single-solve kernels inside the batch (here a
     low threshold makes the larger half of the mix solos, 16-bit storage with n_x % 8 == 0 on the
-    row-staged kernel among them): every member is bitwise the same as the same solve alone, and
-    the step counters count each solo step once."""
+    row-staged kernel among them; they step on their own stream beside the groups' streams): every
+    member is bitwise the same as the same solve alone, and the step counters count each solo step
+    once."""
     from paper_2512_16230_gb300 import lbm
     mix = MIX + [("rD3Q53", "nse", (16, 10, 9), "f16_dev"), ("rD2Q17", "ncde", (24, 20), "bf16_dev")]
     cache = {}
@@ -77,10 +78,11 @@ def test_batch_solos_equal_single_solve_path():
     for m in batched:
         b.add(m)
     b.step(13)
+    b.step(11)          # stable membership: the groups from the captured graph, the solos beside them
     b.synchronize()
     for m in alone:
-        m.step(13)
-    assert [m.counters()[0] for m in batched] == [13] * len(mix)
+        m.step(24)
+    assert [m.counters()[0] for m in batched] == [24] * len(mix)
     exact = [_compare(x, y, spec[3]) for x, y, spec in zip(alone, batched, mix)]
     assert all(exact)
     b.close()
@@ -94,12 +96,13 @@ def test_batch_equals_single_solve_path():
     b = lbm.Batch(64)
     for m in batched:
         b.add(m)
-    b.step(13)          # one 8-step graph replay, then 5 direct launches (odd: buffers swap)
+    b.step(13)          # the call after a change: direct launches (13, odd: the buffers swap)
+    b.step(19)          # membership stable: captured graph (one branch per group) twice, then 3 direct
     b.synchronize()
     for m in alone:
-        m.step(13)
+        m.step(32)
     c = b.counters()
-    assert c["groups"] == len({(name, st) for name, _, _, st in MIX}) and c["steps"] == 13
+    assert c["groups"] == len({(name, st) for name, _, _, st in MIX}) and c["steps"] == 32
     exact = [_compare(x, y, spec[3]) for x, y, spec in zip(alone, batched, MIX)]
     assert all(exact)   # the same per-cell code: bitwise the same fields
     # membership changes: drop two solves, add a fresh one, keep stepping
