@@ -39,7 +39,8 @@ Q = 53
 # DRAM traffic of the benchmark kernel per cell update, from an ncu capture of the same workload on
 # 256 x 256 x 96 cells (half the grid: 2.7 GB on the device), scaled to the benchmark grid by cells
 PROFILE = os.path.join(ROOT, "profiles", "k_step_rd3q53_f32_tgv3d_256x256x96.md")
-# the sources the benchmark kernel is compiled from (the traffic figure is void once one changes)
+# the sources the benchmark kernel is compiled from (the traffic figure is void once their code,
+# comments aside, changes)
 KERNEL_SOURCES = ("include/lbm_mrt.h", "paper_2512_16230_gb300/csrc/lattices.cuh",
                   "paper_2512_16230_gb300/csrc/lbm_internal.cuh", "paper_2512_16230_gb300/csrc/mrt_kernels.cuh",
                   "paper_2512_16230_gb300/csrc/tc_kernels.cuh", "paper_2512_16230_gb300/csrc/tcgen05.cuh",
@@ -77,11 +78,19 @@ def _config(extra=None, grid=GRID, store="f32"):
     return cfg
 
 
+def _code_only(text):
+    """C/C++ source without its comments and with every run of whitespace as one space, so that
+    an edit of the documentation alone leaves the hash of the compiled code unchanged."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def _source_sha():
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(f.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

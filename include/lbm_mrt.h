@@ -210,10 +210,13 @@ lbm_status lbm_model_set_high_rates(lbm_model* m, const double* s_order, int n_o
  * of 128 cells with the integer monomial table mono_k(e_i) as the other operand (exact in 16 bits);
  * the per-cell moment-space arithmetic stays in FP32. enable = 0 selects the CUDA-core kernel.
  * With distinct rates for the orders >= 4 (lbm_model_set_high_rates) the higher rows join both
- * products as dense 16-bit operands (the full Q x Q collision). On FP32 storage only those
- * higher rows run on the tensor cores, as FP16 high/low splits of per-cell power-of-two scaled
- * operands (three products per contraction, about 22 bits), next to the CUDA-core reduced form;
- * without per-order rates FP32 storage always uses the CUDA-core kernel. Default, until this is
+ * products as dense 16-bit operands (the full Q x Q collision). On FP32 storage only the
+ * correction of those higher rows runs on the tensor cores, next to the CUDA-core reduced form:
+ * it is linear in the pre-collision populations, so it is applied as one dense Q x Q operator
+ * G_ij = sum_r a_r H_r(c_i) H_r(c_j) (a_r = -(s_r - s_high) / N_r, built in FP64), one product
+ * per 128-cell tile with both operands as FP16 high/low splits of power-of-two scaled values
+ * (three products, about 22 bits); without per-order rates FP32 storage always uses the
+ * CUDA-core kernel. Default, until this is
  * called: the tensor cores with distinct higher-order rates (there they are the faster kernel),
  * the CUDA cores otherwise.
  * Device-side waits are bounded; a timeout is latched in the model's status word and returned as
@@ -228,10 +231,11 @@ lbm_status lbm_model_set_tensor_cores(lbm_model* m, int enable);
 
 /* Gather of the pull streaming (Eq. (2-2b)) for 16-bit deviation storage on the CUDA cores
  * (the reduced-form collision and lbm_model_stream_only). ROWS: a CTA works on whole x-rows; the
- * source x-row (y - e_y, z - e_z) of each population comes into shared memory by one bulk copy
- * (n_x * 2 bytes), every thread reads its sources there at (x - e_x) mod n_x, and the collided row
- * goes back to memory by one bulk copy per population. It applies when n_x is a multiple of 8
- * (16-byte rows) and at most 256 cells. THREADS: every thread loads and stores its own cell's
+ * source x-row (y - e_y, z - e_z) of each population comes into a shared-memory row buffer by
+ * 16-byte asynchronous copies (n_x * 2 bytes per population, counted on an mbarrier, a few rows
+ * ahead), every thread reads its sources there at (x - e_x) mod n_x, writes its collided cell
+ * back into the buffer, and the row goes to memory by 16-byte stores. It applies when n_x is a
+ * multiple of 8 (16-byte rows) and at most 256 cells. THREADS: every thread loads and stores its own cell's
  * populations in global memory. Both give bitwise the same populations.
  * With the tensor cores selected (lbm_model_set_tensor_cores), ROWS runs the two contractions
  * on tcgen05 with the A operands written into tensor memory, also with per-order rates (bitwise
