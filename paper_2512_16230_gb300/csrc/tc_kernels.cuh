@@ -358,11 +358,11 @@ __global__ void __launch_bounds__(128, TcShape<L, HI>::CTAS)
 // issued before the CUDA cores collide the same cells and read back after. Both operands are
 // FP32 values, so each is scaled by a power of two (G row by row on the host, the populations per
 // cell) and split into an FP16 high and low part; the product takes three kind::f16 chains into
-// one accumulator,
-// hi.hi + hi.lo + lo.hi (about 22 bits). One CTA-wide barrier per tile orders the operand stores
-// before the product and the previous tile's tensor-memory reads before it is overwritten. The
-// gather of the next tile is issued before this tile's collision, so its latency overlaps the
-// CUDA-core work.
+// one accumulator, hi.hi + hi.lo + lo.hi (about 22 bits). One CTA-wide barrier per tile orders
+// the operand stores before the product and the previous tile's tensor-memory reads before it is
+// overwritten. The gather of the next tile is issued before this tile's collision, so its latency
+// overlaps the CUDA-core work.
+//
 // Resident CTAs per SM of k_step_tc32_high (128 threads each). 3 leaves 168 registers, room for
 // the next tile's populations, which are loaded while the current tile collides: 1.30 ms per step
 // on rD3Q53 256x256x192 against 1.35 ms with 4 CTAs and no prefetch (128 registers) and 1.41 ms
